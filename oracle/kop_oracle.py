@@ -1,0 +1,285 @@
+"""FP64 CPU oracle for Nystrom-preconditioned CG on (K + lam I) x = b.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the library imports this module; only
+the tests, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg call
+it.  It shares no code with the CUDA path: it works from the FP32 input arrays
+promoted to FP64, with plain numpy/scipy primitives and no blocking or fusion
+beyond bounding memory.
+
+What it computes, and where the paper defines it:
+
+* the regularized positive-definite system (K + lam I) x = b with
+  K_ij = k(x_i, x_j) (Sec. 2.1, Eqs. "rlaopt-regularized-linear-system" and
+  "rlaopt-krr");
+* the kernel functions k.  The paper names only k(x_i, x_j); the RBF, Laplace
+  and Matern-5/2 forms used here follow Rasmussen & Williams, which the paper
+  cites for GP inference (Sec. 2.1);
+* the randomized Nystrom approximation of Frangella, Tropp & Udell (cited in
+  Sec. 1, Sec. 2.3 and Sec. 4.3) with damping per the NystromConfig table
+  (App. A.5, "damping_mode");
+* preconditioned CG (Hestenes & Stiefel, cited in Sec. 5.1) with the stopping
+  rule ||r_k|| <= tol ||b|| checked per right-hand side (App. A.1,
+  PCGStoppingCriteria);
+* the adjoint gradient of a validation loss through the solve (Sec. 3.2,
+  Eq. "rlaopt-bilevel"; computed here by an adjoint solve instead of unrolled
+  backpropagation, which gives the same gradient at convergence).
+
+Parity status: every function here is pinned by tests/test_oracle_pins.py
+against closed forms, brute force, library direct solves, exact-recovery and
+finite-termination properties.  Iteration counts of PCG are not pinned
+(rounding changes them).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as sla
+
+RBF, LAPLACE, MATERN52 = 0, 1, 2
+SQRT5 = np.sqrt(5.0)
+EPS64 = np.finfo(np.float64).eps
+
+
+# --------------------------------------------------------------------------
+# Kernel entries (Sec. 2.1: K_ij = k(x_i, x_j)).
+# --------------------------------------------------------------------------
+def sqdist(A, B):
+    """Squared Euclidean distances D2_ij = sum_k (a_ik - b_jk)^2 by direct
+    differences (no norm identity, so no cancellation).  FP64."""
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    out = np.empty((A.shape[0], B.shape[0]))
+    step = max(1, int(2_000_000 // max(1, B.shape[0] * A.shape[1])))
+    for i0 in range(0, A.shape[0], step):
+        diff = A[i0:i0 + step, None, :] - B[None, :, :]
+        out[i0:i0 + step] = np.einsum("ijk,ijk->ij", diff, diff)
+    return out
+
+
+def kernel_from_sqdist(kind, D2, bw):
+    """k as a function of the squared distance.
+    RBF: exp(-r^2 / (2 s^2)); Laplace: exp(-r / s) with Euclidean r;
+    Matern-5/2: (1 + sqrt5 r/l + 5 r^2/(3 l^2)) exp(-sqrt5 r/l)."""
+    D2 = np.asarray(D2, dtype=np.float64)
+    if kind == RBF:
+        return np.exp(-D2 / (2.0 * bw * bw))
+    r = np.sqrt(D2)
+    if kind == LAPLACE:
+        return np.exp(-r / bw)
+    if kind == MATERN52:
+        a = SQRT5 * r / bw
+        return (1.0 + a + a * a / 3.0) * np.exp(-a)
+    raise ValueError(kind)
+
+
+def dkernel_dbw_from_sqdist(kind, D2, bw):
+    """Derivative of k with respect to the bandwidth (sigma or lengthscale)."""
+    D2 = np.asarray(D2, dtype=np.float64)
+    if kind == RBF:
+        return np.exp(-D2 / (2.0 * bw * bw)) * D2 / bw ** 3
+    r = np.sqrt(D2)
+    if kind == LAPLACE:
+        return np.exp(-r / bw) * r / (bw * bw)
+    if kind == MATERN52:
+        a = SQRT5 * r / bw
+        # dk/da = -(a/3)(1+a) e^{-a},  da/dl = -a/l
+        return np.exp(-a) * (a * a / 3.0) * (1.0 + a) / bw
+    raise ValueError(kind)
+
+
+def kernel_matrix(kind, A, B, bw):
+    return kernel_from_sqdist(kind, sqdist(A, B), bw)
+
+
+def kernel_matvec(kind, X, V, bw, Z=None, deriv=False, rows_per_block=None):
+    """O = K(Z, X) V (Z defaults to X), matrix-free over row blocks.
+    With deriv=True, O = (dK(Z, X)/d bw) V."""
+    X = np.asarray(X, dtype=np.float64)
+    Z = X if Z is None else np.asarray(Z, dtype=np.float64)
+    V = np.asarray(V, dtype=np.float64)
+    vec = V.ndim == 1
+    V2 = V[:, None] if vec else V
+    f = dkernel_dbw_from_sqdist if deriv else kernel_from_sqdist
+    if rows_per_block is None:
+        rows_per_block = max(1, int(4_000_000 // max(1, X.shape[0])))
+    out = np.empty((Z.shape[0], V2.shape[1]))
+    for i0 in range(0, Z.shape[0], rows_per_block):
+        out[i0:i0 + rows_per_block] = f(kind, sqdist(Z[i0:i0 + rows_per_block], X), bw) @ V2
+    return out[:, 0] if vec else out
+
+
+# --------------------------------------------------------------------------
+# Randomized Nystrom approximation (Frangella-Tropp-Udell; cited Sec. 1, 2.3).
+# --------------------------------------------------------------------------
+def nystrom(Y, Omega, nu_rel=None):
+    """Rank-r Nystrom approximation A_nys = U diag(lam_hat) U^T of a psd A from
+    the sketch Y = A Omega.
+
+    Steps, in the published order:
+      nu = nu_rel * ||Y||_2 (default nu_rel = sqrt(n) * eps64),
+      Y_nu = Y + nu Omega,
+      C = chol((Omega^T Y_nu + Y_nu^T Omega) / 2)  (upper, C^T C = ...),
+      B = Y_nu C^{-1},
+      B = U Sigma V^T (thin SVD),
+      lam_hat = max(0, Sigma^2 - nu).
+    Omega is used as given (no QR): the approximation Y (Omega^T Y)^+ Y^T is
+    invariant under Omega -> Omega R.  Returns (U, lam_hat descending, nu)."""
+    Y = np.asarray(Y, dtype=np.float64)
+    Om = np.asarray(Omega, dtype=np.float64)
+    n = Y.shape[0]
+    if nu_rel is None:
+        nu_rel = np.sqrt(n) * EPS64
+    nu = nu_rel * np.linalg.norm(Y, 2)
+    Ynu = Y + nu * Om
+    M = Om.T @ Ynu
+    C = np.linalg.cholesky(0.5 * (M + M.T)).T          # upper: M = C^T C
+    Bm = sla.solve_triangular(C, Ynu.T, trans="T", lower=False).T   # Y_nu C^{-1}
+    U, s, _ = np.linalg.svd(Bm, full_matrices=False)
+    lam_hat = np.maximum(0.0, s * s - nu)
+    return U, lam_hat, nu
+
+
+def nystrom_rho(lam_hat, mu, adaptive=True):
+    """Damping of the complement subspace (App. A.5 NystromConfig):
+    adaptive adds the smallest retained eigenvalue lam_hat_r to mu."""
+    return (lam_hat[-1] + mu) if adaptive else mu
+
+
+def precond_apply(U, lam_hat, mu, rho, V):
+    """P^{-1} V = V / rho + U [ (diag(lam_hat) + mu I)^{-1} - I / rho ] U^T V."""
+    V = np.asarray(V, dtype=np.float64)
+    W = U.T @ V
+    scale = 1.0 / (lam_hat + mu) - 1.0 / rho
+    W = (scale[:, None] * W) if W.ndim == 2 else scale * W
+    return V / rho + U @ W
+
+
+# --------------------------------------------------------------------------
+# Preconditioned CG (Hestenes-Stiefel; stopping rule App. A.1).
+# --------------------------------------------------------------------------
+def pcg(apply_A, b, apply_Pinv=None, tol=1e-6, maxit=1000, x0=None):
+    """Textbook PCG for one right-hand side.
+
+    x0 = 0 unless given; r = b - A x0; z = P^{-1} r; p = z; then repeat
+      q = A p; alpha = r^T z / p^T q; x += alpha p; r -= alpha q;
+      stop if ||r|| <= tol ||b||;  z = P^{-1} r;  beta = r^T z_new / r^T z_old;
+      p = z + beta p.
+    Returns x, the number of A-products, and the recursive relative residual
+    history ||r_k|| / ||b|| (entry 0 is the initial residual)."""
+    b = np.asarray(b, dtype=np.float64)
+    P = apply_Pinv if apply_Pinv is not None else (lambda v: v)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
+    r = b - apply_A(x) if x0 is not None else b.copy()
+    nb = np.linalg.norm(b)
+    hist = [np.linalg.norm(r) / nb]
+    if hist[0] <= tol:
+        return x, 0, hist
+    z = P(r)
+    p = z.copy()
+    rz = r @ z
+    it = 0
+    while it < maxit:
+        q = apply_A(p)
+        pq = p @ q
+        if not pq > 0:
+            raise FloatingPointError("PCG breakdown: p^T A p <= 0")
+        alpha = rz / pq
+        x = x + alpha * p
+        r = r - alpha * q
+        it += 1
+        hist.append(np.linalg.norm(r) / nb)
+        if hist[-1] <= tol:
+            break
+        z = P(r)
+        rz_new = r @ z
+        beta = rz_new / rz
+        rz = rz_new
+        p = z + beta * p
+    return x, it, hist
+
+
+def shifted_operator(kind, X, bw, lam, K=None):
+    """v -> (K + lam I) v, with K explicit if given, else matrix-free."""
+    if K is not None:
+        return lambda v: K @ v + lam * v
+    return lambda v: kernel_matvec(kind, X, v, bw) + lam * v
+
+
+def krr_solve(kind, X, B, bw, lambdas, Omega=None, mu=None, adaptive=True, tol=1e-6,
+              maxit=1000, nu_rel=None, explicit=True):
+    """Nystrom PCG over all columns of B and all shifts (column c = rhs j,
+    shift s with c = s * nrhs + j); each column runs its own CG (App. A.1:
+    the stopping condition must hold for each right-hand side).  mu defaults
+    to each column's lam.  Returns X_sol (n x cols), iteration counts and
+    histories, plus the Nystrom factors."""
+    X = np.asarray(X, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    if B.ndim == 1:
+        B = B[:, None]
+    K = kernel_matrix(kind, X, X, bw) if explicit else None
+    apply_K = (lambda v: K @ v) if explicit else (lambda v: kernel_matvec(kind, X, v, bw))
+    U = lam_hat = None
+    if Omega is not None:
+        Y = apply_K(np.asarray(Omega, dtype=np.float64))
+        U, lam_hat, _ = nystrom(Y, Omega, nu_rel)
+    cols, iters, hists = [], [], []
+    for lam in np.atleast_1d(lambdas):
+        m = lam if mu is None else mu
+        Pinv = None
+        if U is not None:
+            rho = nystrom_rho(lam_hat, m, adaptive)
+            Pinv = (lambda v, m=m, rho=rho: precond_apply(U, lam_hat, m, rho, v))
+        for j in range(B.shape[1]):
+            x, it, h = pcg(lambda v, lam=lam: apply_K(v) + lam * v, B[:, j], Pinv, tol, maxit)
+            cols.append(x)
+            iters.append(it)
+            hists.append(h)
+    return np.stack(cols, axis=1), iters, hists, (U, lam_hat)
+
+
+def true_relres(kind, X, bw, lam, x, b, K=None):
+    """||(K + lam I) x - b|| / ||b|| in FP64 (App. B.2, relative-residual check)."""
+    x = np.asarray(x, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    Kx = (K @ x) if K is not None else kernel_matvec(kind, X, x, bw)
+    return np.linalg.norm(Kx + lam * x - b) / np.linalg.norm(b)
+
+
+# --------------------------------------------------------------------------
+# Gradient of a validation loss through the solve (Sec. 3.2).
+# --------------------------------------------------------------------------
+def krr_val_loss(kind, X, y, Xv, yv, bw, lam):
+    """L(bw, lam) = (1/n_val) ||K(Xv, X) x - yv||^2, x = (K + lam I)^{-1} y,
+    by a dense Cholesky solve (for finite-difference checks)."""
+    K = kernel_matrix(kind, X, X, bw)
+    A = K + lam * np.eye(K.shape[0])
+    x = sla.cho_solve(sla.cho_factor(A), np.asarray(y, dtype=np.float64))
+    e = kernel_matrix(kind, Xv, X, bw) @ x - np.asarray(yv, dtype=np.float64)
+    return float(e @ e / len(e)), x
+
+
+def krr_val_grad(kind, X, y, Xv, yv, bw, lam, x=None, solve=None):
+    """Adjoint gradient of L with respect to (bw, lam).
+
+    e = K_v x - yv;  dL/dx = (2/n_val) K_v^T e;  g = (K + lam I)^{-1} dL/dx;
+    dL/dlam = -g^T x;
+    dL/dbw  = (2/n_val) e^T (dK_v/dbw) x - g^T (dK/dbw) x.
+    ``solve`` maps a right-hand side to (K + lam I)^{-1} rhs (dense Cholesky
+    by default)."""
+    X = np.asarray(X, dtype=np.float64)
+    Xv = np.asarray(Xv, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    yv = np.asarray(yv, dtype=np.float64)
+    if solve is None:
+        K = kernel_matrix(kind, X, X, bw)
+        cf = sla.cho_factor(K + lam * np.eye(K.shape[0]))
+        solve = lambda rhs: sla.cho_solve(cf, rhs)
+    if x is None:
+        x = solve(y)
+    nv = Xv.shape[0]
+    e = kernel_matvec(kind, X, x, bw, Z=Xv) - yv
+    dLdx = (2.0 / nv) * kernel_matvec(kind, Xv, e, bw, Z=X)
+    g = solve(dLdx)
+    dlam = -g @ x
+    dbw = (2.0 / nv) * (e @ kernel_matvec(kind, X, x, bw, Z=Xv, deriv=True)) \
+        - g @ kernel_matvec(kind, X, x, bw, deriv=True)
+    return float(e @ e / nv), float(dbw), float(dlam), g
