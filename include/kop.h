@@ -1,0 +1,192 @@
+/*
+ * kop.h - C ABI of a single-GPU (B300, sm_103a) Nystrom-preconditioned CG
+ * solver for dense regularized kernel systems
+ *
+ *     (K(X, X) + lam I) x = b,        K_ij = k(x_i, x_j),
+ *
+ * the problem class of the paper's Sec. 2.1 (Eq. "rlaopt-regularized-linear-
+ * system"; kernel ridge regression, Eq. "rlaopt-krr", whose optimality
+ * condition is exactly this system with b = y).  K is never formed: every
+ * product K V is computed tile by tile by a fused kernel (distances on the
+ * tensor cores, kernel function in registers, contraction with V) - the
+ * matrix-free linear operator of Sec. 4.3.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Matrices are row-major FP32 unless stated.  X is n x d, a block of vectors
+ *   V is n x m (m columns, column c of row i at V[i*m + c]).
+ * - Array pointers are DEVICE pointers owned by the caller and borrowed only
+ *   for the duration of the call (stream-ordered on `stream`, a cudaStream_t
+ *   passed as void*; NULL = legacy default stream).  Arguments documented as
+ *   "host" are host pointers.
+ * - Handles own device copies of whatever they keep: kop_t keeps the centred
+ *   points, their row norms and their BF16 split; nys_t keeps U and the
+ *   approximate eigenvalues.  A nys_t must not outlive the kop_t it was built
+ *   from.  Handles are not thread-safe; distinct handles may be used from
+ *   distinct host threads.
+ * - Every call returns a status (enum kop_status).  No C++ exception crosses
+ *   the ABI.  On failure kop_last_error() returns a message for the calling
+ *   host thread.  Invalid arguments (n < 1, d outside 1..128, bandwidth or
+ *   shifts not finite and > 0, null pointers, m < 1) give KOP_EINVAL with
+ *   nothing launched.  Device-side waits are bounded: a wait that runs out
+ *   makes the call return KOP_ETIMEOUT instead of hanging.
+ */
+#ifndef KOP_H_
+#define KOP_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kop_s* kop_t;
+typedef struct nys_s* nys_t;
+
+/* Kernel functions.  The paper names only k(x_i, x_j) (Sec. 2.1); the forms
+ * follow Rasmussen & Williams (cited there for GP inference), with Euclidean
+ * r = ||x_i - x_j|| and bandwidth s (sigma, or the Matern lengthscale):
+ *   RBF       exp(-r^2 / (2 s^2))
+ *   LAPLACE   exp(-r / s)
+ *   MATERN52  (1 + sqrt5 r/s + 5 r^2 / (3 s^2)) exp(-sqrt5 r / s)          */
+enum kop_kernel { KOP_RBF = 0, KOP_LAPLACE = 1, KOP_MATERN52 = 2 };
+
+/* Operator precision modes.
+ *   KOP_FAST      distances from a 2-term BF16 split (hi + mid) of the centred
+ *                 points on the tensor cores (3 MMAs, FP32 accumulation);
+ *                 entries accurate to about 2^-15 relative.
+ *   KOP_ACCURATE  3-term split (6 MMAs), entries accurate to FP32 rounding;
+ *                 used for the periodic true residual of the solver.
+ *   KOP_PLAIN     plain FP32 CUDA-core path: direct-difference distances,
+ *                 FP32 exp and FMA contraction; no tensor cores.  The speed
+ *                 baseline of the fused path.                               */
+enum kop_mode { KOP_FAST = 0, KOP_ACCURATE = 1, KOP_PLAIN = 2 };
+
+enum kop_status {
+  KOP_OK = 0,
+  KOP_NOT_CONVERGED = 1, /* warning: maxit reached, outputs written        */
+  KOP_EINVAL = -1,       /* invalid argument, nothing launched              */
+  KOP_ENOMEM = -2,       /* device allocation failed                        */
+  KOP_ECUDA = -3,        /* CUDA runtime/launch error                        */
+  KOP_ENOTPD = -4,       /* Cholesky pivot <= 0 or PCG breakdown p^T A p <= 0 */
+  KOP_ETIMEOUT = -5      /* a bounded device-side wait ran out              */
+};
+
+/* Message describing the last failure on this host thread ("" if none). */
+const char* kop_last_error(void);
+
+/* Number of CUDA kernels this library has launched since it was loaded (all
+ * host threads; a diagnostic for benchmarks).  Not in the paper: it only
+ * reports on the library itself. */
+int64_t kop_launch_count(void);
+
+/* ---------------------------------------------------------------------------
+ * Kernel operator (the matrix-free linear operator of Sec. 4.3; K of
+ * Sec. 2.1 Eq. "rlaopt-krr").
+ *
+ * kop_create: X (device, n x d FP32) is copied: the column mean is removed
+ * (k depends on x_i - x_j only, so K is unchanged), then FP32 row norms and
+ * the hi/mid/lo BF16 split are stored, padded to 128 rows and to d' in
+ * {16, 32, 64, 128} columns.  Synchronizes `stream` before
+ * returning.  1 <= n < 2^31, 1 <= d <= 128.  Device memory held:
+ * about n * d' * 10 bytes.                                                  */
+int kop_create(const float* X, int64_t n, int32_t d, int32_t kernel, double bandwidth,
+               void* stream, kop_t* out);
+int kop_destroy(kop_t op);
+/* Change the bandwidth in place (the points are kept). */
+int kop_set_bandwidth(kop_t op, double bandwidth);
+
+/* O (n x m) = K(X, X) V for V (n x m).  mode: enum kop_mode.  Asynchronous;
+ * the device status of the operator is read by kop_sync(). */
+int kop_matvec(kop_t op, const float* V, int32_t m, float* O, int32_t mode, void* stream);
+
+/* Rectangular products against other points Z (device, nz x d FP32; centred
+ * with the operator's own column mean):
+ *   transpose = 0:  O (nz x m) = K(Z, X) V,     V is n x m
+ *   transpose = 1:  O (n x m)  = K(X, Z) V,     V is nz x m
+ * deriv = 1 replaces k by dk/d(bandwidth) (used by the adjoint gradient).   */
+int kop_cross_matvec(kop_t op, const float* Z, int64_t nz, const float* V, int32_t m, float* O,
+                     int32_t transpose, int32_t deriv, int32_t mode, void* stream);
+
+/* O (n x m) = (dK(X, X)/d bandwidth) V. */
+int kop_dbw_matvec(kop_t op, const float* V, int32_t m, float* O, int32_t mode, void* stream);
+
+/* Synchronize `stream` and return the operator's device status (KOP_OK or
+ * KOP_ETIMEOUT), clearing it. */
+int kop_sync(kop_t op, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Randomized Nystrom preconditioner (Frangella, Tropp & Udell, cited in
+ * Sec. 1 and Sec. 2.3; NystromConfig, App. A.5).
+ *
+ * nys_build: Omega (device, n x r FP32) is the caller's test matrix (the
+ * library does not orthonormalize it; Gaussian N(0,1)/sqrt(n) entries are
+ * expected).  Steps: Y = K Omega (fused operator, `mode`),
+ * nu = nu_rel * ||Y||_2 (nu_rel <= 0 selects 2^-16 for KOP_FAST and 2^-21
+ * otherwise), Y_nu = Y + nu Omega, C = chol(sym(Omega^T Y_nu)) in FP64 (on a
+ * failed pivot nu grows 10x, at most 3 times, then KOP_ENOTPD),
+ * eigen-decomposition of C^-T (Y_nu^T Y_nu) C^-1 = V S^2 V^T in FP64,
+ * U = Y_nu C^-1 V S^-1 (re-orthonormalized once), lam_hat = max(0, S^2 - nu)
+ * in descending order.  1 <= r <= min(n, 2048).  Synchronizes `stream`.   */
+int nys_build(kop_t op, const float* Omega, int32_t r, double nu_rel, int32_t mode, void* stream,
+              nys_t* out);
+int nys_destroy(nys_t ny);
+
+/* O = P^-1 V column by column, with damping mu[c] (host, m values):
+ *   P^-1 v = v / rho + U [ (diag(lam_hat) + mu I)^-1 - I / rho ] U^T v,
+ *   rho = lam_hat_r + mu (adaptive != 0) or mu (adaptive == 0).
+ * This is the inverse of the damped Nystrom preconditioner of App. A.5
+ * ("damping_mode") divided by rho; PCG iterates do not depend on that
+ * scale.  V, O: device n x m.                                               */
+int nys_apply(nys_t ny, const double* mu, int32_t adaptive, const float* V, int32_t m, float* O,
+              void* stream);
+
+/* Host copies: lam_hat (r doubles, descending), nu (1 double), r (int). */
+int nys_eigs(nys_t ny, double* lam_hat, double* nu, int32_t* r);
+/* Device copy of U (n x r FP32 row-major) into U_out. */
+int nys_factor(nys_t ny, float* U_out, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Preconditioned CG (Hestenes & Stiefel, cited in Sec. 5.1) over a block of
+ * independent columns: column c = s * nrhs + j solves
+ *     (K + lambdas[s] I) x_c = B[:, j]
+ * with its own alpha and beta; each column stops when its recursive residual
+ * satisfies ||r|| <= tol ||b|| (PCGStoppingCriteria, App. A.1: the
+ * condition must hold for every right-hand side) AND the true residual,
+ * recomputed with `refine_mode`, does too.  Every `refine_every` iterations
+ * (0 = only at the end) the recursive residual is replaced by the true one
+ * (iterative refinement: inner products with `inner_mode`, accuracy from
+ * `refine_mode`).  ny = NULL gives plain CG (IdentityConfig, App. A.1).
+ * The preconditioner of column c uses damping mu[s] (host; NULL: mu = lambdas).
+ *   lambdas      host, n_shifts values > 0
+ *   B            device, n x nrhs
+ *   Xout         device, n x (nrhs * n_shifts); x0 = 0
+ *   iters        host, nrhs * n_shifts ints (operator products per column)
+ *   res_hist     host or NULL, (maxit + 1) x cols doubles: recursive
+ *                ||r_k|| / ||b|| per iteration (NaN after a column stops)
+ *   true_relres  host or NULL, cols doubles: final true relative residual
+ * Returns KOP_OK, KOP_NOT_CONVERGED (outputs written), KOP_ENOTPD on a
+ * breakdown.  Synchronizes `stream`.                                         */
+int pcg_solve(kop_t op, nys_t ny, const double* lambdas, int32_t n_shifts, const double* mu,
+              int32_t adaptive, const float* B, int32_t nrhs, double tol, int32_t maxit,
+              int32_t refine_every, int32_t inner_mode, int32_t refine_mode, float* Xout,
+              int32_t* iters, double* res_hist, double* true_relres, void* stream);
+
+/* Adjoint of one solve (the paper differentiates through the solver,
+ * Sec. 3.2, Eq. "rlaopt-bilevel"; here by an adjoint solve instead of
+ * unrolling, which gives the same gradient at convergence).  Given the
+ * solution x of (K + lam I) x = b and dL/dx (device, n), solves
+ *     (K + lam I) g = dL/dx
+ * with the same preconditioner (mu = lam), writes g (device, n) and the host
+ * scalars
+ *     dL/dlam = -g^T x,        dL/dbw|_K = -g^T (dK/dbw) x,
+ * (dL/db = g).  iters: host int (may be NULL).                              */
+int pcg_adjoint(kop_t op, nys_t ny, double lam, int32_t adaptive, const float* x,
+                const float* dLdx, double tol, int32_t maxit, int32_t refine_every,
+                int32_t inner_mode, int32_t refine_mode, float* g_out, int32_t* iters,
+                double* dLdlam, double* dLdbw, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KOP_H_ */

@@ -1,0 +1,705 @@
+// Dense helpers of the Nystrom construction and the preconditioner apply:
+// tall-skinny products over the n rows (FP32 data, FP64 accumulation) and
+// the small r x r factorizations in FP64 (Cholesky, triangular solves, the
+// symmetric eigen-decomposition by parallel cyclic Jacobi, sorting).
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "kop_device.cuh"
+#include "kop_dense.h"
+#include "kop_internal.h"
+
+namespace kop {
+
+// ------------------------------------------------------------------ Gram
+// C (p x q, FP64, row-major, ldc) += A^T B over rows [0, n) of A (n x p, lda)
+// and B (n x q, ldb).  CTA tile 64 x 64 of C, 256 threads with 4 x 4 outputs
+// each; rows are consumed in chunks of 32 staged in shared memory, summed in
+// FP32 within a chunk and in FP64 across chunks; CTAs along z split the rows
+// and add their partial tiles atomically.
+constexpr int GT = 64, GK = 32;
+
+__global__ void __launch_bounds__(256) gram_kernel(const float* __restrict__ A, int lda, const float* __restrict__ B,
+                                                   int ldb, int64_t n, int p, int q, double* __restrict__ C, int ldc,
+                                                   int64_t rows_per_split) {
+  __shared__ float As[GK][GT + 4];
+  __shared__ float Bs[GK][GT + 4];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int p0 = blockIdx.x * GT, q0 = blockIdx.y * GT;
+  const int64_t r0 = (int64_t)blockIdx.z * rows_per_split;
+  const int64_t r1 = r0 + rows_per_split < n ? r0 + rows_per_split : n;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  for (int64_t k0 = r0; k0 < r1; k0 += GK) {
+    for (int idx = threadIdx.x; idx < GK * GT; idx += 256) {
+      const int kk = idx / GT, c = idx - kk * GT;
+      const int64_t row = k0 + kk;
+      As[kk][c] = (row < r1 && p0 + c < p) ? A[row * lda + p0 + c] : 0.0f;
+      Bs[kk][c] = (row < r1 && q0 + c < q) ? B[row * ldb + q0 + c] : 0.0f;
+    }
+    __syncthreads();
+    float part[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) part[i][j] = 0.0f;
+#pragma unroll 8
+    for (int kk = 0; kk < GK; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) part[i][j] = fmaf(a[i], b[j], part[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] += (double)part[i][j];
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int pi = p0 + ty * 4 + i;
+    if (pi >= p) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int qj = q0 + tx * 4 + j;
+      if (qj < q) atomicAdd(&C[(int64_t)pi * ldc + qj], acc[i][j]);
+    }
+  }
+}
+
+int gram(const float* A, int lda, const float* B, int ldb, int64_t n, int p, int q, double* C, int ldc,
+         cudaStream_t st) {
+  KOP_CUDA_TRY(cudaMemsetAsync(C, 0, sizeof(double) * (size_t)p * ldc, st));
+  const int tiles = ((p + GT - 1) / GT) * ((q + GT - 1) / GT);
+  int64_t splits = (2 * num_sms() + tiles - 1) / tiles;
+  const int64_t max_splits = (n + 255) / 256;
+  if (splits > max_splits) splits = max_splits;
+  if (splits < 1) splits = 1;
+  int64_t rps = (n + splits - 1) / splits;
+  rps = ((rps + GK - 1) / GK) * GK;
+  splits = (n + rps - 1) / rps;
+  dim3 grid((p + GT - 1) / GT, (q + GT - 1) / GT, (unsigned)splits);
+  gram_kernel<<<grid, 256, 0, st>>>(A, lda, B, ldb, n, p, q, C, ldc, rps);
+  KOP_LAUNCHED();
+  return KOP_OK;
+}
+
+// ------------------------------------------------------------------ tall GEMM
+// O (n x q, ldo) = alpha_col[c] * V[i][c]  +  (A + beta * A2)(n x p) W (p x q, FP32)
+// (V, A2 optional).  CTA tile 64 rows x 64 columns, 256 threads x (4 x 4).
+__global__ void __launch_bounds__(256) tall_gemm_kernel(const float* __restrict__ A, const float* __restrict__ A2,
+                                                        float beta, int lda, int64_t n, int p,
+                                                        const float* __restrict__ W, int ldw, int q,
+                                                        const float* __restrict__ V, int ldv,
+                                                        const float* __restrict__ alpha_col, float* __restrict__ O,
+                                                        int ldo) {
+  __shared__ float As[GT][GK + 1];
+  __shared__ float Ws[GK][GT + 4];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int64_t i0 = (int64_t)blockIdx.x * GT;
+  const int c0 = blockIdx.y * GT;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+  for (int k0 = 0; k0 < p; k0 += GK) {
+    for (int idx = threadIdx.x; idx < GT * GK; idx += 256) {
+      const int r = idx / GK, kk = idx - r * GK;
+      const int64_t row = i0 + r;
+      float v = 0.0f;
+      if (row < n && k0 + kk < p) {
+        v = A[row * lda + k0 + kk];
+        if (A2) v = fmaf(beta, A2[row * lda + k0 + kk], v);
+      }
+      As[r][kk] = v;
+    }
+    for (int idx = threadIdx.x; idx < GK * GT; idx += 256) {
+      const int kk = idx / GT, c = idx - kk * GT;
+      Ws[kk][c] = (k0 + kk < p && c0 + c < q) ? W[(int64_t)(k0 + kk) * ldw + c0 + c] : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < GK; ++kk) {
+      float a[4], w[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[ty * 4 + i][kk];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) w[j] = Ws[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], w[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t row = i0 + ty * 4 + i;
+    if (row >= n) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = c0 + tx * 4 + j;
+      if (c >= q) continue;
+      float v = acc[i][j];
+      if (V) v = fmaf(alpha_col[c], V[row * ldv + c], v);
+      O[row * ldo + c] = v;
+    }
+  }
+}
+
+int tall_gemm(const float* A, const float* A2, float beta, int lda, int64_t n, int p, const float* W, int ldw, int q,
+              const float* V, int ldv, const float* alpha_col, float* O, int ldo, cudaStream_t st) {
+  dim3 grid((unsigned)((n + GT - 1) / GT), (unsigned)((q + GT - 1) / GT));
+  tall_gemm_kernel<<<grid, 256, 0, st>>>(A, A2, beta, lda, n, p, W, ldw, q, V, ldv, alpha_col, O, ldo);
+  KOP_LAUNCHED();
+  return KOP_OK;
+}
+
+// ------------------------------------------------------------------ single vector
+// w (p, FP64, pre-zeroed) += U^T v over rows; U n x p (ldu), v n (stride ldv).
+__global__ void __launch_bounds__(256) utv_kernel(const float* __restrict__ U, int ldu, int64_t n, int p,
+                                                  const float* __restrict__ v, int ldv, int64_t rows_per_block,
+                                                  double* __restrict__ w) {
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
+  const int64_t r1 = r0 + rows_per_block < n ? r0 + rows_per_block : n;
+  for (int k = threadIdx.x; k < p; k += blockDim.x) {
+    float s = 0.0f, e = 0.0f;
+    for (int64_t i = r0; i < r1; i += 16) {
+      float part = 0.0f;
+      const int64_t iend = i + 16 < r1 ? i + 16 : r1;
+      for (int64_t ii = i; ii < iend; ++ii) part = fmaf(U[ii * ldu + k], v[ii * ldv], part);
+      two_sum_acc(s, e, part);
+    }
+    atomicAdd(&w[k], (double)s + (double)e);
+  }
+}
+
+// o[i] = alpha[0] * v[i] + sum_k U[i][k] w[k]; one warp per row.
+__global__ void __launch_bounds__(256) uw_kernel(const float* __restrict__ U, int ldu, int64_t n, int p,
+                                                 const float* __restrict__ w, const float* __restrict__ v, int ldv,
+                                                 const float* __restrict__ alpha, float* __restrict__ o, int ldo) {
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  float s = 0.0f;
+  for (int k = lane; k < p; k += 32) s = fmaf(U[row * ldu + k], w[k], s);
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (lane == 0) o[row * ldo] = fmaf(alpha[0], v[row * ldv], s);
+}
+
+int utv(const float* U, int ldu, int64_t n, int p, const float* v, int ldv, double* w, cudaStream_t st) {
+  KOP_CUDA_TRY(cudaMemsetAsync(w, 0, sizeof(double) * p, st));
+  int64_t blocks = 4 * num_sms();
+  int64_t rpb = (n + blocks - 1) / blocks;
+  if (rpb < 64) rpb = 64;
+  blocks = (n + rpb - 1) / rpb;
+  utv_kernel<<<(unsigned)blocks, 256, 0, st>>>(U, ldu, n, p, v, ldv, rpb, w);
+  KOP_LAUNCHED();
+  return KOP_OK;
+}
+
+int uw(const float* U, int ldu, int64_t n, int p, const float* w, const float* v, int ldv, const float* alpha,
+       float* o, int ldo, cudaStream_t st) {
+  const int64_t threads = n * 32;
+  uw_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(U, ldu, n, p, w, v, ldv, alpha, o, ldo);
+  KOP_LAUNCHED();
+  return KOP_OK;
+}
+
+// ------------------------------------------------------------------ r x r FP64
+// Element-wise combinations of the r x r Gram blocks.
+//   mode 0: M = (Goy + Goy^T)/2 + nu Goo
+//   mode 1: M = Gyy + nu (Goy + Goy^T) + nu^2 Goo
+__global__ void combine_kernel(const double* __restrict__ Goo, const double* __restrict__ Goy,
+                               const double* __restrict__ Gyy, int r, double nu, int mode, double* __restrict__ M) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)r * r) return;
+  const int i = (int)(idx / r), j = (int)(idx - (int64_t)i * r);
+  const double s = Goy[(int64_t)i * r + j] + Goy[(int64_t)j * r + i];
+  if (mode == 0)
+    M[idx] = 0.5 * s + nu * Goo[idx];
+  else
+    M[idx] = Gyy[idx] + nu * s + nu * nu * Goo[idx];
+}
+
+int combine(const double* Goo, const double* Goy, const double* Gyy, int r, double nu, int mode, double* M,
+            cudaStream_t st) {
+  const int64_t tot = (int64_t)r * r;
+  combine_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(Goo, Goy, Gyy, r, nu, mode, M);
+  KOP_LAUNCHED();
+  return KOP_OK;
+}
+
+// In-place lower Cholesky A = L L^T (row-major r x r; the strict upper part is
+// zeroed).  One CTA, right-looking.  info[0] = 0 on success, k + 1 if pivot k
+// is not positive (or not finite).
+__global__ void __launch_bounds__(1024) cholesky_kernel(double* A, int r, int* info) {
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int k = 0; k < r; ++k) {
+    if (threadIdx.x == 0) {
+      const double akk = A[(int64_t)k * r + k];
+      if (!(akk > 0.0) || !isfinite(akk)) {
+        bad = k + 1;
+      } else {
+        A[(int64_t)k * r + k] = sqrt(akk);
+      }
+    }
+    __syncthreads();
+    if (bad) break;
+    const double lkk = A[(int64_t)k * r + k];
+    for (int i = k + 1 + threadIdx.x; i < r; i += blockDim.x) A[(int64_t)i * r + k] /= lkk;
+    __syncthreads();
+    // trailing update of the lower triangle: A[i][j] -= L[i][k] L[j][k], k < j <= i;
+    // one warp per row, lanes along j
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int i = k + 1 + warp; i < r; i += nw) {
+      const double lik = A[(int64_t)i * r + k];
+      for (int j = k + 1 + lane; j <= i; j += 32) A[(int64_t)i * r + j] -= lik * A[(int64_t)j * r + k];
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  for (int64_t t = threadIdx.x; t < (int64_t)r * r; t += blockDim.x) {
+    const int i = (int)(t / r), j = (int)(t - (int64_t)i * r);
+    if (j > i) A[t] = 0.0;
+  }
+  if (threadIdx.x == 0) info[0] = bad;
+}
+
+int cholesky(double* A, int r, int* info, cudaStream_t st) {
+  cholesky_kernel<<<1, 1024, 0, st>>>(A, r, info);
+  KOP_LAUNCHED();
+  return KOP_OK;
+}
+
+// Triangular solves with r x r L (lower, row-major) and q right-hand sides
+// stored as COLUMNS of B (r x q, row-major, ldb); the solution overwrites B.
+//   trans = 0: L X = B   (forward)
+//   trans = 1: L^T X = B (backward)
+// One warp per right-hand side column.
+__global__ void __launch_bounds__(256) trsm_kernel(const double* __restrict__ L, int r, double* B, int ldb, int q,
+                                                   int trans) {
+  const int col = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (col >= q) return;
+  if (!trans) {
+    for (int i = 0; i < r; ++i) {
+      double s = 0.0;
+      for (int k = lane; k < i; k += 32) s += L[(int64_t)i * r + k] * B[(int64_t)k * ldb + col];
+      for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+      if (lane == 0) B[(int64_t)i * ldb + col] = (B[(int64_t)i * ldb + col] - s) / L[(int64_t)i * r + i];
+      __syncwarp();
+    }
+  } else {
+    for (int i = r - 1; i >= 0; --i) {
+      double s = 0.0;
+      for (int k = i + 1 + lane; k < r; k += 32) s += L[(int64_t)k * r + i] * B[(int64_t)k * ldb + col];
+      for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+      if (lane == 0) B[(int64_t)i * ldb + col] = (B[(int64_t)i * ldb + col] - s) / L[(int64_t)i * r + i];
+      __syncwarp();
+    }
+  }
+}
+
+int trsm(const double* L, int r, double* B, int ldb, int q, int trans, cudaStream_t st) {
+  const int64_t threads = (int64_t)q * 32;
+  trsm_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(L, r, B, ldb, q, trans);
+  KOP_LAUNCHED();
+  return KOP_OK;
+}
+
+// B = A^T (r x r) and optionally symmetrize: S = (A + A^T) / 2.
+__global__ void transpose_kernel(const double* __restrict__ A, int r, double* __restrict__ B, int sym) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)r * r) return;
+  const int i = (int)(t / r), j = (int)(t - (int64_t)i * r);
+  B[t] = sym ? 0.5 * (A[t] + A[(int64_t)j * r + i]) : A[(int64_t)j * r + i];
+}
+
+int transpose(const double* A, int r, double* B, int sym, cudaStream_t st) {
+  const int64_t tot = (int64_t)r * r;
+  transpose_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(A, r, B, sym);
+  KOP_LAUNCHED();
+  return KOP_OK;
+}
+
+// Largest eigenvalue of a symmetric psd r x r matrix by power iteration (one
+// CTA, FP64).  out[0] = Rayleigh quotient after `iters` steps.
+__global__ void __launch_bounds__(1024) power_kernel(const double* __restrict__ G, int r, int iters, double* out) {
+  extern __shared__ double pv[];  // 2r
+  double* v = pv;
+  double* w = pv + r;
+  __shared__ double red[32];
+  __shared__ double scal;
+  for (int i = threadIdx.x; i < r; i += blockDim.x) v[i] = 1.0 + 0.01 * (double)(i % 7);
+  __syncthreads();
+  double lam = 0.0;
+  for (int it = 0; it < iters; ++it) {
+    for (int i = threadIdx.x; i < r; i += blockDim.x) {
+      double s = 0.0;
+      for (int k = 0; k < r; ++k) s += G[(int64_t)i * r + k] * v[k];
+      w[i] = s;
+    }
+    __syncthreads();
+    // lam = v.w / v.v ; v = w / |w|
+    double vw = 0.0, vv = 0.0, ww = 0.0;
+    for (int i = threadIdx.x; i < r; i += blockDim.x) {
+      vw += v[i] * w[i];
+      vv += v[i] * v[i];
+      ww += w[i] * w[i];
+    }
+    double vals[3] = {vw, vv, ww};
+    double tot[3];
+    for (int c = 0; c < 3; ++c) {
+      double x = vals[c];
+      for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
+      __syncthreads();
+      if (threadIdx.x < 32) {
+        double y = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int off = 16; off > 0; off >>= 1) y += __shfl_xor_sync(0xffffffffu, y, off);
+        if (threadIdx.x == 0) scal = y;
+      }
+      __syncthreads();
+      tot[c] = scal;
+      __syncthreads();
+    }
+    lam = tot[1] > 0.0 ? tot[0] / tot[1] : 0.0;
+    const double inv = tot[2] > 0.0 ? 1.0 / sqrt(tot[2]) : 0.0;
+    for (int i = threadIdx.x; i < r; i += blockDim.x) v[i] = w[i] * inv;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = lam;
+}
+
+int power_max_eig(const double* G, int r, int iters, double* out, cudaStream_t st) {
+  const size_t smem = sizeof(double) * 2 * r;
+  if (smem > 48 * 1024) KOP_CUDA_TRY(cudaFuncSetAttribute(power_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                          (int)smem));
+  power_kernel<<<1, 1024, smem, st>>>(G, r, iters, out);
+  KOP_LAUNCHED();
+  return KOP_OK;
+}
+
+// ------------------------------------------------------------------ Jacobi
+// Symmetric eigen-decomposition A = V diag(w) V^T by cyclic Jacobi with the
+// round-robin (tournament) ordering, so that all re/2 rotations of one step
+// touch disjoint index pairs and are applied at once:
+//   B = J^T A J,   V <- V J,
+// where column i of J has a_i at row i and b_i at row partner(i).  For a pair
+// (p, q) the rotation zeroing A_pq is the one of Golub & Van Loan
+// (symmetric Schur decomposition): tau = (A_qq - A_pp) / (2 A_pq),
+// t = sign(tau) / (|tau| + sqrt(1 + tau^2)), c = 1/sqrt(1 + t^2), s = t c;
+// column p of J is (c at p, -s at q), column q is (s at p, c at q).
+// The matrix is padded to an even size re with a zero row/column that is
+// never rotated.  One cooperative launch; steps are separated by a bounded
+// grid barrier.  Sweeps stop when the off-diagonal Frobenius norm falls below
+// tol times the norm of the diagonal, or after max_sweeps.
+struct JacobiArgs {
+  double* A;  // re x re, current
+  double* B;  // re x re, next
+  double* V;  // re x re
+  double* V2;
+  int re;
+  int max_sweeps;
+  double tol;
+  double* offsum;  // per sweep: [2 * s] = off^2, [2 * s + 1] = diag^2
+  unsigned int* bar_count;
+  unsigned int* bar_gen;
+  int* status;
+  int* sweeps_done;
+};
+
+KOP_DEV int rr_partner_pos(int pos, int re) { return re - 1 - pos; }
+
+// Index sitting at position `pos` of the tournament table in step s:
+// position 0 holds index 0; positions 1..re-1 hold (pos - 1 + s) mod (re - 1) + 1.
+KOP_DEV int rr_index(int pos, int s, int re) { return pos == 0 ? 0 : ((pos - 1 + s) % (re - 1)) + 1; }
+
+KOP_DEV bool grid_barrier(unsigned int* count, unsigned int* gen, unsigned int nblocks, int* status) {
+  __syncthreads();
+  __shared__ int ok_s;
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned int* vgen = gen;
+    const unsigned int g = *vgen;
+    __threadfence();
+    if (atomicAdd(count, 1u) == nblocks - 1) {
+      atomicExch(count, 0u);
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      const uint64_t t0 = globaltimer_ns();
+      while (*vgen == g) {
+        if (globaltimer_ns() - t0 > KOP_WAIT_LIMIT_NS) {
+          ok = 0;
+          atomicExch(status, KOP_DEV_TIMEOUT);
+          break;
+        }
+      }
+    }
+    __threadfence();
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+__global__ void __launch_bounds__(256) jacobi_kernel(JacobiArgs a) {
+  extern __shared__ double js[];
+  double* ca = js;            // re: a_i
+  double* cb = js + a.re;     // re: b_i
+  int* partner = (int*)(js + 2 * a.re);
+  __shared__ double red[2][8];
+  const int re = a.re;
+  const unsigned int nblocks = gridDim.x;
+  const int64_t tot = (int64_t)re * re;
+  double* A = a.A;
+  double* B = a.B;
+  double* V = a.V;
+  double* V2 = a.V2;
+  int sweep = 0;
+  for (; sweep < a.max_sweeps; ++sweep) {
+    for (int step = 0; step < re - 1; ++step) {
+      // every CTA computes all rotations of this step from the current A
+      for (int pos = threadIdx.x; pos < re / 2; pos += blockDim.x) {
+        int p = rr_index(pos, step, re), q = rr_index(rr_partner_pos(pos, re), step, re);
+        if (p > q) {
+          const int t = p;
+          p = q;
+          q = t;
+        }
+        const double app = __ldcg(&A[(int64_t)p * re + p]);
+        const double aqq = __ldcg(&A[(int64_t)q * re + q]);
+        const double apq = __ldcg(&A[(int64_t)p * re + q]);
+        double c = 1.0, s = 0.0;
+        if (apq != 0.0 && fabs(apq) > 1e-300) {
+          const double tau = (aqq - app) / (2.0 * apq);
+          double t;
+          if (fabs(tau) > 1e150)
+            t = 0.5 / tau;
+          else
+            t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          c = 1.0 / sqrt(1.0 + t * t);
+          s = t * c;
+        }
+        ca[p] = c;
+        cb[p] = -s;
+        partner[p] = q;
+        ca[q] = c;
+        cb[q] = s;
+        partner[q] = p;
+      }
+      __syncthreads();
+      const bool last = step == re - 2;
+      double off = 0.0, dia = 0.0;
+      for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)nblocks * blockDim.x) {
+        const int i = (int)(t / re), j = (int)(t - (int64_t)i * re);
+        const int pi = partner[i], pj = partner[j];
+        const double ai = ca[i], bi = cb[i], aj = ca[j], bj = cb[j];
+        double v = ai * aj * __ldcg(&A[t]) + ai * bj * __ldcg(&A[(int64_t)i * re + pj]) +
+                   bi * aj * __ldcg(&A[(int64_t)pi * re + j]) + bi * bj * __ldcg(&A[(int64_t)pi * re + pj]);
+        if (j == pi) v = 0.0;  // the rotated pair's off-diagonal entry is zero by construction
+        B[t] = v;
+        V2[t] = aj * __ldcg(&V[t]) + bj * __ldcg(&V[(int64_t)i * re + pj]);
+        if (last) {
+          if (i == j)
+            dia += v * v;
+          else
+            off += v * v;
+        }
+      }
+      if (last) {
+        for (int o = 16; o > 0; o >>= 1) {
+          off += __shfl_xor_sync(0xffffffffu, off, o);
+          dia += __shfl_xor_sync(0xffffffffu, dia, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+          red[0][threadIdx.x >> 5] = off;
+          red[1][threadIdx.x >> 5] = dia;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          double so = 0.0, sd = 0.0;
+          for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            so += red[0][w];
+            sd += red[1][w];
+          }
+          atomicAdd(&a.offsum[2 * sweep], so);
+          atomicAdd(&a.offsum[2 * sweep + 1], sd);
+        }
+      }
+      double* tA = A;
+      A = B;
+      B = tA;
+      double* tV = V;
+      V = V2;
+      V2 = tV;
+      if (!grid_barrier(a.bar_count, a.bar_gen, nblocks, a.status)) return;
+    }
+    const double so = __ldcg(&a.offsum[2 * sweep]), sd = __ldcg(&a.offsum[2 * sweep + 1]);
+    if (so <= a.tol * a.tol * sd) {
+      ++sweep;
+      break;
+    }
+  }
+  // results must end in a.A / a.V: copy if the last step left them in the other buffers
+  if (A != a.A) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)nblocks * blockDim.x) {
+      a.A[t] = __ldcg(&A[t]);
+      a.V[t] = __ldcg(&V[t]);
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *a.sweeps_done = sweep;
+}
+
+// Copy r x r into the padded re x re buffer, identity into V.
+__global__ void jacobi_init_kernel(const double* __restrict__ H, int r, int re, double* A, double* V) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)re * re) return;
+  const int i = (int)(t / re), j = (int)(t - (int64_t)i * re);
+  A[t] = (i < r && j < r) ? H[(int64_t)i * r + j] : 0.0;
+  V[t] = i == j ? 1.0 : 0.0;
+}
+
+int sym_eig(const double* H, int r, double* work, int* status, double* evals_out, double* evecs_out,
+            cudaStream_t st) {
+  // work layout: A, B, V, V2 (re^2 each) + offsum (2 * 64) + barrier words + sweeps
+  const int re = r + (r & 1);
+  const size_t rr = (size_t)re * re;
+  double* A = work;
+  double* B = A + rr;
+  double* V = B + rr;
+  double* V2 = V + rr;
+  double* offsum = V2 + rr;
+  unsigned int* bar = (unsigned int*)(offsum + 128);
+  int* sweeps = (int*)(bar + 2);
+  KOP_CUDA_TRY(cudaMemsetAsync(offsum, 0, sizeof(double) * 128 + 16, st));
+  jacobi_init_kernel<<<(unsigned)((rr + 255) / 256), 256, 0, st>>>(H, r, re, A, V);
+  KOP_LAUNCHED();
+  JacobiArgs a;
+  a.A = A;
+  a.B = B;
+  a.V = V;
+  a.V2 = V2;
+  a.re = re;
+  a.max_sweeps = 40;
+  a.tol = 1e-13;
+  a.offsum = offsum;
+  a.bar_count = bar;
+  a.bar_gen = bar + 1;
+  a.status = status;
+  a.sweeps_done = sweeps;
+  const size_t smem = sizeof(double) * 2 * re + sizeof(int) * re;
+  if (smem > 48 * 1024)
+    KOP_CUDA_TRY(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  KOP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, 256, smem));
+  if (per_sm < 1) return fail(KOP_ECUDA, "jacobi: kernel does not fit on an SM");
+  int blocks = num_sms() * (per_sm < 2 ? per_sm : 2);
+  const int64_t want = (int64_t)((rr + 255) / 256);
+  if (want < blocks) blocks = (int)want;
+  if (blocks < 1) blocks = 1;
+  void* args[] = {&a};
+  KOP_CUDA_TRY(cudaLaunchCooperativeKernel((void*)jacobi_kernel, dim3(blocks), dim3(256), args, smem, st));
+  note_launch();
+  // unpad: eigenvalues = diag(A)[0..r), eigenvectors = V[0..r, 0..r)
+  extract_eig(A, V, r, re, evals_out, evecs_out, st);
+  return KOP_OK;
+}
+
+__global__ void extract_kernel(const double* __restrict__ A, const double* __restrict__ V, int r, int re,
+                               double* __restrict__ w, double* __restrict__ E) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < r) w[t] = A[t * re + t];
+  if (t < (int64_t)r * r) {
+    const int i = (int)(t / r), j = (int)(t - (int64_t)i * r);
+    E[t] = V[(int64_t)i * re + j];
+  }
+}
+
+void extract_eig(const double* A, const double* V, int r, int re, double* w, double* E, cudaStream_t st) {
+  const int64_t tot = (int64_t)r * r;
+  extract_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(A, V, r, re, w, E);
+  note_launch();
+}
+
+// Descending order: perm[k] = index of the k-th largest eigenvalue (ties by index).
+__global__ void sort_desc_kernel(const double* __restrict__ w, int r, int* __restrict__ perm) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < r; i += gridDim.x * blockDim.x) {
+    const double wi = w[i];
+    int rank = 0;
+    for (int j = 0; j < r; ++j) {
+      const double wj = w[j];
+      rank += (wj > wi) || (wj == wi && j < i);
+    }
+    perm[rank] = i;
+  }
+}
+
+int sort_desc(const double* w, int r, int* perm, cudaStream_t st) {
+  sort_desc_kernel<<<(r + 255) / 256, 256, 0, st>>>(w, r, perm);
+  KOP_LAUNCHED();
+  return KOP_OK;
+}
+
+// After sorting: lam[k] = max(0, w[perm[k]] - nu); Wm[:, k] = E[:, perm[k]] / sqrt(w[perm[k]]).
+__global__ void nys_finish_kernel(const double* __restrict__ w, const double* __restrict__ E, const int* __restrict__ perm,
+                                  int r, double nu, double* __restrict__ lam, double* __restrict__ Wm) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)r * r) return;
+  const int i = (int)(t / r), k = (int)(t - (int64_t)i * r);
+  const int src = perm[k];
+  const double wk = w[src];
+  const double sig = sqrt(wk > 1e-300 ? wk : 1e-300);
+  Wm[t] = E[(int64_t)i * r + src] / sig;
+  if (i == 0) lam[k] = wk - nu > 0.0 ? wk - nu : 0.0;
+}
+
+int nys_finish(const double* w, const double* E, const int* perm, int r, double nu, double* lam, double* Wm,
+               cudaStream_t st) {
+  const int64_t tot = (int64_t)r * r;
+  nys_finish_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(w, E, perm, r, nu, lam, Wm);
+  KOP_LAUNCHED();
+  return KOP_OK;
+}
+
+__global__ void d2f_kernel(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) b[t] = (float)a[t];
+}
+
+int d2f(const double* a, float* b, int64_t n, cudaStream_t st) {
+  d2f_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, b, n);
+  KOP_LAUNCHED();
+  return KOP_OK;
+}
+
+// Identity into an r x r FP64 matrix.
+__global__ void eye_kernel(double* M, int r) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < (int64_t)r * r) M[t] = (t / r == t % r) ? 1.0 : 0.0;
+}
+
+int eye(double* M, int r, cudaStream_t st) {
+  const int64_t tot = (int64_t)r * r;
+  eye_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(M, r);
+  KOP_LAUNCHED();
+  return KOP_OK;
+}
+
+}  // namespace kop

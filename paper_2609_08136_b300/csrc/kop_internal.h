@@ -1,0 +1,105 @@
+// Host-side internals shared by the library's translation units.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/kop.h"
+
+namespace kop {
+
+// Kernel-function ids used by the device epilogues.  0..2 are k itself
+// (enum kop_kernel), 3..5 its derivative with respect to the bandwidth.
+enum { KF_RBF = 0, KF_LAPLACE = 1, KF_MATERN = 2, KF_DRBF = 3, KF_DLAPLACE = 4, KF_DMATERN = 5 };
+
+struct KConst {
+  float c0, c1, c2;  // fused-epilogue constants (exp2 form)
+  double bw;         // bandwidth itself
+};
+KConst kernel_constants(int kind, double bw);
+
+// A prepared point set: centred FP32 copy, FP32 row norms and the BF16
+// hi/mid/lo split, rows padded to a multiple of 128 and columns to dp.
+struct PointSet {
+  int64_t n = 0, n_pad = 0;
+  int d = 0, dp = 0;
+  float* xc = nullptr;     // n_pad x dp
+  float* norms = nullptr;  // n_pad
+  __nv_bfloat16* sp[3] = {nullptr, nullptr, nullptr};
+  CUtensorMap tm[3][2];  // [split][0: 128-row boxes, 1: 64-row boxes]
+  void* block = nullptr;
+};
+
+int padded_dim(int d);
+int pointset_alloc(PointSet& ps, int64_t n, int d, cudaStream_t st);
+void pointset_free(PointSet& ps, cudaStream_t st);
+// Centre X with `mean` (device, d doubles), write xc, norms and the split.
+int pointset_fill(PointSet& ps, const float* X, const double* mean, cudaStream_t st);
+// Column mean of X (n x d) in FP64 into mean (device, d).
+int column_mean(const float* X, int64_t n, int d, double* mean, cudaStream_t st);
+
+// Fused operator: O (nq x m, ld ldo) = f(K(Q, Kset)) V (nk x m, ld ldv).
+// nsplit: 2 (KOP_FAST) or 3 (KOP_ACCURATE).  self: Q and Kset are the same
+// points, so the diagonal distance is set to exactly 0.
+int fused_matvec(const PointSet& Q, const PointSet& Ks, bool self, int kf, const KConst& kc, int nsplit,
+                 const float* V, int m, int ldv, float* O, int ldo, int* status, cudaStream_t st);
+// Tensor-core contraction variant for m > 8 (2-term split only).
+int fused_matvec_mma(const PointSet& Q, const PointSet& Ks, bool self, int kf, const KConst& kc, const float* V,
+                     int m, int ldv, float* O, int ldo, int* status, cudaStream_t st);
+// Plain FP32 CUDA-core operator (same contract, no tensor cores).
+int plain_matvec(const PointSet& Q, const PointSet& Ks, bool self, int kf, const KConst& kc, const float* V,
+                 int m, int ldv, float* O, int ldo, cudaStream_t st);
+
+// Any mode.
+int op_matvec(const PointSet& Q, const PointSet& Ks, bool self, int kf, const KConst& kc, int mode,
+              const float* V, int m, int ldv, float* O, int ldo, int* status, cudaStream_t st);
+
+int num_sms();
+inline size_t smem_limit_bytes() { return 227u * 1024u; }
+int encode_tmap_bf16(CUtensorMap* map, const void* base, int64_t rows, int cols, int box_cols, int box_rows);
+
+// Error reporting: set the thread-local message and return the code.
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* where);
+// Count one kernel launch and report a launch error.
+void note_launch();
+#define KOP_LAUNCHED()                      \
+  do {                                      \
+    ::kop::note_launch();                   \
+    KOP_CUDA_TRY(cudaGetLastError());       \
+  } while (0)
+#define KOP_CUDA_TRY(expr)                                  \
+  do {                                                      \
+    cudaError_t _e = (expr);                                \
+    if (_e != cudaSuccess) return ::kop::cuda_fail(_e, #expr); \
+  } while (0)
+
+}  // namespace kop
+
+namespace kop {
+// Device part of nys_apply (scratch from the caller; see kop_nystrom.cu).
+int nys_apply_dev(const nys_s* ny, const double* mu_dev, int adaptive, const float* V, int m, float* O, double* Wd,
+                  float* Wf, float* alpha, cudaStream_t st);
+}  // namespace kop
+
+struct kop_s {
+  kop::PointSet pts;
+  int kernel = 0;
+  double bw = 1.0;
+  double* mean = nullptr;  // device, d
+  int* status = nullptr;   // device status word
+};
+
+struct nys_s {
+  kop_s* op = nullptr;
+  int r = 0;
+  int64_t n = 0;
+  float* U = nullptr;            // device, n_pad x r
+  double* lam_dev = nullptr;     // device, r (descending)
+  double* lam_host = nullptr;    // host copy
+  double nu = 0.0;
+};

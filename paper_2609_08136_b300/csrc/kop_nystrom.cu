@@ -1,0 +1,254 @@
+// Randomized Nystrom preconditioner: nys_build / nys_apply / nys_eigs /
+// nys_factor / nys_destroy.
+//
+// The approximation is the one of Frangella, Tropp & Udell (the paper's
+// randomized Nystrom preconditioner, Sec. 1 and Sec. 2.3; configuration in
+// App. A.5):  Y = K Omega, a shift nu, Y_nu = Y + nu Omega,
+// C = chol(Omega^T Y_nu), B = Y_nu C^-1 = U S V^T, lam_hat = max(0, S^2 - nu).
+// Here B is never formed: its thin SVD comes from the r x r matrix
+//   B^T B = C^-T (Y_nu^T Y_nu) C^-1 = V S^2 V^T
+// (Y_nu^T Y_nu = Y^T Y + nu (Omega^T Y + Y^T Omega) + nu^2 Omega^T Omega, so
+// only three r x r Gram blocks are needed), then U = Y_nu C^-1 V S^-1 is one
+// tall product.  All r x r work is FP64 on the device; the O(n r^2) Gram and
+// product passes read FP32 and accumulate in FP64 / FP32.  One Cholesky-QR
+// pass afterwards restores the orthonormality of U lost to FP32 rounding.
+#include <cmath>
+#include <vector>
+
+#include "kop_dense.h"
+#include "kop_device.cuh"
+#include "kop_internal.h"
+
+namespace kop {
+
+struct DevBuf {
+  void* p = nullptr;
+  cudaStream_t st = 0;
+  ~DevBuf() {
+    if (p) cudaFreeAsync(p, st);
+  }
+};
+
+// Per-column damping of the preconditioner apply.
+//   d_k(c) = 1 / (lam_k + mu_c) - 1 / rho_c,   alpha_c = 1 / rho_c,
+//   rho_c = lam_r + mu_c (adaptive) or mu_c.
+__global__ void nys_scale_kernel(const double* __restrict__ W, int r, int m, const double* __restrict__ lam,
+                                 const double* __restrict__ mu, int adaptive, float* __restrict__ Wf,
+                                 float* __restrict__ alpha) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)r * m) return;
+  const int k = (int)(t / m), c = (int)(t - (int64_t)k * m);
+  const double rho = adaptive ? lam[r - 1] + mu[c] : mu[c];
+  Wf[t] = (float)(W[t] * (1.0 / (lam[k] + mu[c]) - 1.0 / rho));
+  if (k == 0) alpha[c] = (float)(1.0 / rho);
+}
+
+// Device side of nys_apply with caller-provided scratch:
+//   Wd: r*m doubles, Wf: r*m floats, alpha: m floats, mu_dev: m doubles.
+int nys_apply_dev(const nys_s* ny, const double* mu_dev, int adaptive, const float* V, int m, float* O, double* Wd,
+                  float* Wf, float* alpha, cudaStream_t st) {
+  const int r = ny->r;
+  const int64_t n = ny->n;
+  if (m == 1) {
+    int rc = utv(ny->U, r, n, r, V, 1, Wd, st);
+    if (rc) return rc;
+  } else {
+    int rc = gram(ny->U, r, V, m, n, r, m, Wd, m, st);
+    if (rc) return rc;
+  }
+  const int64_t tot = (int64_t)r * m;
+  nys_scale_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(Wd, r, m, ny->lam_dev, mu_dev, adaptive, Wf, alpha);
+  KOP_LAUNCHED();
+  if (m == 1) return uw(ny->U, r, n, r, Wf, V, 1, alpha, O, 1, st);
+  return tall_gemm(ny->U, nullptr, 0.0f, r, n, r, Wf, m, m, V, m, alpha, O, m, st);
+}
+
+static int read_info(const int* dev, int* host, cudaStream_t st) {
+  KOP_CUDA_TRY(cudaMemcpyAsync(host, dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+  KOP_CUDA_TRY(cudaStreamSynchronize(st));
+  return KOP_OK;
+}
+
+}  // namespace kop
+
+using namespace kop;
+
+extern "C" int nys_build(kop_t op, const float* Omega, int32_t r, double nu_rel, int32_t mode, void* stream,
+                         nys_t* out) {
+  if (!out) return fail(KOP_EINVAL, "nys_build: out is NULL");
+  *out = nullptr;
+  if (!op || !Omega) return fail(KOP_EINVAL, "nys_build: NULL argument");
+  const int64_t n = op->pts.n;
+  if (r < 1 || r > 2048 || r > n) return fail(KOP_EINVAL, "nys_build: r must be in [1, min(n, 2048)]");
+  if (mode != KOP_FAST && mode != KOP_ACCURATE && mode != KOP_PLAIN) return fail(KOP_EINVAL, "nys_build: bad mode");
+  if (!std::isfinite(nu_rel)) return fail(KOP_EINVAL, "nys_build: nu_rel must be finite");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!(nu_rel > 0.0)) nu_rel = mode == KOP_FAST ? std::ldexp(1.0, -16) : std::ldexp(1.0, -21);
+
+  const size_t rr = (size_t)r * r;
+  const int64_t n_pad = op->pts.n_pad;
+  // workspace
+  DevBuf wsY, wsR, wsU;
+  wsY.st = wsR.st = wsU.st = st;
+  KOP_CUDA_TRY(cudaMallocAsync(&wsY.p, sizeof(float) * (size_t)n * r, st));
+  const size_t nd = 9 * rr + 4 * (size_t)r + 16 + sym_eig_work_doubles(r);
+  KOP_CUDA_TRY(cudaMallocAsync(&wsR.p, sizeof(double) * nd + sizeof(float) * rr + sizeof(int) * (r + 8), st));
+  KOP_CUDA_TRY(cudaMallocAsync(&wsU.p, sizeof(float) * (size_t)n_pad * r, st));
+  float* Y = (float*)wsY.p;
+  float* U2 = (float*)wsU.p;
+  double* Goo = (double*)wsR.p;
+  double* Goy = Goo + rr;
+  double* Gyy = Goy + rr;
+  double* M = Gyy + rr;   // becomes L
+  double* G2 = M + rr;
+  double* Z = G2 + rr;
+  double* H = Z + rr;
+  double* E = H + rr;
+  double* Wm = E + rr;
+  double* w = Wm + rr;
+  double* lam = w + r;
+  double* scal = lam + r;  // 16
+  double* jw = scal + 16;
+  float* Wf = (float*)(jw + sym_eig_work_doubles(r));
+  int* perm = (int*)(Wf + rr);
+  int* info = perm + r;
+
+  int rc;
+  // 1. sketch Y = K Omega (fused operator, m = r)
+  const KConst kc = kernel_constants(op->kernel, op->bw);
+  rc = op_matvec(op->pts, op->pts, true, op->kernel, kc, mode, Omega, r, r, Y, r, op->status, st);
+  if (rc) return rc;
+  // 2. Gram blocks
+  if ((rc = gram(Omega, r, Omega, r, n, r, r, Goo, r, st))) return rc;
+  if ((rc = gram(Omega, r, Y, r, n, r, r, Goy, r, st))) return rc;
+  if ((rc = gram(Y, r, Y, r, n, r, r, Gyy, r, st))) return rc;
+  // 3. ||Y||_2 by power iteration on Y^T Y
+  if ((rc = power_max_eig(Gyy, r, 60, scal, st))) return rc;
+  double ymax2 = 0.0;
+  KOP_CUDA_TRY(cudaMemcpyAsync(&ymax2, scal, sizeof(double), cudaMemcpyDeviceToHost, st));
+  KOP_CUDA_TRY(cudaStreamSynchronize(st));
+  {
+    const int s = kop_sync(op, stream);
+    if (s != KOP_OK) return s;
+  }
+  if (!std::isfinite(ymax2) || !(ymax2 > 0.0)) return fail(KOP_ENOTPD, "nys_build: sketch is zero or not finite");
+  double nu = nu_rel * std::sqrt(ymax2);
+  // 4. C = chol(sym(Omega^T Y_nu)); grow nu on a failed pivot
+  int attempt = 0, hinfo = 1;
+  for (; attempt < 4; ++attempt) {
+    if ((rc = combine(Goo, Goy, Gyy, r, nu, 0, M, st))) return rc;
+    if ((rc = cholesky(M, r, info, st))) return rc;
+    if ((rc = read_info(info, &hinfo, st))) return rc;
+    if (hinfo == 0) break;
+    nu *= 10.0;
+  }
+  if (hinfo != 0) return fail(KOP_ENOTPD, "nys_build: Cholesky of Omega^T Y_nu failed after growing the shift");
+  // 5. Y_nu^T Y_nu
+  if ((rc = combine(Goo, Goy, Gyy, r, nu, 1, G2, st))) return rc;
+  // 6. H = L^-1 G2 L^-T  (C = L^T)
+  if ((rc = trsm(M, r, G2, r, r, 0, st))) return rc;          // G2 <- L^-1 G2
+  if ((rc = transpose(G2, r, Z, 0, st))) return rc;           // Z = (L^-1 G2)^T
+  if ((rc = trsm(M, r, Z, r, r, 0, st))) return rc;           // Z <- L^-1 Z
+  if ((rc = transpose(Z, r, H, 1, st))) return rc;            // H = sym(Z)
+  // 7. H = E diag(w) E^T
+  KOP_CUDA_TRY(cudaMemsetAsync(op->status, 0, sizeof(int), st));
+  if ((rc = sym_eig(H, r, jw, op->status, w, E, st))) return rc;
+  // 8. descending order, lam_hat, Wm = E_sorted diag(w)^-1/2
+  if ((rc = sort_desc(w, r, perm, st))) return rc;
+  if ((rc = nys_finish(w, E, perm, r, nu, lam, Wm, st))) return rc;
+  // 9. W = C^-1 Wm = L^-T Wm
+  if ((rc = trsm(M, r, Wm, r, r, 1, st))) return rc;
+  if ((rc = d2f(Wm, Wf, (int64_t)rr, st))) return rc;
+  // 10. U = (Y + nu Omega) W   (rows beyond n stay zero)
+  nys_s* ny = new nys_s();
+  ny->op = op;
+  ny->r = r;
+  ny->n = n;
+  ny->nu = nu;
+  cudaError_t e = cudaMalloc(&ny->U, sizeof(float) * (size_t)n_pad * r);
+  if (e == cudaSuccess) e = cudaMalloc(&ny->lam_dev, sizeof(double) * r);
+  if (e != cudaSuccess) {
+    if (ny->U) cudaFree(ny->U);
+    delete ny;
+    return cuda_fail(e, "nys_build: cudaMalloc");
+  }
+  ny->lam_host = new double[r];
+  auto drop = [&](int code) {
+    cudaStreamSynchronize(st);
+    cudaFree(ny->U);
+    cudaFree(ny->lam_dev);
+    delete[] ny->lam_host;
+    delete ny;
+    return code;
+  };
+  KOP_CUDA_TRY(cudaMemsetAsync(U2, 0, sizeof(float) * (size_t)n_pad * r, st));
+  if ((rc = tall_gemm(Y, Omega, (float)nu, r, n, r, Wf, r, r, nullptr, 0, nullptr, U2, r, st))) return drop(rc);
+  // 11. Cholesky-QR: U <- U2 Lu^-T with Lu Lu^T = U2^T U2
+  if ((rc = gram(U2, r, U2, r, n, r, r, Goo, r, st))) return drop(rc);
+  if ((rc = cholesky(Goo, r, info, st))) return drop(rc);
+  if ((rc = read_info(info, &hinfo, st))) return drop(rc);
+  if (hinfo != 0) return drop(fail(KOP_ENOTPD, "nys_build: U lost rank (Cholesky-QR failed)"));
+  if ((rc = eye(Z, r, st))) return drop(rc);
+  if ((rc = trsm(Goo, r, Z, r, r, 1, st))) return drop(rc);   // Z = Lu^-T
+  if ((rc = d2f(Z, Wf, (int64_t)rr, st))) return drop(rc);
+  if (cudaMemsetAsync(ny->U, 0, sizeof(float) * (size_t)n_pad * r, st) != cudaSuccess) return drop(KOP_ECUDA);
+  if ((rc = tall_gemm(U2, nullptr, 0.0f, r, n, r, Wf, r, r, nullptr, 0, nullptr, ny->U, r, st))) return drop(rc);
+  if (cudaMemcpyAsync(ny->lam_dev, lam, sizeof(double) * r, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(ny->lam_host, lam, sizeof(double) * r, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return drop(KOP_ECUDA);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return drop(cuda_fail(cudaGetLastError(), "nys_build"));
+  {
+    const int s = kop_sync(op, stream);
+    if (s != KOP_OK) return drop(s);
+  }
+  *out = ny;
+  return KOP_OK;
+}
+
+extern "C" int nys_destroy(nys_t ny) {
+  if (!ny) return KOP_OK;
+  cudaDeviceSynchronize();
+  cudaFree(ny->U);
+  cudaFree(ny->lam_dev);
+  delete[] ny->lam_host;
+  delete ny;
+  return KOP_OK;
+}
+
+extern "C" int nys_eigs(nys_t ny, double* lam_hat, double* nu, int32_t* r) {
+  if (!ny) return fail(KOP_EINVAL, "nys_eigs: NULL handle");
+  if (lam_hat)
+    for (int k = 0; k < ny->r; ++k) lam_hat[k] = ny->lam_host[k];
+  if (nu) *nu = ny->nu;
+  if (r) *r = ny->r;
+  return KOP_OK;
+}
+
+extern "C" int nys_factor(nys_t ny, float* U_out, void* stream) {
+  if (!ny || !U_out) return fail(KOP_EINVAL, "nys_factor: NULL argument");
+  KOP_CUDA_TRY(cudaMemcpyAsync(U_out, ny->U, sizeof(float) * (size_t)ny->n * ny->r, cudaMemcpyDeviceToDevice,
+                               (cudaStream_t)stream));
+  return KOP_OK;
+}
+
+extern "C" int nys_apply(nys_t ny, const double* mu, int32_t adaptive, const float* V, int32_t m, float* O,
+                         void* stream) {
+  if (!ny || !mu || !V || !O) return fail(KOP_EINVAL, "nys_apply: NULL argument");
+  if (m < 1) return fail(KOP_EINVAL, "nys_apply: m must be >= 1");
+  for (int c = 0; c < m; ++c)
+    if (!(mu[c] >= 0.0) || !std::isfinite(mu[c]) || (!adaptive && !(mu[c] > 0.0)))
+      return fail(KOP_EINVAL, "nys_apply: mu must be finite, >= 0 (and > 0 when non-adaptive)");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t r = ny->r;
+  DevBuf ws;
+  ws.st = st;
+  KOP_CUDA_TRY(cudaMallocAsync(&ws.p, sizeof(double) * (r * m + m) + sizeof(float) * (r * m + m), st));
+  double* Wd = (double*)ws.p;
+  double* mu_dev = Wd + r * m;
+  float* Wf = (float*)(mu_dev + m);
+  float* alpha = Wf + r * m;
+  KOP_CUDA_TRY(cudaMemcpyAsync(mu_dev, mu, sizeof(double) * m, cudaMemcpyHostToDevice, st));
+  const int rc = nys_apply_dev(ny, mu_dev, adaptive, V, m, O, Wd, Wf, alpha, st);
+  KOP_CUDA_TRY(cudaStreamSynchronize(st));
+  return rc;
+}

@@ -1,0 +1,457 @@
+// Preconditioned CG over a block of independent columns: pcg_solve and
+// pcg_adjoint.
+//
+// PCG as in Hestenes & Stiefel (cited in the paper's Sec. 5.1), started from
+// x0 = 0:  r = b, z = P^-1 r, p = z;  per iteration
+//   q = (K + lam I) p,  alpha = r^T z / p^T q,  x += alpha p,  r -= alpha q,
+//   stop if ||r|| <= tol ||b||,  z = P^-1 r,  beta = r^T z_new / r^T z_old,
+//   p = z + beta p.
+// Every column has its own alpha and beta and stops on its own (App. A.1: the
+// stopping condition must hold for every right-hand side).  The products with
+// K use the fast operator; every `refine_every` iterations, and whenever a
+// column's recursive residual meets the tolerance, the true residual
+// b - (K + lam I) x is recomputed with the accurate operator and replaces the
+// recursive one (iterative refinement), and a column stops only when the true
+// residual meets the tolerance too.  Vector updates run in fused passes over
+// the n x cols block with FP64 per-column reductions; the scalars alpha and
+// beta never leave the device.
+#include <cmath>
+#include <vector>
+
+#include "kop_dense.h"
+#include "kop_device.cuh"
+#include "kop_internal.h"
+
+namespace kop {
+
+enum { OP_INIT = 0, OP_PQ = 1, OP_XR = 2, OP_DOT = 3, OP_P = 4, OP_RES = 5 };
+
+struct VecArgs {
+  int64_t n;
+  int cols, nrhs;
+  float* X;
+  float* R;
+  const float* Z;
+  float* P;
+  float* Q;
+  const float* B;  // n x nrhs; column c reads B[:, c % nrhs]
+  const float* T;  // K x (for OP_RES)
+  const double* lam;
+  const double* alpha;
+  const double* beta;
+  double* acc;  // per column, pre-zeroed
+};
+
+template <int OP>
+KOP_DEV double vec_elem(const VecArgs& a, int64_t i, int c) {
+  const int64_t e = i * a.cols + c;
+  if constexpr (OP == OP_INIT) {
+    const float b = a.B[i * a.nrhs + (c % a.nrhs)];
+    a.X[e] = 0.0f;
+    a.R[e] = b;
+    return (double)b * b;
+  } else if constexpr (OP == OP_PQ) {
+    const float p = a.P[e];
+    const float q = (float)((double)a.Q[e] + a.lam[c] * (double)p);
+    a.Q[e] = q;
+    return (double)p * q;
+  } else if constexpr (OP == OP_XR) {
+    const double al = a.alpha[c];
+    a.X[e] = (float)((double)a.X[e] + al * (double)a.P[e]);
+    const float r = (float)((double)a.R[e] - al * (double)a.Q[e]);
+    a.R[e] = r;
+    return (double)r * r;
+  } else if constexpr (OP == OP_DOT) {
+    return (double)a.R[e] * (double)a.Z[e];
+  } else if constexpr (OP == OP_P) {
+    a.P[e] = (float)((double)a.Z[e] + a.beta[c] * (double)a.P[e]);
+    return 0.0;
+  } else {
+    const double r = (double)a.B[i * a.nrhs + (c % a.nrhs)] - (double)a.T[e] - a.lam[c] * (double)a.X[e];
+    const float rf = (float)r;
+    a.R[e] = rf;
+    return r * r;
+  }
+}
+
+// Several columns: 32 columns x 8 rows per block, row-strided.
+template <int OP>
+__global__ void __launch_bounds__(256) vec_cols_kernel(VecArgs a) {
+  const int c = blockIdx.y * 32 + threadIdx.x;
+  double acc = 0.0;
+  if (c < a.cols)
+    for (int64_t i = (int64_t)blockIdx.x * 8 + threadIdx.y; i < a.n; i += (int64_t)gridDim.x * 8)
+      acc += vec_elem<OP>(a, i, c);
+  if (OP == OP_P) return;
+  __shared__ double red[8][33];
+  red[threadIdx.y][threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.y == 0 && c < a.cols) {
+    double s = 0.0;
+    for (int y = 0; y < 8; ++y) s += red[y][threadIdx.x];
+    atomicAdd(&a.acc[c], s);
+  }
+}
+
+// One column: flat grid-stride with a block reduction.
+template <int OP>
+__global__ void __launch_bounds__(256) vec_one_kernel(VecArgs a) {
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x)
+    acc += vec_elem<OP>(a, i, 0);
+  if (OP == OP_P) return;
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  __shared__ double red[8];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += red[w];
+    atomicAdd(&a.acc[0], s);
+  }
+}
+
+template <int OP>
+static int vec_launch(const VecArgs& a, cudaStream_t st) {
+  if (OP != OP_P) KOP_CUDA_TRY(cudaMemsetAsync(a.acc, 0, sizeof(double) * a.cols, st));
+  if (a.cols == 1) {
+    int64_t blocks = (a.n + 255) / 256;
+    const int64_t cap = 8 * num_sms();
+    if (blocks > cap) blocks = cap;
+    vec_one_kernel<OP><<<(unsigned)blocks, 256, 0, st>>>(a);
+  } else {
+    const unsigned gy = (unsigned)((a.cols + 31) / 32);
+    int64_t gx = (a.n + 7) / 8;
+    const int64_t cap = (8 * num_sms() + gy - 1) / gy;
+    if (gx > cap) gx = cap;
+    vec_cols_kernel<OP><<<dim3((unsigned)gx, gy), dim3(32, 8), 0, st>>>(a);
+  }
+  KOP_LAUNCHED();
+  return KOP_OK;
+}
+
+// alpha_c = rz_c / pq_c for active columns (0 otherwise); p^T q <= 0 on an
+// active column is a breakdown.
+__global__ void fin_alpha_kernel(int cols, const double* rz, const double* pq, const int* active, double* alpha,
+                                 int* status) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  double al = 0.0;
+  if (active[c]) {
+    if (pq[c] > 0.0 && isfinite(pq[c]))
+      al = rz[c] / pq[c];
+    else
+      atomicExch(status, KOP_DEV_BREAKDOWN);
+  }
+  alpha[c] = al;
+}
+
+// beta_c = rz_new_c / rz_c, rz_c <- rz_new_c.
+__global__ void fin_beta_kernel(int cols, double* rz, const double* rzn, double* beta) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  beta[c] = rz[c] != 0.0 ? rzn[c] / rz[c] : 0.0;
+  rz[c] = rzn[c];
+}
+
+__global__ void dot_kernel(const float* a, const float* b, int64_t n, double* out) {
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc += (double)a[i] * (double)b[i];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  __shared__ double red[8];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += red[w];
+    atomicAdd(out, s);
+  }
+}
+
+struct PcgProblem {
+  kop_s* op = nullptr;
+  nys_s* ny = nullptr;
+  int cols = 1, nrhs = 1;
+  std::vector<double> lam, mu;
+  int adaptive = 1;
+  const float* B = nullptr;
+  float* Xout = nullptr;
+  double tol = 1e-6;
+  int maxit = 1000, refine_every = 0, inner_mode = KOP_FAST, refine_mode = KOP_ACCURATE;
+  int32_t* iters = nullptr;
+  double* res_hist = nullptr;
+  double* true_relres = nullptr;
+};
+
+struct Workspace {
+  void* p = nullptr;
+  cudaStream_t st = 0;
+  ~Workspace() {
+    if (p) cudaFreeAsync(p, st);
+  }
+};
+
+static int device_status(kop_s* op, cudaStream_t st, int* h) {
+  KOP_CUDA_TRY(cudaMemcpyAsync(h, op->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  KOP_CUDA_TRY(cudaStreamSynchronize(st));
+  return KOP_OK;
+}
+
+int pcg_core(PcgProblem& pb, cudaStream_t st) {
+  kop_s* op = pb.op;
+  const int64_t n = op->pts.n;
+  const int cols = pb.cols;
+  const size_t nc = (size_t)n * cols;
+  const int r = pb.ny ? pb.ny->r : 0;
+  Workspace ws;
+  ws.st = st;
+  const size_t fbytes = sizeof(float) * (5 * nc + (size_t)r * cols + cols);
+  const size_t dbytes = sizeof(double) * (9 * (size_t)cols + (size_t)r * cols);
+  const size_t ibytes = sizeof(int) * (size_t)cols;
+  KOP_CUDA_TRY(cudaMallocAsync(&ws.p, dbytes + fbytes + ibytes + 256, st));
+  double* lam = (double*)ws.p;
+  double* mu = lam + cols;
+  double* alpha = mu + cols;
+  double* beta = alpha + cols;
+  double* rz = beta + cols;
+  double* acc = rz + cols;
+  double* acc2 = acc + cols;
+  double* spare = acc2 + cols;
+  double* spare2 = spare + cols;
+  double* Wd = spare2 + cols;
+  float* R = (float*)(Wd + (size_t)r * cols);
+  float* Z = R + nc;
+  float* P = Z + nc;
+  float* Q = P + nc;
+  float* T = Q + nc;
+  float* Wf = T + nc;
+  float* acol = Wf + (size_t)r * cols;
+  int* active = (int*)(acol + cols);
+  float* X = pb.Xout;
+
+  std::vector<int> act(cols, 1);
+  std::vector<double> hb(cols), nb(cols), rel(cols, 0.0);
+  KOP_CUDA_TRY(cudaMemcpyAsync(lam, pb.lam.data(), sizeof(double) * cols, cudaMemcpyHostToDevice, st));
+  KOP_CUDA_TRY(cudaMemcpyAsync(mu, pb.mu.data(), sizeof(double) * cols, cudaMemcpyHostToDevice, st));
+  KOP_CUDA_TRY(cudaMemsetAsync(op->status, 0, sizeof(int), st));
+
+  VecArgs va;
+  va.n = n;
+  va.cols = cols;
+  va.nrhs = pb.nrhs;
+  va.X = X;
+  va.R = R;
+  va.Z = Z;
+  va.P = P;
+  va.Q = Q;
+  va.B = pb.B;
+  va.T = T;
+  va.lam = lam;
+  va.alpha = alpha;
+  va.beta = beta;
+  va.acc = acc;
+  int rc;
+  auto apply_prec = [&]() -> int {
+    if (!pb.ny) {
+      KOP_CUDA_TRY(cudaMemcpyAsync(Z, R, sizeof(float) * nc, cudaMemcpyDeviceToDevice, st));
+      return KOP_OK;
+    }
+    return nys_apply_dev(pb.ny, mu, pb.adaptive, R, cols, Z, Wd, Wf, acol, st);
+  };
+  const KConst kc = kernel_constants(op->kernel, op->bw);
+  auto matvec = [&](const float* V, float* O, int mode) -> int {
+    return op_matvec(op->pts, op->pts, true, op->kernel, kc, mode, V, cols, cols, O, cols, op->status, st);
+  };
+
+  // x0 = 0, r0 = b, ||b|| per column
+  if ((rc = vec_launch<OP_INIT>(va, st))) return rc;
+  KOP_CUDA_TRY(cudaMemcpyAsync(hb.data(), acc, sizeof(double) * cols, cudaMemcpyDeviceToHost, st));
+  KOP_CUDA_TRY(cudaStreamSynchronize(st));
+  bool any = false;
+  for (int c = 0; c < cols; ++c) {
+    nb[c] = std::sqrt(hb[c]);
+    if (pb.res_hist) pb.res_hist[c] = nb[c] > 0.0 ? 1.0 : 0.0;
+    if (!(nb[c] > 0.0)) {  // b = 0: x = 0 is exact
+      act[c] = 0;
+      if (pb.iters) pb.iters[c] = 0;
+      if (pb.true_relres) pb.true_relres[c] = 0.0;
+    }
+    any = any || act[c];
+  }
+  for (int it = 1; pb.res_hist && it <= pb.maxit; ++it)
+    for (int c = 0; c < cols; ++c) pb.res_hist[(size_t)it * cols + c] = NAN;
+  KOP_CUDA_TRY(cudaMemcpyAsync(active, act.data(), sizeof(int) * cols, cudaMemcpyHostToDevice, st));
+  if ((rc = apply_prec())) return rc;
+  va.acc = rz;
+  if ((rc = vec_launch<OP_DOT>(va, st))) return rc;
+  va.acc = acc;
+  KOP_CUDA_TRY(cudaMemcpyAsync(P, Z, sizeof(float) * nc, cudaMemcpyDeviceToDevice, st));
+
+  int it = 0;
+  bool breakdown = false;
+  std::vector<double> hr(cols);
+  std::vector<char> cand(cols);
+  for (it = 1; any && it <= pb.maxit; ++it) {
+    if ((rc = matvec(P, Q, pb.inner_mode))) return rc;
+    va.acc = acc2;
+    if ((rc = vec_launch<OP_PQ>(va, st))) return rc;
+    fin_alpha_kernel<<<(cols + 127) / 128, 128, 0, st>>>(cols, rz, acc2, active, alpha, op->status);
+    KOP_LAUNCHED();
+    va.acc = acc;
+    if ((rc = vec_launch<OP_XR>(va, st))) return rc;
+    KOP_CUDA_TRY(cudaMemcpyAsync(hr.data(), acc, sizeof(double) * cols, cudaMemcpyDeviceToHost, st));
+    int hs = 0;
+    if ((rc = device_status(op, st, &hs))) return rc;
+    if (hs == KOP_DEV_BREAKDOWN) {
+      breakdown = true;
+      break;
+    }
+    if (hs == KOP_DEV_TIMEOUT) return fail(KOP_ETIMEOUT, "pcg: a bounded device wait timed out");
+    bool any_cand = false;
+    for (int c = 0; c < cols; ++c) {
+      cand[c] = 0;
+      if (!act[c]) continue;
+      rel[c] = std::sqrt(hr[c]) / nb[c];
+      if (pb.res_hist) pb.res_hist[(size_t)it * cols + c] = rel[c];
+      if (rel[c] <= pb.tol) {
+        cand[c] = 1;
+        any_cand = true;
+      }
+    }
+    const bool refine = any_cand || (pb.refine_every > 0 && it % pb.refine_every == 0) || it == pb.maxit;
+    if (refine) {
+      // true residual with the accurate operator replaces the recursive one
+      if ((rc = matvec(X, T, pb.refine_mode))) return rc;
+      if ((rc = vec_launch<OP_RES>(va, st))) return rc;
+      KOP_CUDA_TRY(cudaMemcpyAsync(hr.data(), acc, sizeof(double) * cols, cudaMemcpyDeviceToHost, st));
+      KOP_CUDA_TRY(cudaStreamSynchronize(st));
+      any = false;
+      for (int c = 0; c < cols; ++c) {
+        if (!act[c]) continue;
+        const double tr = std::sqrt(hr[c]) / nb[c];
+        if (pb.true_relres) pb.true_relres[c] = tr;
+        if (cand[c] && tr <= pb.tol) {
+          act[c] = 0;
+          if (pb.iters) pb.iters[c] = it;
+        }
+        any = any || act[c];
+      }
+      KOP_CUDA_TRY(cudaMemcpyAsync(active, act.data(), sizeof(int) * cols, cudaMemcpyHostToDevice, st));
+      if (!any) break;
+    }
+    if ((rc = apply_prec())) return rc;
+    va.acc = acc2;
+    if ((rc = vec_launch<OP_DOT>(va, st))) return rc;
+    fin_beta_kernel<<<(cols + 127) / 128, 128, 0, st>>>(cols, rz, acc2, beta);
+    KOP_LAUNCHED();
+    va.acc = acc;
+    if ((rc = vec_launch<OP_P>(va, st))) return rc;
+  }
+  KOP_CUDA_TRY(cudaStreamSynchronize(st));
+  bool all = true;
+  for (int c = 0; c < cols; ++c)
+    if (act[c]) {
+      all = false;
+      if (pb.iters) pb.iters[c] = it > pb.maxit ? pb.maxit : it;
+    }
+  if (breakdown) return fail(KOP_ENOTPD, "pcg: breakdown (p^T A p <= 0)");
+  return all ? KOP_OK : KOP_NOT_CONVERGED;
+}
+
+}  // namespace kop
+
+using namespace kop;
+
+static bool valid_mode(int m) { return m == KOP_FAST || m == KOP_ACCURATE || m == KOP_PLAIN; }
+
+extern "C" int pcg_solve(kop_t op, nys_t ny, const double* lambdas, int32_t n_shifts, const double* mu,
+                         int32_t adaptive, const float* B, int32_t nrhs, double tol, int32_t maxit,
+                         int32_t refine_every, int32_t inner_mode, int32_t refine_mode, float* Xout, int32_t* iters,
+                         double* res_hist, double* true_relres, void* stream) {
+  if (!op || !lambdas || !B || !Xout || !iters) return fail(KOP_EINVAL, "pcg_solve: NULL argument");
+  if (ny && ny->op != op) return fail(KOP_EINVAL, "pcg_solve: preconditioner built for another operator");
+  if (n_shifts < 1 || nrhs < 1 || (int64_t)n_shifts * nrhs > 4096)
+    return fail(KOP_EINVAL, "pcg_solve: need 1 <= nrhs * n_shifts <= 4096");
+  if (!(tol > 0.0) || maxit < 1 || refine_every < 0) return fail(KOP_EINVAL, "pcg_solve: bad tol / maxit / refine");
+  if (!valid_mode(inner_mode) || !valid_mode(refine_mode)) return fail(KOP_EINVAL, "pcg_solve: bad mode");
+  PcgProblem pb;
+  pb.op = op;
+  pb.ny = ny;
+  pb.nrhs = nrhs;
+  pb.cols = nrhs * n_shifts;
+  for (int s = 0; s < n_shifts; ++s) {
+    const double l = lambdas[s];
+    const double m = mu ? mu[s] : l;
+    if (!(l > 0.0) || !std::isfinite(l) || !(m > 0.0) || !std::isfinite(m))
+      return fail(KOP_EINVAL, "pcg_solve: shifts and damping must be finite and > 0");
+    for (int j = 0; j < nrhs; ++j) {
+      pb.lam.push_back(l);
+      pb.mu.push_back(m);
+    }
+  }
+  pb.adaptive = adaptive ? 1 : 0;
+  pb.B = B;
+  pb.Xout = Xout;
+  pb.tol = tol;
+  pb.maxit = maxit;
+  pb.refine_every = refine_every;
+  pb.inner_mode = inner_mode;
+  pb.refine_mode = refine_mode;
+  pb.iters = iters;
+  pb.res_hist = res_hist;
+  pb.true_relres = true_relres;
+  return pcg_core(pb, (cudaStream_t)stream);
+}
+
+extern "C" int pcg_adjoint(kop_t op, nys_t ny, double lam, int32_t adaptive, const float* x, const float* dLdx,
+                           double tol, int32_t maxit, int32_t refine_every, int32_t inner_mode, int32_t refine_mode,
+                           float* g_out, int32_t* iters, double* dLdlam, double* dLdbw, void* stream) {
+  if (!op || !x || !dLdx || !g_out || !dLdlam || !dLdbw) return fail(KOP_EINVAL, "pcg_adjoint: NULL argument");
+  if (ny && ny->op != op) return fail(KOP_EINVAL, "pcg_adjoint: preconditioner built for another operator");
+  if (!(lam > 0.0) || !std::isfinite(lam)) return fail(KOP_EINVAL, "pcg_adjoint: lam must be > 0");
+  if (!(tol > 0.0) || maxit < 1 || refine_every < 0) return fail(KOP_EINVAL, "pcg_adjoint: bad tol / maxit");
+  if (!valid_mode(inner_mode) || !valid_mode(refine_mode)) return fail(KOP_EINVAL, "pcg_adjoint: bad mode");
+  cudaStream_t st = (cudaStream_t)stream;
+  PcgProblem pb;
+  pb.op = op;
+  pb.ny = ny;
+  pb.cols = pb.nrhs = 1;
+  pb.lam = {lam};
+  pb.mu = {lam};
+  pb.adaptive = adaptive ? 1 : 0;
+  pb.B = dLdx;
+  pb.Xout = g_out;
+  pb.tol = tol;
+  pb.maxit = maxit;
+  pb.refine_every = refine_every;
+  pb.inner_mode = inner_mode;
+  pb.refine_mode = refine_mode;
+  int32_t it = 0;
+  pb.iters = &it;
+  const int rc = pcg_core(pb, st);
+  if (iters) *iters = it;
+  if (rc < 0) return rc;
+  const int64_t n = op->pts.n;
+  Workspace ws;
+  ws.st = st;
+  KOP_CUDA_TRY(cudaMallocAsync(&ws.p, sizeof(float) * n + 2 * sizeof(double), st));
+  float* T = (float*)ws.p;
+  double* acc = (double*)(T + ((n + 1) / 2) * 2);
+  // dL/dbw = -g^T (dK/dbw) x,  dL/dlam = -g^T x
+  const KConst kc = kernel_constants(op->kernel + 3, op->bw);
+  int r2 = op_matvec(op->pts, op->pts, true, op->kernel + 3, kc, refine_mode, x, 1, 1, T, 1, op->status, st);
+  if (r2) return r2;
+  KOP_CUDA_TRY(cudaMemsetAsync(acc, 0, 2 * sizeof(double), st));
+  dot_kernel<<<4 * num_sms(), 256, 0, st>>>(g_out, x, n, acc);
+  dot_kernel<<<4 * num_sms(), 256, 0, st>>>(g_out, T, n, acc + 1);
+  KOP_LAUNCHED();
+  double h[2];
+  KOP_CUDA_TRY(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, st));
+  KOP_CUDA_TRY(cudaStreamSynchronize(st));
+  const int s = kop_sync(op, stream);
+  if (s != KOP_OK) return s;
+  *dLdlam = -h[0];
+  *dLdbw = -h[1];
+  return rc;
+}

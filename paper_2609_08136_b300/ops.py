@@ -1,0 +1,273 @@
+"""Thin PyTorch binding of the kop C ABI: device tensors in, device tensors out.
+
+PyTorch supplies device memory and the current stream; every step of the
+computation runs in the library's CUDA kernels.  Names follow include/kop.h.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _ffi
+from ._ffi import check
+
+RBF, LAPLACE, MATERN52 = 0, 1, 2
+FAST, ACCURATE, PLAIN = 0, 1, 2
+KERNELS = {"rbf": RBF, "laplace": LAPLACE, "matern52": MATERN52}
+
+
+def _ptr(t: torch.Tensor):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_f32(t: torch.Tensor, name: str, cols: int | None = None) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32:
+        raise TypeError(f"{name} must be float32")
+    if t.dim() == 1:
+        t = t.unsqueeze(1)
+    return t.contiguous()
+
+
+def _kind(kernel) -> int:
+    return KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+
+
+class KernelOperator:
+    """K(X, X) for points X (n x d, CUDA float32): kop_create / kop_matvec."""
+
+    def __init__(self, X: torch.Tensor, kernel="rbf", bandwidth: float = 1.0, stream=None):
+        X = _dev_f32(X, "X")
+        self.n, self.d = X.shape
+        self.kernel = _kind(kernel)
+        self.bandwidth = float(bandwidth)
+        self.device = X.device
+        h = ctypes.c_void_p()
+        check(_ffi.lib().kop_create(_ptr(X), self.n, self.d, self.kernel, self.bandwidth, _stream(stream),
+                                    ctypes.byref(h)), "kop_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _ffi.lib().kop_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_bandwidth(self, bw: float):
+        check(_ffi.lib().kop_set_bandwidth(self._h, float(bw)), "kop_set_bandwidth")
+        self.bandwidth = float(bw)
+
+    def matvec(self, V: torch.Tensor, mode: int = FAST, out: torch.Tensor | None = None, stream=None):
+        vec = V.dim() == 1
+        V2 = _dev_f32(V, "V")
+        if V2.shape[0] != self.n:
+            raise ValueError("V must have n rows")
+        O = out if out is not None else torch.empty_like(V2)
+        check(_ffi.lib().kop_matvec(self._h, _ptr(V2), V2.shape[1], _ptr(O), int(mode), _stream(stream)),
+              "kop_matvec")
+        return O[:, 0] if vec and out is None else O
+
+    def dbw_matvec(self, V: torch.Tensor, mode: int = FAST, stream=None):
+        vec = V.dim() == 1
+        V2 = _dev_f32(V, "V")
+        O = torch.empty_like(V2)
+        check(_ffi.lib().kop_dbw_matvec(self._h, _ptr(V2), V2.shape[1], _ptr(O), int(mode), _stream(stream)),
+              "kop_dbw_matvec")
+        return O[:, 0] if vec else O
+
+    def cross_matvec(self, Z: torch.Tensor, V: torch.Tensor, transpose: bool = False, deriv: bool = False,
+                     mode: int = FAST, stream=None):
+        """K(Z, X) V (transpose=False) or K(X, Z) V (transpose=True)."""
+        vec = V.dim() == 1
+        Z = _dev_f32(Z, "Z")
+        V2 = _dev_f32(V, "V")
+        rows = self.n if transpose else Z.shape[0]
+        O = torch.empty((rows, V2.shape[1]), dtype=torch.float32, device=V2.device)
+        check(_ffi.lib().kop_cross_matvec(self._h, _ptr(Z), Z.shape[0], _ptr(V2), V2.shape[1], _ptr(O),
+                                          int(bool(transpose)), int(bool(deriv)), int(mode), _stream(stream)),
+              "kop_cross_matvec")
+        return O[:, 0] if vec else O
+
+    def sync(self, stream=None):
+        check(_ffi.lib().kop_sync(self._h, _stream(stream)), "kop_sync")
+
+
+class Nystrom:
+    """Randomized Nystrom preconditioner of an operator: nys_build / nys_apply."""
+
+    def __init__(self, op: KernelOperator, Omega: torch.Tensor, nu_rel: float = 0.0, mode: int = FAST,
+                 stream=None):
+        Om = _dev_f32(Omega, "Omega")
+        if Om.shape[0] != op.n:
+            raise ValueError("Omega must have n rows")
+        self.op = op
+        self.r = Om.shape[1]
+        h = ctypes.c_void_p()
+        check(_ffi.lib().nys_build(op.handle, _ptr(Om), self.r, float(nu_rel), int(mode), _stream(stream),
+                                   ctypes.byref(h)), "nys_build")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _ffi.lib().nys_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def eigs(self):
+        lam = (ctypes.c_double * self.r)()
+        nu = ctypes.c_double()
+        r = ctypes.c_int32()
+        check(_ffi.lib().nys_eigs(self._h, lam, ctypes.byref(nu), ctypes.byref(r)), "nys_eigs")
+        return torch.tensor(list(lam), dtype=torch.float64), nu.value
+
+    def factor(self, stream=None):
+        U = torch.empty((self.op.n, self.r), dtype=torch.float32, device=self.op.device)
+        check(_ffi.lib().nys_factor(self._h, _ptr(U), _stream(stream)), "nys_factor")
+        return U
+
+    def apply(self, V: torch.Tensor, mu, adaptive: bool = True, stream=None):
+        vec = V.dim() == 1
+        V2 = _dev_f32(V, "V")
+        m = V2.shape[1]
+        mus = [float(mu)] * m if not hasattr(mu, "__len__") else [float(x) for x in mu]
+        arr = (ctypes.c_double * m)(*mus)
+        O = torch.empty_like(V2)
+        check(_ffi.lib().nys_apply(self._h, arr, int(bool(adaptive)), _ptr(V2), m, _ptr(O), _stream(stream)),
+              "nys_apply")
+        return O[:, 0] if vec else O
+
+
+class SolveResult:
+    def __init__(self, x, iters, res_hist, true_relres, status):
+        self.x, self.iters, self.res_hist, self.true_relres, self.status = x, iters, res_hist, true_relres, status
+
+    @property
+    def converged(self):
+        return self.status == 0
+
+
+def pcg_solve(op: KernelOperator, B: torch.Tensor, lambdas, nys: Nystrom | None = None, mu=None,
+              adaptive: bool = True, tol: float = 1e-6, maxit: int = 1000, refine_every: int = 20,
+              inner_mode: int = FAST, refine_mode: int = ACCURATE, history: bool = False, stream=None):
+    """Block PCG for (K + lam_s I) x = B[:, j] over all shifts s and columns j
+    (column s * nrhs + j of the result)."""
+    vec = B.dim() == 1
+    B2 = _dev_f32(B, "B")
+    nrhs = B2.shape[1]
+    lams = [float(lambdas)] if not hasattr(lambdas, "__len__") else [float(x) for x in lambdas]
+    ns = len(lams)
+    cols = ns * nrhs
+    lam_arr = (ctypes.c_double * ns)(*lams)
+    mu_arr = None
+    if mu is not None:
+        mus = [float(mu)] * ns if not hasattr(mu, "__len__") else [float(x) for x in mu]
+        mu_arr = (ctypes.c_double * ns)(*mus)
+    X = torch.empty((op.n, cols), dtype=torch.float32, device=B2.device)
+    iters = (ctypes.c_int32 * cols)()
+    hist = (ctypes.c_double * ((maxit + 1) * cols))() if history else None
+    tr = (ctypes.c_double * cols)()
+    rc = check(_ffi.lib().pcg_solve(op.handle, nys.handle if nys is not None else None, lam_arr, ns, mu_arr,
+                                    int(bool(adaptive)), _ptr(B2), nrhs, float(tol), int(maxit), int(refine_every),
+                                    int(inner_mode), int(refine_mode), _ptr(X), iters, hist, tr,
+                                    _stream(stream)), "pcg_solve")
+    h = None
+    if history:
+        import numpy as np
+        h = np.array(list(hist)).reshape(maxit + 1, cols)
+    x = X[:, 0] if (vec and cols == 1) else X
+    return SolveResult(x, list(iters), h, list(tr), rc)
+
+
+def pcg_adjoint(op: KernelOperator, x: torch.Tensor, dLdx: torch.Tensor, lam: float, nys: Nystrom | None = None,
+                adaptive: bool = True, tol: float = 1e-6, maxit: int = 1000, refine_every: int = 20,
+                inner_mode: int = FAST, refine_mode: int = ACCURATE, stream=None):
+    """g = (K + lam I)^{-1} dL/dx, and dL/dlam = -g^T x, dL/dbw = -g^T (dK/dbw) x."""
+    x2 = _dev_f32(x, "x").reshape(-1).contiguous()
+    d2 = _dev_f32(dLdx, "dLdx").reshape(-1).contiguous()
+    g = torch.empty_like(x2)
+    it = ctypes.c_int32()
+    dl = ctypes.c_double()
+    db = ctypes.c_double()
+    check(_ffi.lib().pcg_adjoint(op.handle, nys.handle if nys is not None else None, float(lam),
+                                 int(bool(adaptive)), _ptr(x2), _ptr(d2), float(tol), int(maxit), int(refine_every),
+                                 int(inner_mode), int(refine_mode), _ptr(g), ctypes.byref(it), ctypes.byref(dl),
+                                 ctypes.byref(db), _stream(stream)), "pcg_adjoint")
+    return g, dl.value, db.value, it.value
+
+
+class _KRRSolve(torch.autograd.Function):
+    """x = (K(bw) + lam I)^{-1} b with an adjoint backward (pcg_adjoint)."""
+
+    @staticmethod
+    def forward(ctx, b, bw, lam, op, nys, kw):
+        op.set_bandwidth(float(bw))
+        res = pcg_solve(op, b.detach(), [float(lam)], nys=nys, **kw)
+        if res.status < 0:
+            raise RuntimeError("pcg_solve failed")
+        x = res.x.reshape(b.shape)
+        ctx.save_for_backward(x)
+        ctx.op, ctx.nys, ctx.kw, ctx.lam = op, nys, kw, float(lam)
+        ctx.bw_dtype, ctx.lam_dtype = bw.dtype, lam.dtype
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        (x,) = ctx.saved_tensors
+        kw = dict(ctx.kw)
+        kw.pop("history", None)
+        g, dlam, dbw, _ = pcg_adjoint(ctx.op, x, gx.contiguous(), ctx.lam, nys=ctx.nys, **kw)
+        return (g.reshape(x.shape), torch.tensor(dbw, dtype=ctx.bw_dtype), torch.tensor(dlam, dtype=ctx.lam_dtype),
+                None, None, None)
+
+
+def krr_solve(op: KernelOperator, b: torch.Tensor, bw: torch.Tensor, lam: torch.Tensor, nys: Nystrom | None = None,
+              **kw):
+    """Differentiable solve of (K(bw) + lam I) x = b with respect to b, bw and lam
+    (bw and lam are 0-dim CPU tensors).  The paper differentiates through the
+    solver (Sec. 3.2); here the backward pass is one adjoint solve."""
+    return _KRRSolve.apply(b, bw, lam, op, nys, kw)
+
+
+def krr_val_loss_and_grad(op: KernelOperator, nys: Nystrom | None, y: torch.Tensor, Xv: torch.Tensor,
+                          yv: torch.Tensor, lam: float, tol: float = 1e-6, maxit: int = 1000, refine_every: int = 20,
+                          inner_mode: int = FAST, refine_mode: int = ACCURATE):
+    """Validation loss L = (1/n_val) ||K(Xv, X) x - yv||^2 with x = (K + lam I)^{-1} y,
+    and its derivatives with respect to the bandwidth and lam (adjoint method)."""
+    res = pcg_solve(op, y, [lam], nys=nys, tol=tol, maxit=maxit, refine_every=refine_every, inner_mode=inner_mode,
+                    refine_mode=refine_mode)
+    x = res.x.reshape(-1)
+    nv = Xv.shape[0]
+    e = op.cross_matvec(Xv, x, mode=refine_mode) - yv.reshape(-1)
+    e64 = e.double()
+    loss = float(e64 @ e64) / nv
+    dLdx = op.cross_matvec(Xv, e, transpose=True, mode=refine_mode) * (2.0 / nv)
+    g, dlam, dbw_k, _ = pcg_adjoint(op, x, dLdx, lam, nys=nys, tol=tol, maxit=maxit, refine_every=refine_every,
+                                    inner_mode=inner_mode, refine_mode=refine_mode)
+    dkv = op.cross_matvec(Xv, x, deriv=True, mode=refine_mode).double()
+    dbw = (2.0 / nv) * float(e64 @ dkv) + dbw_k
+    return loss, dbw, dlam

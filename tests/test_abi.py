@@ -1,0 +1,43 @@
+"""CPU checks of the C ABI: the library builds, loads without a GPU and
+exports every entry point that include/kop.h declares."""
+import os
+import re
+
+from paper_2609_08136_b300 import _ffi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "kop.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(\w+)\s*\(", src, flags=re.M)
+    return sorted(set(n for n in names if n not in ("if", "while")))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("kop_create", "kop_matvec", "nys_build", "pcg_solve", "pcg_adjoint", "kop_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = _ffi.lib()
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_ctypes_table_matches_header():
+    assert set(_ffi.SIGNATURES) == set(_declared())
+
+
+def test_invalid_arguments_rejected_without_gpu():
+    import ctypes
+    lib = _ffi.lib()
+    h = ctypes.c_void_p()
+    # NULL X, bad d, bad bandwidth: rejected before any CUDA call
+    assert lib.kop_create(None, 10, 4, 0, 1.0, None, ctypes.byref(h)) == -1
+    assert lib.kop_create(ctypes.c_void_p(16), 10, 0, 0, 1.0, None, ctypes.byref(h)) == -1
+    assert lib.kop_create(ctypes.c_void_p(16), 10, 4, 0, -1.0, None, ctypes.byref(h)) == -1
+    assert lib.kop_create(ctypes.c_void_p(16), 10, 4, 7, 1.0, None, ctypes.byref(h)) == -1
+    assert b"kernel" in lib.kop_last_error()

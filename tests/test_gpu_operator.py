@@ -1,0 +1,82 @@
+"""Parity of the kernel-operator products (fused tensor-core path in both
+precision modes, and the plain FP32 path) with the FP64 oracle.
+
+Error measure: per output, |O - O_ref| / sum_j |K_ij| |V_jc| (the scale of
+the terms being summed).  Bounds: KOP_FAST forms distances from a 2-term BF16
+split (about 2^-16 relative per coordinate), so the kernel exponent is off by
+about 2^-15 * |x|^2 / s^2; with the test data |x|^2 / s^2 <= ~6 this gives
+< 3e-4.  KOP_ACCURATE and KOP_PLAIN are FP32-level: < 4e-6."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import kop_oracle as O
+from paper_2609_08136_b300 import ops
+from paper_2609_08136_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {ops.FAST: 3e-4, ops.ACCURATE: 4e-6, ops.PLAIN: 4e-6}
+
+
+def _rel_err(kind, Xq, Xk, V, bw, got, deriv=False):
+    D2 = O.sqdist(Xq, Xk)
+    f = O.dkernel_dbw_from_sqdist if deriv else O.kernel_from_sqdist
+    Km = f(kind, D2, bw)
+    V64 = V.astype(np.float64)
+    ref = Km @ V64
+    scale = np.abs(Km) @ np.abs(V64) + 1e-300
+    return np.max(np.abs(got.astype(np.float64) - ref) / scale)
+
+
+CASES = [  # n, d, m
+    (1, 3, 1), (2, 16, 1), (127, 16, 1), (129, 32, 3), (300, 64, 1), (257, 5, 8), (640, 128, 2),
+    (1000, 100, 1), (385, 64, 13),
+]
+
+
+@pytest.mark.parametrize("mode", [ops.FAST, ops.ACCURATE, ops.PLAIN])
+@pytest.mark.parametrize("kind", [ops.RBF, ops.LAPLACE, ops.MATERN52])
+@pytest.mark.parametrize("n,d,m", CASES)
+def test_matvec_parity(n, d, m, kind, mode):
+    X = W.random_points(n, d, seed=n + d, scale=1.0, shift=2.0)
+    V = W.random_block(n, m, seed=7 * n + m)
+    bw = float(np.sqrt(d)) * (0.8 if kind == ops.RBF else 1.5)
+    op = ops.KernelOperator(torch.from_numpy(X).cuda(), kind, bw)
+    got = op.matvec(torch.from_numpy(V).cuda(), mode=mode).cpu().numpy()
+    op.sync()
+    assert _rel_err(kind, X, X, V, bw, got) < TOL[mode]
+
+
+@pytest.mark.parametrize("mode", [ops.FAST, ops.ACCURATE])
+def test_diagonal_is_exact(mode):
+    n, d = 200, 64
+    X = W.random_points(n, d, seed=3)
+    op = ops.KernelOperator(torch.from_numpy(X).cuda(), ops.RBF, 8.0)
+    E = np.zeros((n, 8), dtype=np.float32)
+    cols = [0, 5, 127, 128, 150, 199, 64, 1]
+    for c, j in enumerate(cols):
+        E[j, c] = 1.0
+    got = op.matvec(torch.from_numpy(E).cuda(), mode=mode).cpu().numpy()
+    for c, j in enumerate(cols):
+        assert got[j, c] == 1.0
+
+
+@pytest.mark.parametrize("mode", [ops.FAST, ops.ACCURATE, ops.PLAIN])
+@pytest.mark.parametrize("kind", [ops.RBF, ops.LAPLACE, ops.MATERN52])
+def test_cross_and_derivative_parity(kind, mode):
+    n, nz, d, m = 333, 77, 32, 2
+    X = W.random_points(n, d, seed=1)
+    Z = W.random_points(nz, d, seed=2, shift=0.3)
+    bw = 7.0
+    op = ops.KernelOperator(torch.from_numpy(X).cuda(), kind, bw)
+    Vn = W.random_block(n, m, seed=3)
+    Vz = W.random_block(nz, m, seed=4)
+    got = op.cross_matvec(torch.from_numpy(Z).cuda(), torch.from_numpy(Vn).cuda(), mode=mode).cpu().numpy()
+    assert _rel_err(kind, Z, X, Vn, bw, got) < TOL[mode]
+    got = op.cross_matvec(torch.from_numpy(Z).cuda(), torch.from_numpy(Vz).cuda(), transpose=True,
+                          mode=mode).cpu().numpy()
+    assert _rel_err(kind, X, Z, Vz, bw, got) < TOL[mode]
+    got = op.dbw_matvec(torch.from_numpy(Vn).cuda(), mode=mode).cpu().numpy()
+    assert _rel_err(kind, X, X, Vn, bw, got, deriv=True) < 2 * TOL[mode]
+    op.sync()
