@@ -59,8 +59,13 @@ enum kop_kernel { KOP_RBF = 0, KOP_LAPLACE = 1, KOP_MATERN52 = 2 };
  *                 used for the periodic true residual of the solver.
  *   KOP_PLAIN     plain FP32 CUDA-core path: direct-difference distances,
  *                 FP32 exp and FMA contraction; no tensor cores.  The speed
- *                 baseline of the fused path.                               */
-enum kop_mode { KOP_FAST = 0, KOP_ACCURATE = 1, KOP_PLAIN = 2 };
+ *                 baseline of the fused path.
+ *   KOP_EXACT     FP64 CUDA-core path: direct differences of the original
+ *                 points, FP64 kernel values and accumulation (the paper's
+ *                 float64 residual check, App. B.2).  About two orders of
+ *                 magnitude slower than KOP_FAST on a B300; meant for true
+ *                 residuals of small or badly conditioned problems.         */
+enum kop_mode { KOP_FAST = 0, KOP_ACCURATE = 1, KOP_PLAIN = 2, KOP_EXACT = 3 };
 
 enum kop_status {
   KOP_OK = 0,
@@ -107,6 +112,10 @@ int kop_matvec(kop_t op, const float* V, int32_t m, float* O, int32_t mode, void
  * deriv = 1 replaces k by dk/d(bandwidth) (used by the adjoint gradient).   */
 int kop_cross_matvec(kop_t op, const float* Z, int64_t nz, const float* V, int32_t m, float* O,
                      int32_t transpose, int32_t deriv, int32_t mode, void* stream);
+
+/* FP64 product with the KOP_EXACT operator: O (n x m, FP64) = K V (V FP64),
+ * or (dK/d bandwidth) V when deriv != 0. */
+int kop_matvec_f64(kop_t op, const double* V, int32_t m, double* O, int32_t deriv, void* stream);
 
 /* O (n x m) = (dK(X, X)/d bandwidth) V. */
 int kop_dbw_matvec(kop_t op, const float* V, int32_t m, float* O, int32_t mode, void* stream);
@@ -160,7 +169,9 @@ int nys_factor(nys_t ny, float* U_out, void* stream);
  * The preconditioner of column c uses damping mu[s] (host; NULL: mu = lambdas).
  *   lambdas      host, n_shifts values > 0
  *   B            device, n x nrhs
- *   Xout         device, n x (nrhs * n_shifts); x0 = 0
+ *   Xout         device, n x (nrhs * n_shifts), FP64 (x0 = 0).  The iterate is
+ *                accumulated in FP64: FP32 storage of x alone would bound the
+ *                attainable FP64 residual near 2^-24 ||A|| ||x|| / ||b||.
  *   iters        host, nrhs * n_shifts ints (operator products per column)
  *   res_hist     host or NULL, (maxit + 1) x cols doubles: recursive
  *                ||r_k|| / ||b|| per iteration (NaN after a column stops)
@@ -169,21 +180,21 @@ int nys_factor(nys_t ny, float* U_out, void* stream);
  * breakdown.  Synchronizes `stream`.                                         */
 int pcg_solve(kop_t op, nys_t ny, const double* lambdas, int32_t n_shifts, const double* mu,
               int32_t adaptive, const float* B, int32_t nrhs, double tol, int32_t maxit,
-              int32_t refine_every, int32_t inner_mode, int32_t refine_mode, float* Xout,
+              int32_t refine_every, int32_t inner_mode, int32_t refine_mode, double* Xout,
               int32_t* iters, double* res_hist, double* true_relres, void* stream);
 
 /* Adjoint of one solve (the paper differentiates through the solver,
  * Sec. 3.2, Eq. "rlaopt-bilevel"; here by an adjoint solve instead of
  * unrolling, which gives the same gradient at convergence).  Given the
- * solution x of (K + lam I) x = b and dL/dx (device, n), solves
+ * solution x of (K + lam I) x = b and dL/dx (device, n, both FP64), solves
  *     (K + lam I) g = dL/dx
- * with the same preconditioner (mu = lam), writes g (device, n) and the host
- * scalars
+ * with the same preconditioner (mu = lam), writes g (device, n, FP64) and the
+ * host scalars
  *     dL/dlam = -g^T x,        dL/dbw|_K = -g^T (dK/dbw) x,
  * (dL/db = g).  iters: host int (may be NULL).                              */
-int pcg_adjoint(kop_t op, nys_t ny, double lam, int32_t adaptive, const float* x,
-                const float* dLdx, double tol, int32_t maxit, int32_t refine_every,
-                int32_t inner_mode, int32_t refine_mode, float* g_out, int32_t* iters,
+int pcg_adjoint(kop_t op, nys_t ny, double lam, int32_t adaptive, const double* x,
+                const double* dLdx, double tol, int32_t maxit, int32_t refine_every,
+                int32_t inner_mode, int32_t refine_mode, double* g_out, int32_t* iters,
                 double* dLdlam, double* dLdbw, void* stream);
 
 #ifdef __cplusplus

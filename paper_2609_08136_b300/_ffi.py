@@ -24,6 +24,7 @@ SIGNATURES = {
     "kop_matvec": (c_int, [c_vp, c_vp, c_i32, c_vp, c_i32, c_vp]),
     "kop_cross_matvec": (c_int, [c_vp, c_vp, c_i64, c_vp, c_i32, c_vp, c_i32, c_i32, c_i32, c_vp]),
     "kop_dbw_matvec": (c_int, [c_vp, c_vp, c_i32, c_vp, c_i32, c_vp]),
+    "kop_matvec_f64": (c_int, [c_vp, c_vp, c_i32, c_vp, c_i32, c_vp]),
     "kop_sync": (c_int, [c_vp, c_vp]),
     "nys_build": (c_int, [c_vp, c_vp, c_i32, c_dbl, c_i32, c_vp, P(c_vp)]),
     "nys_destroy": (c_int, [c_vp]),

@@ -11,10 +11,11 @@ namespace kop {
 int op_matvec(const PointSet& Q, const PointSet& Ks, bool self, int kf, const KConst& kc, int mode,
               const float* V, int m, int ldv, float* O, int ldo, int* status, cudaStream_t st) {
   if (mode == KOP_PLAIN) return plain_matvec(Q, Ks, self, kf, kc, V, m, ldv, O, ldo, st);
+  if (mode == KOP_EXACT) return exact_matvec_f32(Q, Ks, kf, kc.bw, V, m, ldv, O, ldo, st);
   return fused_matvec(Q, Ks, self, kf, kc, mode == KOP_ACCURATE ? 3 : 2, V, m, ldv, O, ldo, status, st);
 }
 
-static bool bad_mode(int mode) { return mode != KOP_FAST && mode != KOP_ACCURATE && mode != KOP_PLAIN; }
+static bool bad_mode(int mode) { return mode < KOP_FAST || mode > KOP_EXACT; }
 
 }  // namespace kop
 
@@ -83,6 +84,12 @@ extern "C" int kop_matvec(kop_t op, const float* V, int32_t m, float* O, int32_t
   if (bad_mode(mode)) return fail(KOP_EINVAL, "kop_matvec: unknown mode");
   const KConst kc = kernel_constants(op->kernel, op->bw);
   return op_matvec(op->pts, op->pts, true, op->kernel, kc, mode, V, m, m, O, m, op->status, (cudaStream_t)stream);
+}
+
+extern "C" int kop_matvec_f64(kop_t op, const double* V, int32_t m, double* O, int32_t deriv, void* stream) {
+  if (!op || !V || !O) return fail(KOP_EINVAL, "kop_matvec_f64: NULL argument");
+  if (m < 1) return fail(KOP_EINVAL, "kop_matvec_f64: m must be >= 1");
+  return exact_matvec(op->pts, op->pts, op->kernel + (deriv ? 3 : 0), op->bw, V, m, m, O, m, (cudaStream_t)stream);
 }
 
 extern "C" int kop_dbw_matvec(kop_t op, const float* V, int32_t m, float* O, int32_t mode, void* stream) {

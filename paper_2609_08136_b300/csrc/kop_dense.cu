@@ -218,6 +218,74 @@ int uw(const float* U, int ldu, int64_t n, int p, const float* w, const float* v
   return KOP_OK;
 }
 
+// ------------------------------------------------------------------ FP64 projections
+// W (p x m, FP64, pre-zeroed) += U^T V for m <= 8 columns, products and sums in
+// FP64.  Thread k owns column k of U; the rows of V are read as broadcasts.
+__global__ void __launch_bounds__(256) utv64_kernel(const float* __restrict__ U, int ldu, int64_t n, int p,
+                                                    const float* __restrict__ V, int m, int64_t rows_per_block,
+                                                    double* __restrict__ W) {
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
+  const int64_t r1 = r0 + rows_per_block < n ? r0 + rows_per_block : n;
+  for (int k = threadIdx.x; k < p; k += blockDim.x) {
+    double acc[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c] = 0.0;
+    for (int64_t i = r0; i < r1; ++i) {
+      const double u = (double)U[i * ldu + k];
+#pragma unroll
+      for (int c = 0; c < 8; ++c)
+        if (c < m) acc[c] = fma(u, (double)V[i * m + c], acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+      if (c < m) atomicAdd(&W[(int64_t)k * m + c], acc[c]);
+  }
+}
+
+// O[i][c] = (float)(alpha[c] V[i][c] + sum_k U[i][k] W[k][c]) in FP64; one warp per row.
+__global__ void __launch_bounds__(256) uw64_kernel(const float* __restrict__ U, int ldu, int64_t n, int p,
+                                                   const double* __restrict__ W, const float* __restrict__ V, int m,
+                                                   const double* __restrict__ alpha, float* __restrict__ O) {
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  double s[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) s[c] = 0.0;
+  for (int k = lane; k < p; k += 32) {
+    const double u = (double)U[row * ldu + k];
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+      if (c < m) s[c] = fma(u, W[(int64_t)k * m + c], s[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    if (c >= m) break;
+    double x = s[c];
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+    if (lane == 0) O[row * m + c] = (float)fma(alpha[c], (double)V[row * m + c], x);
+  }
+}
+
+int utv64(const float* U, int ldu, int64_t n, int p, const float* V, int m, double* W, cudaStream_t st) {
+  KOP_CUDA_TRY(cudaMemsetAsync(W, 0, sizeof(double) * (size_t)p * m, st));
+  int64_t blocks = 4 * num_sms();
+  int64_t rpb = (n + blocks - 1) / blocks;
+  if (rpb < 64) rpb = 64;
+  blocks = (n + rpb - 1) / rpb;
+  utv64_kernel<<<(unsigned)blocks, 256, 0, st>>>(U, ldu, n, p, V, m, rpb, W);
+  KOP_LAUNCHED();
+  return KOP_OK;
+}
+
+int uw64(const float* U, int ldu, int64_t n, int p, const double* W, const float* V, int m, const double* alpha,
+         float* O, cudaStream_t st) {
+  const int64_t threads = n * 32;
+  uw64_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(U, ldu, n, p, W, V, m, alpha, O);
+  KOP_LAUNCHED();
+  return KOP_OK;
+}
+
 // ------------------------------------------------------------------ r x r FP64
 // Element-wise combinations of the r x r Gram blocks.
 //   mode 0: M = (Goy + Goy^T)/2 + nu Goo

@@ -17,6 +17,11 @@ int utv(const float* U, int ldu, int64_t n, int p, const float* v, int ldv, doub
 // o = alpha[0] v + U w for one vector (alpha on the device).
 int uw(const float* U, int ldu, int64_t n, int p, const float* w, const float* v, int ldv, const float* alpha,
        float* o, int ldo, cudaStream_t st);
+// FP64-accurate projections for m <= 8 columns: W = U^T V, and
+// O = alpha (.) V + U W (row-major V, O with m columns).
+int utv64(const float* U, int ldu, int64_t n, int p, const float* V, int m, double* W, cudaStream_t st);
+int uw64(const float* U, int ldu, int64_t n, int p, const double* W, const float* V, int m, const double* alpha,
+         float* O, cudaStream_t st);
 // mode 0: M = sym(Goy) + nu Goo;  mode 1: M = Gyy + nu (Goy + Goy^T) + nu^2 Goo.
 int combine(const double* Goo, const double* Goy, const double* Gyy, int r, double nu, int mode, double* M,
             cudaStream_t st);

@@ -1,0 +1,41 @@
+// Kernel-function epilogue shared by the fused operator kernels.
+//
+// The kernels see a pre-scaled squared distance u = s * D2, with the scale s
+// folded into the row norms and into the MMA result:
+//     u = s|q_i|^2 + s|x_j|^2 - 2 s (q_i . x_j)
+//   RBF       s = -log2(e) / (2 bw^2):  k = 2^u
+//   Laplace   s = (log2(e) / bw)^2:     k = 2^-sqrt(u)
+//   Matern52  s = 5 / bw^2:             a = sqrt(u), k = (1 + a + u/3) 2^(-log2(e) a)
+// and the bandwidth derivatives dk/dbw:
+//   RBF       k D2 / bw^3        = 2^u * u * c2,  c2 = 1 / (s bw^3)
+//   Laplace   k r / bw^2         = 2^-sqrt(u) * sqrt(u) * c2,  c2 = 1 / (sqrt(s) bw^2)
+//   Matern52  e^-a (a^2/3)(1+a)/bw = 2^(-log2(e) a) (u/3)(1 + a) c2,  c2 = 1 / bw
+// u can be slightly negative from rounding when D2 ~ 0: sqrt takes |u|.
+#pragma once
+#include "kop_device.cuh"
+
+namespace kop {
+
+constexpr float kNegLog2e = -1.4426950408889634f;
+
+template <int KF>
+KOP_DEV float kval_u(float u, float c2) {
+  if constexpr (KF == 0) {
+    return ex2_approx(u);
+  } else if constexpr (KF == 1) {
+    return ex2_approx(-sqrt_approx(fabsf(u)));
+  } else if constexpr (KF == 2) {
+    const float a = sqrt_approx(fabsf(u));
+    return fmaf(u, 1.0f / 3.0f, 1.0f + a) * ex2_approx(kNegLog2e * a);
+  } else if constexpr (KF == 3) {
+    return ex2_approx(u) * u * c2;
+  } else if constexpr (KF == 4) {
+    const float r = sqrt_approx(fabsf(u));
+    return ex2_approx(-r) * r * c2;
+  } else {
+    const float a = sqrt_approx(fabsf(u));
+    return ex2_approx(kNegLog2e * a) * (u * (1.0f / 3.0f)) * (1.0f + a) * c2;
+  }
+}
+
+}  // namespace kop

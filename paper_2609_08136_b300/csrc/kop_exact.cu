@@ -1,0 +1,171 @@
+// FP64 CUDA-core kernel operator (KOP_EXACT): O = K(Q, X) V with FP64
+// vectors, direct differences of the original FP32 points in FP64, the kernel
+// function in FP64 and FP64 accumulation.
+//
+// This is the true-residual operator of the solver's iterative refinement:
+// the paper checks the relative residual in float64 (App. B.2), and on badly
+// conditioned systems FP32 rounding of the kernel values alone leaves a
+// residual floor near 1e-6.  B300's FP64 rate makes this about two orders of
+// magnitude slower than the fused product, so it is used for the periodic
+// true residual, not for the inner iterations.  One thread per query row;
+// tiles of 32 points and their V rows are staged in shared memory.
+#include <cmath>
+
+#include "kop_device.cuh"
+#include "kop_internal.h"
+
+namespace kop {
+
+constexpr int K4_ROWS = 128;
+constexpr int K4_KEYS = 32;
+
+template <int KF>
+KOP_DEV double exact_kernel_value(double d2, double bw) {
+  if constexpr (KF == KF_RBF) {
+    return exp(-d2 / (2.0 * bw * bw));
+  } else if constexpr (KF == KF_LAPLACE) {
+    return exp(-sqrt(d2) / bw);
+  } else if constexpr (KF == KF_MATERN) {
+    const double a = 2.23606797749978969640 * sqrt(d2) / bw;
+    return (1.0 + a + a * a / 3.0) * exp(-a);
+  } else if constexpr (KF == KF_DRBF) {
+    return exp(-d2 / (2.0 * bw * bw)) * d2 / (bw * bw * bw);
+  } else if constexpr (KF == KF_DLAPLACE) {
+    const double r = sqrt(d2);
+    return exp(-r / bw) * r / (bw * bw);
+  } else {
+    const double a = 2.23606797749978969640 * sqrt(d2) / bw;
+    return exp(-a) * (a * a / 3.0) * (1.0 + a) / bw;
+  }
+}
+
+template <int KF, int MV>
+__global__ void __launch_bounds__(K4_ROWS) k4_exact_kernel(const float* __restrict__ Q, const float* __restrict__ Xk,
+                                                           int d, const double* __restrict__ V, int ldv,
+                                                           double* __restrict__ O, int ldo, int nq, int nk, int m,
+                                                           double bw) {
+  extern __shared__ double sd[];
+  double* Qs = sd;                          // d x (K4_ROWS + 1), transposed
+  double* Xs = Qs + d * (K4_ROWS + 1);      // K4_KEYS x d
+  double* Vs = Xs + K4_KEYS * d;            // K4_KEYS x MV
+  const int tid = threadIdx.x;
+  const int row0 = blockIdx.x * K4_ROWS;
+  for (int idx = tid; idx < K4_ROWS * d; idx += K4_ROWS) {
+    const int r = idx / d, k = idx - r * d;
+    Qs[k * (K4_ROWS + 1) + r] = (row0 + r < nq) ? (double)Q[(int64_t)(row0 + r) * d + k] : 0.0;
+  }
+  double acc[MV];
+#pragma unroll
+  for (int c = 0; c < MV; ++c) acc[c] = 0.0;
+  for (int j0 = 0; j0 < nk; j0 += K4_KEYS) {
+    __syncthreads();
+    for (int idx = tid; idx < K4_KEYS * d; idx += K4_ROWS) {
+      const int jj = idx / d;
+      Xs[idx] = (j0 + jj < nk) ? (double)Xk[(int64_t)j0 * d + idx] : 0.0;
+    }
+    for (int idx = tid; idx < K4_KEYS * MV; idx += K4_ROWS) {
+      const int jj = idx / MV, c = idx - jj * MV;
+      Vs[idx] = (j0 + jj < nk && c < m) ? V[(int64_t)(j0 + jj) * ldv + c] : 0.0;
+    }
+    __syncthreads();
+    const int jn = nk - j0 < K4_KEYS ? nk - j0 : K4_KEYS;
+    for (int jj = 0; jj < jn; ++jj) {
+      double d2 = 0.0;
+      for (int k = 0; k < d; ++k) {
+        const double t = Qs[k * (K4_ROWS + 1) + tid] - Xs[jj * d + k];
+        d2 = fma(t, t, d2);
+      }
+      const double kv = exact_kernel_value<KF>(d2, bw);
+#pragma unroll
+      for (int c = 0; c < MV; ++c) acc[c] = fma(kv, Vs[jj * MV + c], acc[c]);
+    }
+  }
+  const int gi = row0 + tid;
+  if (gi < nq) {
+#pragma unroll
+    for (int c = 0; c < MV; ++c)
+      if (c < m) O[(int64_t)gi * ldo + c] = acc[c];
+  }
+}
+
+template <int KF, int MV>
+static int launch_exact_t(const PointSet& Q, const PointSet& Ks, const double* V, int m, int ldv, double* O, int ldo,
+                          double bw, cudaStream_t st) {
+  auto kern = k4_exact_kernel<KF, MV>;
+  const int d = Q.d;
+  const size_t smem = sizeof(double) * ((size_t)d * (K4_ROWS + 1) + (size_t)K4_KEYS * d + K4_KEYS * MV);
+  static bool attr_set = false;
+  if (!attr_set) {
+    KOP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_limit_bytes()));
+    attr_set = true;
+  }
+  dim3 grid((unsigned)((Q.n + K4_ROWS - 1) / K4_ROWS));
+  kern<<<grid, K4_ROWS, smem, st>>>(Q.xorig, Ks.xorig, d, V, ldv, O, ldo, (int)Q.n, (int)Ks.n, m, bw);
+  KOP_LAUNCHED();
+  return KOP_OK;
+}
+
+template <int KF>
+static int launch_exact_kf(const PointSet& Q, const PointSet& Ks, const double* V, int m, int ldv, double* O, int ldo,
+                           double bw, cudaStream_t st) {
+  for (int c0 = 0; c0 < m; c0 += 8) {
+    const int mc = (m - c0) < 8 ? (m - c0) : 8;
+    int rc;
+    if (mc == 1)
+      rc = launch_exact_t<KF, 1>(Q, Ks, V + c0, mc, ldv, O + c0, ldo, bw, st);
+    else if (mc <= 2)
+      rc = launch_exact_t<KF, 2>(Q, Ks, V + c0, mc, ldv, O + c0, ldo, bw, st);
+    else
+      rc = launch_exact_t<KF, 8>(Q, Ks, V + c0, mc, ldv, O + c0, ldo, bw, st);
+    if (rc) return rc;
+  }
+  return KOP_OK;
+}
+
+int exact_matvec(const PointSet& Q, const PointSet& Ks, int kf, double bw, const double* V, int m, int ldv, double* O,
+                 int ldo, cudaStream_t st) {
+  if (Q.n == 0 || Ks.n == 0 || m == 0) return KOP_OK;
+  switch (kf) {
+    case KF_RBF: return launch_exact_kf<KF_RBF>(Q, Ks, V, m, ldv, O, ldo, bw, st);
+    case KF_LAPLACE: return launch_exact_kf<KF_LAPLACE>(Q, Ks, V, m, ldv, O, ldo, bw, st);
+    case KF_MATERN: return launch_exact_kf<KF_MATERN>(Q, Ks, V, m, ldv, O, ldo, bw, st);
+    case KF_DRBF: return launch_exact_kf<KF_DRBF>(Q, Ks, V, m, ldv, O, ldo, bw, st);
+    case KF_DLAPLACE: return launch_exact_kf<KF_DLAPLACE>(Q, Ks, V, m, ldv, O, ldo, bw, st);
+    default: return launch_exact_kf<KF_DMATERN>(Q, Ks, V, m, ldv, O, ldo, bw, st);
+  }
+}
+
+__global__ void f2d_kernel(const float* __restrict__ a, int ld, int m, int64_t n, double* __restrict__ b) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * m) return;
+  const int64_t i = t / m;
+  const int c = (int)(t - i * m);
+  b[t] = (double)a[i * ld + c];
+}
+
+__global__ void d2f_out_kernel(const double* __restrict__ a, int m, int64_t n, float* __restrict__ b, int ld) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * m) return;
+  const int64_t i = t / m;
+  const int c = (int)(t - i * m);
+  b[i * ld + c] = (float)a[t];
+}
+
+// FP32 in / FP32 out wrapper (the FP64 product is rounded once at the end).
+int exact_matvec_f32(const PointSet& Q, const PointSet& Ks, int kf, double bw, const float* V, int m, int ldv,
+                     float* O, int ldo, cudaStream_t st) {
+  double* buf = nullptr;
+  const size_t nv = (size_t)Ks.n * m, no = (size_t)Q.n * m;
+  KOP_CUDA_TRY(cudaMallocAsync((void**)&buf, sizeof(double) * (nv + no), st));
+  f2d_kernel<<<(unsigned)((nv + 255) / 256), 256, 0, st>>>(V, ldv, m, Ks.n, buf);
+  KOP_LAUNCHED();
+  int rc = exact_matvec(Q, Ks, kf, bw, buf, m, m, buf + nv, m, st);
+  if (rc == KOP_OK) {
+    d2f_out_kernel<<<(unsigned)((no + 255) / 256), 256, 0, st>>>(buf + nv, m, Q.n, O, ldo);
+    KOP_LAUNCHED();
+  }
+  cudaFreeAsync(buf, st);
+  return rc;
+}
+
+}  // namespace kop

@@ -1,72 +1,54 @@
-// Fused kernel-operator product O = f(K(Q, X)) V on the tensor cores.
+// Fused kernel-operator product O = k(Q, X) V on the tensor cores, for blocks
+// of up to 8 vectors (the PCG iterations: m = 1 per right-hand side).
 //
 // This is the matrix-free operator of the paper (Sec. 4.3: the linear
-// operator is applied without ever being formed; Sec. 2.1: K_ij = k(x_i, x_j)
-// and each CG iteration costs one O(n^2) product).  Per 128-row block of Q a
-// CTA streams tiles of X:
-//   S   = Q_I X_J^T      tcgen05.mma, BF16 split operands, FP32 in TMEM
-//   D2  = |q_i|^2 + |x_j|^2 - 2 S_ij   (clamped at 0, exactly 0 on the
-//                                        diagonal of a symmetric product)
-//   K   = k(D2)          in registers (ex2 / sqrt on the SFU)
-//   O  += K V_J          FP32 FMAs in registers (this file: m <= 8 columns)
-// K never reaches global memory.  Warp roles: warp 0 loads tiles (TMA for the
-// split operands, plain loads for norms and V), warp 1 issues the MMAs,
-// warp 2 owns the TMEM allocation, warps 4..11 (two warpgroups, one half of
-// the tile columns each) run the epilogue.  The S accumulator is double
-// buffered in TMEM so that the MMAs of tile t+1 overlap the epilogue of t.
+// operator is applied without being formed; Sec. 2.1: K_ij = k(x_i, x_j), and
+// every CG iteration costs one O(n^2) product).  Per 128-row block of Q a CTA
+// streams tiles of 128 (or 64) points of X:
+//   S  = Q_I X_J^T       tcgen05.mma on BF16 split operands, FP32 in TMEM
+//   u  = s|q_i|^2 + s|x_j|^2 - 2 s S_ij     (s folds the bandwidth; see
+//                                             kop_epilogue.cuh)
+//   K  = k(u)            in registers (SFU ex2 / sqrt)
+//   O += K V_J           FP32 FMAs, compensated running sum per output
+// K never reaches global memory.  Warp roles: warp 0 issues all loads
+// asynchronously (tensor-map TMA for the split operands, bulk copies for the
+// scaled norms and V), warp 1 issues the MMAs, warp 2 owns TMEM, warps 4..11
+// (two warpgroups, one half of the tile columns each) run the epilogue.  The
+// S accumulator is double-buffered in TMEM so that the MMAs of tile t+1
+// overlap the epilogue of tile t.
 #include "kop_device.cuh"
+#include "kop_epilogue.cuh"
 #include "kop_internal.h"
 
 namespace kop {
 
 constexpr int K1_THREADS = 384;
-constexpr int K1_NST = 2;  // smem pipeline stages (2 CTAs fit per SM for d <= 64)
-
-template <int KF>
-KOP_DEV float kernel_value(float d2, float c0, float c1, float c2) {
-  if constexpr (KF == KF_RBF) {
-    return ex2_approx(d2 * c0);
-  } else if constexpr (KF == KF_LAPLACE) {
-    return ex2_approx(sqrt_approx(d2) * c0);
-  } else if constexpr (KF == KF_MATERN) {
-    float a = sqrt_approx(d2) * c1;
-    return fmaf(a, fmaf(a, 1.0f / 3.0f, 1.0f), 1.0f) * ex2_approx(a * c0);
-  } else if constexpr (KF == KF_DRBF) {
-    return ex2_approx(d2 * c0) * d2 * c2;
-  } else if constexpr (KF == KF_DLAPLACE) {
-    float r = sqrt_approx(d2);
-    return ex2_approx(r * c0) * r * c2;
-  } else {
-    float a = sqrt_approx(d2) * c1;
-    return ex2_approx(a * c0) * (a * a * (1.0f / 3.0f)) * (1.0f + a) * c2;
-  }
-}
+constexpr int K1_MAXST = 4;
 
 struct FusedArgs {
-  const float* qnorm;  // padded to the Q block grid
-  const float* knorm;  // padded to the X tile grid
-  const float* V;
+  const float* qnorm;  // scaled row norms of Q, padded to the 128-row grid
+  const float* knorm;  // scaled row norms of X, padded
+  const float* V;      // nk x MV floats (row stride MV), 16-byte aligned
   float* O;
-  int nq, nk, m, ldv, ldo;
-  int dp, row_bytes, swz, self;
-  float c0, c1, c2;
+  int nq, nk, m, ldo;
+  int dp, row_bytes, swz, self, nst;
+  int v_padded;        // V has n_pad rows (else the last tile copies only nk - j0 rows)
+  float m2c, c2;       // -2 s, derivative factor
   int* status;
 };
 
-// Shared-memory layout of the FMA-epilogue kernel (offsets from a 1024-byte
-// aligned base).
+// Shared-memory layout (offsets from a 1024-byte aligned base).
 struct K1Layout {
-  uint32_t q_split, x_split, qs, xs, kn, vs, qn, bars, holder, abort_word, red, total;
-  __host__ __device__ K1Layout(int nsplit, int dp, int bn, int mv) {
+  uint32_t q_split, x_split, qs, xs, kn, vs, bars, holder, abort_word, red, total;
+  __host__ __device__ K1Layout(int nsplit, int dp, int bn, int mv, int nst) {
     q_split = 128u * dp * 2;
     x_split = (uint32_t)bn * dp * 2;
     qs = 0;
     xs = qs + nsplit * q_split;
-    kn = xs + K1_NST * nsplit * x_split;
-    vs = kn + K1_NST * bn * 4;
-    qn = vs + K1_NST * bn * mv * 4;
-    bars = qn + 128 * 4;
-    holder = bars + (2 * K1_NST + 6) * 8;
+    kn = xs + nst * nsplit * x_split;
+    vs = kn + nst * bn * 4;
+    bars = vs + nst * bn * mv * 4;
+    holder = bars + (2 * K1_MAXST + 6) * 8;
     abort_word = holder + 4;
     red = abort_word + 12;
     total = red + 128 * mv * 2 * 4;
@@ -105,24 +87,88 @@ KOP_DEV constexpr int term_b(int t) {
   return NSPLIT == 2 ? (t == 0 ? 1 : 0) : (t == 0 ? 1 : t == 1 ? 2 : t == 3 ? 1 : 0);
 }
 
+// Epilogue over one 32-column chunk.  MASK: check the diagonal and the ragged
+// tail per entry (only the tiles that need it take this path).  COMP: exact
+// products and error-free sums per entry (TwoProduct + TwoSum into part /
+// perr), used by the accurate mode so that the true residual is not limited by
+// the rounding of FP32 partial sums.
+template <int KF, int MV, bool MASK, bool COMP>
+KOP_DEV void chunk_fma(const uint32_t (&r)[32], float qn, const float* __restrict__ kn, const float* __restrict__ v,
+                       float m2c, float c2, int jbase, int gi, int nk, bool self, float (&part)[MV],
+                       float (&perr)[MV]) {
+#pragma unroll
+  for (int j4 = 0; j4 < 32; j4 += 4) {
+    const float4 k4 = *reinterpret_cast<const float4*>(kn + j4);
+    const float kk[4] = {k4.x, k4.y, k4.z, k4.w};
+    float vv[4][MV];
+    if constexpr (MV == 1) {
+      const float4 v4 = *reinterpret_cast<const float4*>(v + j4);
+      vv[0][0] = v4.x;
+      vv[1][0] = v4.y;
+      vv[2][0] = v4.z;
+      vv[3][0] = v4.w;
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+#pragma unroll
+        for (int c4 = 0; c4 < MV; c4 += 4) {
+          const float4 v4 = *reinterpret_cast<const float4*>(v + (j4 + e) * MV + c4);
+          vv[e][c4] = v4.x;
+          vv[e][c4 + 1] = v4.y;
+          vv[e][c4 + 2] = v4.z;
+          vv[e][c4 + 3] = v4.w;
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int jj = j4 + e;
+      float u = fmaf(__uint_as_float(r[jj]), m2c, qn + kk[e]);
+      if constexpr (MASK) {
+        if (self && jbase + jj == gi) u = 0.0f;
+      }
+      float kv = kval_u<KF>(u, c2);
+      if constexpr (MASK) {
+        if (jbase + jj >= nk) kv = 0.0f;
+      }
+#pragma unroll
+      for (int c = 0; c < MV; ++c) {
+        float vc = vv[e][c];
+        if constexpr (MASK) {
+          if (jbase + jj >= nk) vc = 0.0f;
+        }
+        if constexpr (COMP) {
+          const float p = kv * vc;
+          const float pe = fmaf(kv, vc, -p);
+          const float t = part[c] + p;
+          const float bb = t - part[c];
+          perr[c] += ((part[c] - (t - bb)) + (p - bb)) + pe;
+          part[c] = t;
+        } else {
+          part[c] = fmaf(kv, vc, part[c]);
+        }
+      }
+    }
+  }
+}
+
 template <int KF, int NSPLIT, int MV, int BN>
-__global__ void __launch_bounds__(K1_THREADS, 1)
+__global__ void __launch_bounds__(K1_THREADS, MV <= 4 ? 2 : 1)
     k1_fma_kernel(const __grid_constant__ CUtensorMap tq0, const __grid_constant__ CUtensorMap tq1,
                   const __grid_constant__ CUtensorMap tq2, const __grid_constant__ CUtensorMap tk0,
                   const __grid_constant__ CUtensorMap tk1, const __grid_constant__ CUtensorMap tk2,
                   const FusedArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  const K1Layout L(NSPLIT, a.dp, BN, MV);
+  const int nst = a.nst;
+  const K1Layout L(NSPLIT, a.dp, BN, MV, nst);
   uint8_t* qs = smem + L.qs;
   uint8_t* xs = smem + L.xs;
   float* kn = (float*)(smem + L.kn);
   float* vs = (float*)(smem + L.vs);
-  float* qn = (float*)(smem + L.qn);
   uint64_t* bars = (uint64_t*)(smem + L.bars);
   uint64_t* full = bars;
-  uint64_t* empty = bars + K1_NST;
-  uint64_t* tfull = bars + 2 * K1_NST;
+  uint64_t* empty = bars + K1_MAXST;
+  uint64_t* tfull = bars + 2 * K1_MAXST;
   uint64_t* tempty = tfull + 2;
   uint64_t* qbar = tempty + 2;
   uint64_t* drain = qbar + 1;
@@ -137,7 +183,7 @@ __global__ void __launch_bounds__(K1_THREADS, 1)
   const int nsub = (a.dp * 2) / rb;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < K1_NST; ++s) {
+    for (int s = 0; s < nst; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1 + 256);
     }
@@ -163,8 +209,6 @@ __global__ void __launch_bounds__(K1_THREADS, 1)
     // ------------------------------------------------------------ producer
     const CUtensorMap* mq[3] = {&tq0, &tq1, &tq2};
     const CUtensorMap* mk[3] = {&tk0, &tk1, &tk2};
-    for (int i = lane; i < 128; i += 32) qn[i] = a.qnorm[row0 + i];
-    __syncwarp();
     if (lane == 0) {
       mbar_arrive_expect_tx(qbar, NSPLIT * L.q_split);
       for (int sp = 0; sp < NSPLIT; ++sp)
@@ -175,27 +219,25 @@ __global__ void __launch_bounds__(K1_THREADS, 1)
     }
     int t = 0;
     for (; t < ntiles; ++t) {
-      const int s = t % K1_NST;
-      const uint32_t ph = (t / K1_NST) & 1;
+      const int s = t % nst;
+      const uint32_t ph = (t / nst) & 1;
       if (!warp_wait(&empty[s], ph ^ 1, abort_word, a.status)) break;
-      const int j0 = t * BN;
-      for (int i = lane; i < BN; i += 32) kn[s * BN + i] = a.knorm[j0 + i];
-      for (int i = lane; i < BN * MV; i += 32) {
-        const int jj = i / MV, c = i - jj * MV, j = j0 + jj;
-        vs[s * BN * MV + i] = (j < a.nk && c < a.m) ? a.V[(int64_t)j * a.ldv + c] : 0.0f;
-      }
-      __syncwarp();
       if (lane == 0) {
-        mbar_arrive_expect_tx(&full[s], NSPLIT * L.x_split);
+        const int j0 = t * BN;
+        const int rows_v = a.v_padded ? BN : (a.nk - j0 < BN ? a.nk - j0 : BN);
+        const uint32_t vbytes = (uint32_t)rows_v * MV * 4;
+        mbar_arrive_expect_tx(&full[s], NSPLIT * L.x_split + BN * 4 + vbytes);
         for (int sp = 0; sp < NSPLIT; ++sp)
           for (int ks = 0; ks < nsub; ++ks)
             tma_load_2d(xs + (s * NSPLIT + sp) * L.x_split + ks * (BN * rb), mk[sp], &full[s], ks * 64, j0);
+        bulk_load(kn + s * BN, a.knorm + j0, BN * 4, &full[s]);
+        bulk_load(vs + s * BN * MV, a.V + (int64_t)j0 * MV, vbytes, &full[s]);
       }
       __syncwarp();
     }
     if (t < ntiles && lane == 0) {
       // aborted: let the loads already issued land before the CTA exits
-      for (int u = (t - K1_NST > 0 ? t - K1_NST : 0); u < t; ++u) drain_wait(&full[u % K1_NST], (u / K1_NST) & 1);
+      for (int u = (t - nst > 0 ? t - nst : 0); u < t; ++u) drain_wait(&full[u % nst], (u / nst) & 1);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
@@ -204,8 +246,8 @@ __global__ void __launch_bounds__(K1_THREADS, 1)
     const int steps_per_sub = rb / 32;
     bool ok = warp_wait(qbar, 0, abort_word, a.status);
     for (int t = 0; ok && t < ntiles; ++t) {
-      const int s = t % K1_NST;
-      const uint32_t ph = (t / K1_NST) & 1;
+      const int s = t % nst;
+      const uint32_t ph = (t / nst) & 1;
       const int b = t & 1;
       const uint32_t bph = (t >> 1) & 1;
       if (!warp_wait(&full[s], ph, abort_word, a.status)) break;
@@ -244,49 +286,46 @@ __global__ void __launch_bounds__(K1_THREADS, 1)
     const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
     constexpr int HALF = BN / 2;
     constexpr int NCH = HALF / 32;
+    const float qn = a.qnorm[gi];
+    const bool self = a.self != 0;
     float acc_s[MV], acc_e[MV];
 #pragma unroll
     for (int c = 0; c < MV; ++c) acc_s[c] = acc_e[c] = 0.0f;
-    bool ok = warp_wait(qbar, 0, abort_word, a.status);
-    const float qni = qn[row];
-    for (int t = 0; ok && t < ntiles; ++t) {
-      const int s = t % K1_NST;
-      const uint32_t ph = (t / K1_NST) & 1;
+    for (int t = 0; t < ntiles; ++t) {
+      const int s = t % nst;
+      const uint32_t ph = (t / nst) & 1;
       const int b = t & 1;
       const uint32_t bph = (t >> 1) & 1;
       if (!warp_wait(&tfull[b], bph, abort_word, a.status)) break;
       tc_fence_after();
-      uint32_t r[NCH][32];
+      if (!warp_wait(&full[s], ph, abort_word, a.status)) break;
+      const int j0 = t * BN;
+      const bool mask = (self && j0 < row0 + 128 && j0 + BN > row0) || (j0 + BN > a.nk);
+      constexpr bool COMP = NSPLIT == 3;
+      float part[MV], perr[MV];
+#pragma unroll
+      for (int c = 0; c < MV; ++c) part[c] = perr[c] = 0.0f;
 #pragma unroll
       for (int ch = 0; ch < NCH; ++ch) {
-        tmem_ld32(lane_addr + b * BN + wg * HALF + ch * 32, r[ch]);
-        tmem_ld_wait(r[ch]);
+        const int col = wg * HALF + ch * 32;
+        uint32_t r[32];
+        tmem_ld32(lane_addr + b * BN + col, r);
+        tmem_ld_wait(r);
+        const float* knS = kn + s * BN + col;
+        const float* vS = vs + (s * BN + col) * MV;
+        if (mask)
+          chunk_fma<KF, MV, true, COMP>(r, qn, knS, vS, a.m2c, a.c2, j0 + col, gi, a.nk, self, part, perr);
+        else
+          chunk_fma<KF, MV, false, COMP>(r, qn, knS, vS, a.m2c, a.c2, j0 + col, gi, a.nk, self, part, perr);
       }
       tc_fence_before();
       mbar_arrive(&tempty[b]);
-      if (!warp_wait(&full[s], ph, abort_word, a.status)) break;
-      const float* knS = kn + s * BN + wg * HALF;
-      const float* vS = vs + (s * BN + wg * HALF) * MV;
-      const int jbase = t * BN + wg * HALF;
-      float part[MV];
-#pragma unroll
-      for (int c = 0; c < MV; ++c) part[c] = 0.0f;
-#pragma unroll
-      for (int ch = 0; ch < NCH; ++ch) {
-#pragma unroll
-        for (int jj = 0; jj < 32; ++jj) {
-          const int jl = ch * 32 + jj;
-          const float sij = __uint_as_float(r[ch][jj]);
-          float d2 = fmaxf(fmaf(-2.0f, sij, qni + knS[jl]), 0.0f);
-          if (a.self && jbase + jl == gi) d2 = 0.0f;
-          const float kv = kernel_value<KF>(d2, a.c0, a.c1, a.c2);
-#pragma unroll
-          for (int c = 0; c < MV; ++c) part[c] = fmaf(kv, vS[jl * MV + c], part[c]);
-        }
-      }
       mbar_arrive(&empty[s]);
 #pragma unroll
-      for (int c = 0; c < MV; ++c) two_sum_acc(acc_s[c], acc_e[c], part[c]);
+      for (int c = 0; c < MV; ++c) {
+        two_sum_acc(acc_s[c], acc_e[c], part[c]);
+        acc_e[c] += perr[c];
+      }
     }
     if (wg == 1) {
 #pragma unroll
@@ -315,14 +354,29 @@ __global__ void __launch_bounds__(K1_THREADS, 1)
   }
 }
 
+// V (n x m, ld ldv) -> padded n_pad x mv block (zero rows / columns).
+__global__ void vpad_kernel(const float* __restrict__ V, int64_t n, int m, int ldv, int64_t n_pad, int mv,
+                            float* __restrict__ out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_pad * mv) return;
+  const int64_t i = t / mv;
+  const int c = (int)(t - i * mv);
+  out[t] = (i < n && c < m) ? V[i * ldv + c] : 0.0f;
+}
+
 // ---------------------------------------------------------------- host side
 static int swizzle_code(int row_bytes) { return row_bytes == 128 ? 2 : (row_bytes == 64 ? 4 : 6); }
+
+size_t fma_smem_bytes(int nsplit, int dp, int bn, int mv, int nst) {
+  return K1Layout(nsplit, dp, bn, mv, nst).total + 1024;
+}
 
 template <int KF, int NSPLIT, int MV, int BN>
 static int launch_fma_t(const PointSet& Q, const PointSet& Ks, const FusedArgs& a, cudaStream_t st) {
   auto kern = k1_fma_kernel<KF, NSPLIT, MV, BN>;
-  const K1Layout L(NSPLIT, a.dp, BN, MV);
-  const size_t smem = L.total + 1024;
+  size_t smem = fma_smem_bytes(NSPLIT, a.dp, BN, MV, a.nst);
+  // at most two CTAs per SM (TMEM: 256 columns each)
+  if (smem < 80 * 1024) smem = 80 * 1024;
   static bool attr_set = false;
   if (!attr_set) {
     KOP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_limit_bytes()));
@@ -351,40 +405,66 @@ static int launch_fma_kf(int nsplit, int bn, int mv, const PointSet& Q, const Po
   return bn == 128 ? launch_fma_mv<KF, 3, 128>(mv, Q, Ks, a, st) : launch_fma_mv<KF, 3, 64>(mv, Q, Ks, a, st);
 }
 
-size_t fma_smem_bytes(int nsplit, int dp, int bn, int mv) { return K1Layout(nsplit, dp, bn, mv).total + 1024; }
-
 int fused_matvec(const PointSet& Q, const PointSet& Ks, bool self, int kf, const KConst& kc, int nsplit,
                  const float* V, int m, int ldv, float* O, int ldo, int* status, cudaStream_t st) {
   if (Q.dp != Ks.dp) return fail(KOP_EINVAL, "fused_matvec: point sets of different widths");
   if (Q.n == 0 || Ks.n == 0 || m == 0) return KOP_OK;
   if (m > 8 && nsplit == 2) return fused_matvec_mma(Q, Ks, self, kf, kc, V, m, ldv, O, ldo, status, st);
   const int dp = Q.dp;
-  int bn = 128;
-  if (fma_smem_bytes(nsplit, dp, 128, 8) > smem_limit_bytes()) bn = 64;
-  if (fma_smem_bytes(nsplit, dp, bn, 8) > smem_limit_bytes())
+  const size_t lim = smem_limit_bytes();
+  // tile width and pipeline depth: two CTAs per SM when a 2-stage pipeline
+  // fits in half the shared memory (deeper if it still fits), else one CTA
+  // with three stages
+  int bn = 128, nst = 2;
+  if (fma_smem_bytes(nsplit, dp, 128, 8, 2) > lim) bn = 64;
+  if (fma_smem_bytes(nsplit, dp, bn, 8, 2) > lim)
     return fail(KOP_EINVAL, "fused_matvec: feature width too large for the fused kernel");
+  if (fma_smem_bytes(nsplit, dp, bn, 8, 2) <= lim / 2) {
+    while (nst < K1_MAXST && fma_smem_bytes(nsplit, dp, bn, 8, nst + 1) <= lim / 2) ++nst;
+  } else if (fma_smem_bytes(nsplit, dp, bn, 8, 3) <= lim) {
+    nst = 3;
+  }
+  int rc = ensure_scaled_norms(const_cast<PointSet&>(Q), kc.scale, st);
+  if (rc == KOP_OK && &Q != &Ks) rc = ensure_scaled_norms(const_cast<PointSet&>(Ks), kc.scale, st);
+  if (rc) return rc;
   FusedArgs a;
-  a.qnorm = Q.norms;
-  a.knorm = Ks.norms;
+  a.qnorm = Q.snorm;
+  a.knorm = Ks.snorm;
   a.nq = (int)Q.n;
   a.nk = (int)Ks.n;
-  a.ldv = ldv;
   a.ldo = ldo;
   a.dp = dp;
   a.row_bytes = dp >= 64 ? 128 : dp * 2;
   a.swz = swizzle_code(a.row_bytes);
   a.self = self ? 1 : 0;
-  a.c0 = kc.c0;
-  a.c1 = kc.c1;
+  a.nst = nst;
+  a.m2c = -2.0f * kc.scale;
   a.c2 = kc.c2;
   a.status = status;
-  for (int c0 = 0; c0 < m; c0 += 8) {
+  float* vpad = nullptr;
+  for (int c0 = 0; c0 < m && rc == KOP_OK; c0 += 8) {
     const int mc = (m - c0) < 8 ? (m - c0) : 8;
     const int mv = mc == 1 ? 1 : (mc <= 4 ? 4 : 8);
-    a.V = V + c0;
+    // V is read with bulk copies: used in place when its rows are exactly mv
+    // floats and 16-byte aligned, else staged in a padded copy
+    const bool direct = (mc == mv) && (ldv == mv) && (c0 == 0) && ((uintptr_t)V % 16 == 0) &&
+                        (((int64_t)Ks.n * mv * 4) % 16 == 0);
+    if (direct) {
+      a.V = V;
+      a.v_padded = 0;
+    } else {
+      if (!vpad) {
+        cudaError_t e = cudaMallocAsync((void**)&vpad, sizeof(float) * Ks.n_pad * 8, st);
+        if (e != cudaSuccess) return cuda_fail(e, "fused_matvec: V staging");
+      }
+      const int64_t tot = Ks.n_pad * mv;
+      vpad_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(V + c0, Ks.n, mc, ldv, Ks.n_pad, mv, vpad);
+      KOP_LAUNCHED();
+      a.V = vpad;
+      a.v_padded = 1;
+    }
     a.O = O + c0;
     a.m = mc;
-    int rc;
     switch (kf) {
       case KF_RBF: rc = launch_fma_kf<KF_RBF>(nsplit, bn, mv, Q, Ks, a, st); break;
       case KF_LAPLACE: rc = launch_fma_kf<KF_LAPLACE>(nsplit, bn, mv, Q, Ks, a, st); break;
@@ -393,9 +473,9 @@ int fused_matvec(const PointSet& Q, const PointSet& Ks, bool self, int kf, const
       case KF_DLAPLACE: rc = launch_fma_kf<KF_DLAPLACE>(nsplit, bn, mv, Q, Ks, a, st); break;
       default: rc = launch_fma_kf<KF_DMATERN>(nsplit, bn, mv, Q, Ks, a, st); break;
     }
-    if (rc != KOP_OK) return rc;
   }
-  return KOP_OK;
+  if (vpad) cudaFreeAsync(vpad, st);
+  return rc;
 }
 
 }  // namespace kop

@@ -11,6 +11,7 @@
 // from shared memory.  O (128 rows x MC columns, FP32) stays in TMEM for the
 // whole sweep over X and is written once at the end.  Tiles of 64 points.
 #include "kop_device.cuh"
+#include "kop_epilogue.cuh"
 #include "kop_internal.h"
 
 namespace kop {
@@ -19,33 +20,13 @@ constexpr int K3_THREADS = 384;
 constexpr int K3_NST = 2;
 constexpr int K3_BN = 64;
 
-template <int KF>
-KOP_DEV float kernel_value_mma(float d2, float c0, float c1, float c2) {
-  if constexpr (KF == KF_RBF) {
-    return ex2_approx(d2 * c0);
-  } else if constexpr (KF == KF_LAPLACE) {
-    return ex2_approx(sqrt_approx(d2) * c0);
-  } else if constexpr (KF == KF_MATERN) {
-    float a = sqrt_approx(d2) * c1;
-    return fmaf(a, fmaf(a, 1.0f / 3.0f, 1.0f), 1.0f) * ex2_approx(a * c0);
-  } else if constexpr (KF == KF_DRBF) {
-    return ex2_approx(d2 * c0) * d2 * c2;
-  } else if constexpr (KF == KF_DLAPLACE) {
-    float r = sqrt_approx(d2);
-    return ex2_approx(r * c0) * r * c2;
-  } else {
-    float a = sqrt_approx(d2) * c1;
-    return ex2_approx(a * c0) * (a * a * (1.0f / 3.0f)) * (1.0f + a) * c2;
-  }
-}
-
 struct MmaArgs {
   const float* qnorm;
   const float* knorm;
   float* O;
   int nq, nk, m, ldo;
   int dp, row_bytes, swz, self, mc, tcols;
-  float c0, c1, c2;
+  float m2c, c2;
   int* status;
 };
 
@@ -271,9 +252,9 @@ __global__ void __launch_bounds__(K3_THREADS, 1)
       float kv[32];
 #pragma unroll
       for (int jj = 0; jj < 32; ++jj) {
-        float d2 = fmaxf(fmaf(-2.0f, __uint_as_float(r[jj]), qni + knS[jj]), 0.0f);
-        if (a.self && jbase + jj == gi) d2 = 0.0f;
-        kv[jj] = (jbase + jj < a.nk) ? kernel_value_mma<KF>(d2, a.c0, a.c1, a.c2) : 0.0f;
+        float u = fmaf(__uint_as_float(r[jj]), a.m2c, qni + knS[jj]);
+        if (a.self && jbase + jj == gi) u = 0.0f;
+        kv[jj] = (jbase + jj < a.nk) ? kval_u<KF>(u, a.c2) : 0.0f;
       }
       mbar_arrive(&empty[s]);
       uint32_t ph16[16], pl16[16];
@@ -372,6 +353,11 @@ int fused_matvec_mma(const PointSet& Q, const PointSet& Ks, bool self, int kf, c
                      int m, int ldv, float* O, int ldo, int* status, cudaStream_t st) {
   const int mc = mma_chunk(Q.dp, m);
   if (mc == 0) return fail(KOP_EINVAL, "fused_matvec_mma: feature width too large");
+  {
+    int sc = ensure_scaled_norms(const_cast<PointSet&>(Q), kc.scale, st);
+    if (sc == KOP_OK && &Q != &Ks) sc = ensure_scaled_norms(const_cast<PointSet&>(Ks), kc.scale, st);
+    if (sc) return sc;
+  }
   const int nch = (m + mc - 1) / mc;
   const int m_pad = nch * mc;
   const int64_t nk_pad = Ks.n_pad;
@@ -388,8 +374,8 @@ int fused_matvec_mma(const PointSet& Q, const PointSet& Ks, bool self, int kf, c
   if (rc == KOP_OK) rc = encode_tmap_bf16(&tv[1], vl, m_pad, (int)nk_pad, 64, mc);
   if (rc == KOP_OK) {
     MmaArgs a;
-    a.qnorm = Q.norms;
-    a.knorm = Ks.norms;
+    a.qnorm = Q.snorm;
+    a.knorm = Ks.snorm;
     a.O = O;
     a.nq = (int)Q.n;
     a.nk = (int)Ks.n;
@@ -401,8 +387,7 @@ int fused_matvec_mma(const PointSet& Q, const PointSet& Ks, bool self, int kf, c
     a.self = self ? 1 : 0;
     a.mc = mc;
     a.tcols = (2 * K3_BN + mc) <= 256 ? 256 : 512;
-    a.c0 = kc.c0;
-    a.c1 = kc.c1;
+    a.m2c = -2.0f * kc.scale;
     a.c2 = kc.c2;
     a.status = status;
     switch (kf) {

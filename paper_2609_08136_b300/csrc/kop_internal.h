@@ -16,9 +16,11 @@ namespace kop {
 // (enum kop_kernel), 3..5 its derivative with respect to the bandwidth.
 enum { KF_RBF = 0, KF_LAPLACE = 1, KF_MATERN = 2, KF_DRBF = 3, KF_DLAPLACE = 4, KF_DMATERN = 5 };
 
+// Constants of the fused epilogue (kop_epilogue.cuh): the kernel sees
+// u = scale * D2 and, for derivatives, multiplies by c2.
 struct KConst {
-  float c0, c1, c2;  // fused-epilogue constants (exp2 form)
-  double bw;         // bandwidth itself
+  float scale, c2;
+  double bw;  // bandwidth itself (plain path)
 };
 KConst kernel_constants(int kind, double bw);
 
@@ -32,7 +34,12 @@ struct PointSet {
   __nv_bfloat16* sp[3] = {nullptr, nullptr, nullptr};
   CUtensorMap tm[3][2];  // [split][0: 128-row boxes, 1: 64-row boxes]
   void* block = nullptr;
+  float* xorig = nullptr;  // the caller's points, n x d FP32 (exact operator)
+  float* snorm = nullptr;  // scale * norms (n_pad), built on demand
+  float snorm_scale = 0.0f;
 };
+// Make ps.snorm = scale * ps.norms (no-op if already built for this scale).
+int ensure_scaled_norms(PointSet& ps, float scale, cudaStream_t st);
 
 int padded_dim(int d);
 int pointset_alloc(PointSet& ps, int64_t n, int d, cudaStream_t st);
@@ -54,6 +61,11 @@ int fused_matvec_mma(const PointSet& Q, const PointSet& Ks, bool self, int kf, c
 int plain_matvec(const PointSet& Q, const PointSet& Ks, bool self, int kf, const KConst& kc, const float* V,
                  int m, int ldv, float* O, int ldo, cudaStream_t st);
 
+// FP64 CUDA-core operator (KOP_EXACT): FP64 V and O, and an FP32 wrapper.
+int exact_matvec(const PointSet& Q, const PointSet& Ks, int kf, double bw, const double* V, int m, int ldv, double* O,
+                 int ldo, cudaStream_t st);
+int exact_matvec_f32(const PointSet& Q, const PointSet& Ks, int kf, double bw, const float* V, int m, int ldv,
+                     float* O, int ldo, cudaStream_t st);
 // Any mode.
 int op_matvec(const PointSet& Q, const PointSet& Ks, bool self, int kf, const KConst& kc, int mode,
               const float* V, int m, int ldv, float* O, int ldo, int* status, cudaStream_t st);
@@ -83,7 +95,7 @@ void note_launch();
 namespace kop {
 // Device part of nys_apply (scratch from the caller; see kop_nystrom.cu).
 int nys_apply_dev(const nys_s* ny, const double* mu_dev, int adaptive, const float* V, int m, float* O, double* Wd,
-                  float* Wf, float* alpha, cudaStream_t st);
+                  double* alpha, float* Wf, float* alpha_f, cudaStream_t st);
 }  // namespace kop
 
 struct kop_s {

@@ -32,35 +32,49 @@ struct DevBuf {
 // Per-column damping of the preconditioner apply.
 //   d_k(c) = 1 / (lam_k + mu_c) - 1 / rho_c,   alpha_c = 1 / rho_c,
 //   rho_c = lam_r + mu_c (adaptive) or mu_c.
-__global__ void nys_scale_kernel(const double* __restrict__ W, int r, int m, const double* __restrict__ lam,
+// W (r x m) is scaled in place; an FP32 copy is written when Wf != NULL.
+__global__ void nys_scale_kernel(double* __restrict__ W, int r, int m, const double* __restrict__ lam,
                                  const double* __restrict__ mu, int adaptive, float* __restrict__ Wf,
-                                 float* __restrict__ alpha) {
+                                 double* __restrict__ alpha, float* __restrict__ alpha_f) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)r * m) return;
   const int k = (int)(t / m), c = (int)(t - (int64_t)k * m);
   const double rho = adaptive ? lam[r - 1] + mu[c] : mu[c];
-  Wf[t] = (float)(W[t] * (1.0 / (lam[k] + mu[c]) - 1.0 / rho));
-  if (k == 0) alpha[c] = (float)(1.0 / rho);
+  const double w = W[t] * (1.0 / (lam[k] + mu[c]) - 1.0 / rho);
+  W[t] = w;
+  if (Wf) Wf[t] = (float)w;
+  if (k == 0) {
+    alpha[c] = 1.0 / rho;
+    if (alpha_f) alpha_f[c] = (float)(1.0 / rho);
+  }
 }
 
 // Device side of nys_apply with caller-provided scratch:
-//   Wd: r*m doubles, Wf: r*m floats, alpha: m floats, mu_dev: m doubles.
+//   Wd: r*m doubles, alpha: m doubles, Wf: r*m floats, alpha_f: m floats.
+// Up to 8 columns the whole apply runs in FP64 arithmetic on the stored FP32
+// U, so that P^-1 is applied as one fixed symmetric operator: in FP32 the
+// cancellation between v / rho and the projected part loses a factor
+// (lam_1 + mu) / rho of accuracy on the leading subspace.  Wider blocks use
+// FP32 tensor-shaped products (the solver tolerates the inexact apply).
 int nys_apply_dev(const nys_s* ny, const double* mu_dev, int adaptive, const float* V, int m, float* O, double* Wd,
-                  float* Wf, float* alpha, cudaStream_t st) {
+                  double* alpha, float* Wf, float* alpha_f, cudaStream_t st) {
   const int r = ny->r;
   const int64_t n = ny->n;
-  if (m == 1) {
-    int rc = utv(ny->U, r, n, r, V, 1, Wd, st);
-    if (rc) return rc;
-  } else {
-    int rc = gram(ny->U, r, V, m, n, r, m, Wd, m, st);
-    if (rc) return rc;
-  }
   const int64_t tot = (int64_t)r * m;
-  nys_scale_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(Wd, r, m, ny->lam_dev, mu_dev, adaptive, Wf, alpha);
+  if (m <= 8) {
+    int rc = utv64(ny->U, r, n, r, V, m, Wd, st);
+    if (rc) return rc;
+    nys_scale_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(Wd, r, m, ny->lam_dev, mu_dev, adaptive, nullptr,
+                                                                    alpha, nullptr);
+    KOP_LAUNCHED();
+    return uw64(ny->U, r, n, r, Wd, V, m, alpha, O, st);
+  }
+  int rc = gram(ny->U, r, V, m, n, r, m, Wd, m, st);
+  if (rc) return rc;
+  nys_scale_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(Wd, r, m, ny->lam_dev, mu_dev, adaptive, Wf, alpha,
+                                                                  alpha_f);
   KOP_LAUNCHED();
-  if (m == 1) return uw(ny->U, r, n, r, Wf, V, 1, alpha, O, 1, st);
-  return tall_gemm(ny->U, nullptr, 0.0f, r, n, r, Wf, m, m, V, m, alpha, O, m, st);
+  return tall_gemm(ny->U, nullptr, 0.0f, r, n, r, Wf, m, m, V, m, alpha_f, O, m, st);
 }
 
 static int read_info(const int* dev, int* host, cudaStream_t st) {
@@ -80,7 +94,7 @@ extern "C" int nys_build(kop_t op, const float* Omega, int32_t r, double nu_rel,
   if (!op || !Omega) return fail(KOP_EINVAL, "nys_build: NULL argument");
   const int64_t n = op->pts.n;
   if (r < 1 || r > 2048 || r > n) return fail(KOP_EINVAL, "nys_build: r must be in [1, min(n, 2048)]");
-  if (mode != KOP_FAST && mode != KOP_ACCURATE && mode != KOP_PLAIN) return fail(KOP_EINVAL, "nys_build: bad mode");
+  if (mode < KOP_FAST || mode > KOP_EXACT) return fail(KOP_EINVAL, "nys_build: bad mode");
   if (!std::isfinite(nu_rel)) return fail(KOP_EINVAL, "nys_build: nu_rel must be finite");
   cudaStream_t st = (cudaStream_t)stream;
   if (!(nu_rel > 0.0)) nu_rel = mode == KOP_FAST ? std::ldexp(1.0, -16) : std::ldexp(1.0, -21);
@@ -242,13 +256,14 @@ extern "C" int nys_apply(nys_t ny, const double* mu, int32_t adaptive, const flo
   const size_t r = ny->r;
   DevBuf ws;
   ws.st = st;
-  KOP_CUDA_TRY(cudaMallocAsync(&ws.p, sizeof(double) * (r * m + m) + sizeof(float) * (r * m + m), st));
+  KOP_CUDA_TRY(cudaMallocAsync(&ws.p, sizeof(double) * (r * m + 2 * m) + sizeof(float) * (r * m + m), st));
   double* Wd = (double*)ws.p;
   double* mu_dev = Wd + r * m;
-  float* Wf = (float*)(mu_dev + m);
-  float* alpha = Wf + r * m;
+  double* alpha = mu_dev + m;
+  float* Wf = (float*)(alpha + m);
+  float* alpha_f = Wf + r * m;
   KOP_CUDA_TRY(cudaMemcpyAsync(mu_dev, mu, sizeof(double) * m, cudaMemcpyHostToDevice, st));
-  const int rc = nys_apply_dev(ny, mu_dev, adaptive, V, m, O, Wd, Wf, alpha, st);
+  const int rc = nys_apply_dev(ny, mu_dev, adaptive, V, m, O, Wd, alpha, Wf, alpha_f, st);
   KOP_CUDA_TRY(cudaStreamSynchronize(st));
   return rc;
 }

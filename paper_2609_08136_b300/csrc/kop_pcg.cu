@@ -4,8 +4,11 @@
 // PCG as in Hestenes & Stiefel (cited in the paper's Sec. 5.1), started from
 // x0 = 0:  r = b, z = P^-1 r, p = z;  per iteration
 //   q = (K + lam I) p,  alpha = r^T z / p^T q,  x += alpha p,  r -= alpha q,
-//   stop if ||r|| <= tol ||b||,  z = P^-1 r,  beta = r^T z_new / r^T z_old,
+//   stop if ||r|| <= tol ||b||,  z = P^-1 r,  beta = -z^T q / p^T q,
 //   p = z + beta p.
+// This beta is the flexible (Polak-Ribiere / Notay FCG(1)) form; with an
+// exact symmetric preconditioner it equals r^T z_new / r^T z_old, and it
+// keeps the recurrence stable when P^-1 is applied inexactly (FP32 blocks).
 // Every column has its own alpha and beta and stops on its own (App. A.1: the
 // stopping condition must hold for every right-hand side).  The products with
 // K use the fast operator; every `refine_every` iterations, and whenever a
@@ -24,53 +27,74 @@
 
 namespace kop {
 
-enum { OP_INIT = 0, OP_PQ = 1, OP_XR = 2, OP_DOT = 3, OP_P = 4, OP_RES = 5 };
+enum { OP_INIT = 0, OP_PQ = 1, OP_XR = 2, OP_DOT = 3, OP_P = 4, OP_RES = 5, OP_DOT2 = 6, OP_SPLIT = 7, OP_RES64 = 8 };
 
+// The iterate x is accumulated in FP64 (FP32 storage of x alone would limit
+// the attainable FP64 residual to about 2^-24 ||A|| ||x|| / ||b||); p, r, z, q
+// are FP32.  The true residual uses K applied to the exact hi/lo FP32 split
+// of x (two columns per column of x).
 struct VecArgs {
   int64_t n;
   int cols, nrhs;
-  float* X;
+  double* X;
+  float* V2;  // n x 2 cols: [hi | lo] split of X (OP_SPLIT)
   float* R;
   const float* Z;
   float* P;
   float* Q;
   const float* B;  // n x nrhs; column c reads B[:, c % nrhs]
-  const float* T;  // K x (for OP_RES)
+  const float* T;      // n x 2 cols: K applied to the split of X (OP_RES)
+  const double* T64;   // n x cols: K X in FP64 (OP_RES64)
   const double* lam;
   const double* alpha;
   const double* beta;
-  double* acc;  // per column, pre-zeroed
+  double* acc;   // per column, pre-zeroed
+  double* acc2;  // second reduction (OP_DOT2: q^T z)
 };
 
 template <int OP>
-KOP_DEV double vec_elem(const VecArgs& a, int64_t i, int c) {
+KOP_DEV double2 vec_elem(const VecArgs& a, int64_t i, int c) {
   const int64_t e = i * a.cols + c;
   if constexpr (OP == OP_INIT) {
     const float b = a.B[i * a.nrhs + (c % a.nrhs)];
-    a.X[e] = 0.0f;
+    a.X[e] = 0.0;
     a.R[e] = b;
-    return (double)b * b;
+    return make_double2((double)b * b, 0.0);
   } else if constexpr (OP == OP_PQ) {
     const float p = a.P[e];
     const float q = (float)((double)a.Q[e] + a.lam[c] * (double)p);
     a.Q[e] = q;
-    return (double)p * q;
+    return make_double2((double)p * q, 0.0);
   } else if constexpr (OP == OP_XR) {
     const double al = a.alpha[c];
-    a.X[e] = (float)((double)a.X[e] + al * (double)a.P[e]);
+    a.X[e] = a.X[e] + al * (double)a.P[e];
     const float r = (float)((double)a.R[e] - al * (double)a.Q[e]);
     a.R[e] = r;
-    return (double)r * r;
+    return make_double2((double)r * r, 0.0);
   } else if constexpr (OP == OP_DOT) {
-    return (double)a.R[e] * (double)a.Z[e];
+    return make_double2((double)a.R[e] * (double)a.Z[e], 0.0);
+  } else if constexpr (OP == OP_DOT2) {
+    const double z = (double)a.Z[e];
+    return make_double2((double)a.R[e] * z, (double)a.Q[e] * z);
   } else if constexpr (OP == OP_P) {
     a.P[e] = (float)((double)a.Z[e] + a.beta[c] * (double)a.P[e]);
-    return 0.0;
+    return make_double2(0.0, 0.0);
+  } else if constexpr (OP == OP_SPLIT) {
+    const double x = a.X[e];
+    const float hi = (float)x;
+    a.V2[i * 2 * a.cols + c] = hi;
+    a.V2[i * 2 * a.cols + a.cols + c] = (float)(x - (double)hi);
+    return make_double2(0.0, 0.0);
+  } else if constexpr (OP == OP_RES64) {
+    const double r = (double)a.B[i * a.nrhs + (c % a.nrhs)] - a.T64[e] - a.lam[c] * a.X[e];
+    a.R[e] = (float)r;
+    return make_double2(r * r, 0.0);
   } else {
-    const double r = (double)a.B[i * a.nrhs + (c % a.nrhs)] - (double)a.T[e] - a.lam[c] * (double)a.X[e];
-    const float rf = (float)r;
-    a.R[e] = rf;
-    return r * r;
+    const int64_t t = i * 2 * a.cols + c;
+    const double kx = (double)a.T[t] + (double)a.T[t + a.cols];
+    const double r = (double)a.B[i * a.nrhs + (c % a.nrhs)] - kx - a.lam[c] * a.X[e];
+    a.R[e] = (float)r;
+    return make_double2(r * r, 0.0);
   }
 }
 
@@ -78,42 +102,64 @@ KOP_DEV double vec_elem(const VecArgs& a, int64_t i, int c) {
 template <int OP>
 __global__ void __launch_bounds__(256) vec_cols_kernel(VecArgs a) {
   const int c = blockIdx.y * 32 + threadIdx.x;
-  double acc = 0.0;
+  double acc = 0.0, acc2 = 0.0;
   if (c < a.cols)
-    for (int64_t i = (int64_t)blockIdx.x * 8 + threadIdx.y; i < a.n; i += (int64_t)gridDim.x * 8)
-      acc += vec_elem<OP>(a, i, c);
-  if (OP == OP_P) return;
-  __shared__ double red[8][33];
-  red[threadIdx.y][threadIdx.x] = acc;
+    for (int64_t i = (int64_t)blockIdx.x * 8 + threadIdx.y; i < a.n; i += (int64_t)gridDim.x * 8) {
+      const double2 v = vec_elem<OP>(a, i, c);
+      acc += v.x;
+      acc2 += v.y;
+    }
+  if (OP == OP_P || OP == OP_SPLIT) return;
+  __shared__ double red[2][8][33];
+  red[0][threadIdx.y][threadIdx.x] = acc;
+  red[1][threadIdx.y][threadIdx.x] = acc2;
   __syncthreads();
   if (threadIdx.y == 0 && c < a.cols) {
-    double s = 0.0;
-    for (int y = 0; y < 8; ++y) s += red[y][threadIdx.x];
+    double s = 0.0, s2 = 0.0;
+    for (int y = 0; y < 8; ++y) {
+      s += red[0][y][threadIdx.x];
+      s2 += red[1][y][threadIdx.x];
+    }
     atomicAdd(&a.acc[c], s);
+    if (OP == OP_DOT2) atomicAdd(&a.acc2[c], s2);
   }
 }
 
 // One column: flat grid-stride with a block reduction.
 template <int OP>
 __global__ void __launch_bounds__(256) vec_one_kernel(VecArgs a) {
-  double acc = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x)
-    acc += vec_elem<OP>(a, i, 0);
-  if (OP == OP_P) return;
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  __shared__ double red[8];
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  double acc = 0.0, acc2 = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = vec_elem<OP>(a, i, 0);
+    acc += v.x;
+    acc2 += v.y;
+  }
+  if (OP == OP_P || OP == OP_SPLIT) return;
+  for (int o = 16; o > 0; o >>= 1) {
+    acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    acc2 += __shfl_xor_sync(0xffffffffu, acc2, o);
+  }
+  __shared__ double red[2][8];
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = acc;
+    red[1][threadIdx.x >> 5] = acc2;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < 8; ++w) s += red[w];
+    double s = 0.0, s2 = 0.0;
+    for (int w = 0; w < 8; ++w) {
+      s += red[0][w];
+      s2 += red[1][w];
+    }
     atomicAdd(&a.acc[0], s);
+    if (OP == OP_DOT2) atomicAdd(&a.acc2[0], s2);
   }
 }
 
 template <int OP>
 static int vec_launch(const VecArgs& a, cudaStream_t st) {
-  if (OP != OP_P) KOP_CUDA_TRY(cudaMemsetAsync(a.acc, 0, sizeof(double) * a.cols, st));
+  if (OP != OP_P && OP != OP_SPLIT) KOP_CUDA_TRY(cudaMemsetAsync(a.acc, 0, sizeof(double) * a.cols, st));
+  if (OP == OP_DOT2) KOP_CUDA_TRY(cudaMemsetAsync(a.acc2, 0, sizeof(double) * a.cols, st));
   if (a.cols == 1) {
     int64_t blocks = (a.n + 255) / 256;
     const int64_t cap = 8 * num_sms();
@@ -146,18 +192,35 @@ __global__ void fin_alpha_kernel(int cols, const double* rz, const double* pq, c
   alpha[c] = al;
 }
 
-// beta_c = rz_new_c / rz_c, rz_c <- rz_new_c.
-__global__ void fin_beta_kernel(int cols, double* rz, const double* rzn, double* beta) {
+// beta_c = -q_c^T z_c / p_c^T q_c (flexible form), rz_c <- r_c^T z_c.
+__global__ void fin_beta_kernel(int cols, double* rz, const double* rzn, const double* qz, const double* pq,
+                                double* beta) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= cols) return;
-  beta[c] = rz[c] != 0.0 ? rzn[c] / rz[c] : 0.0;
+  beta[c] = pq[c] > 0.0 ? -qz[c] / pq[c] : 0.0;
   rz[c] = rzn[c];
 }
 
-__global__ void dot_kernel(const float* a, const float* b, int64_t n, double* out) {
+// out += sum_i a_i (b_i + b2_i)   (b2 may be NULL); a in FP64.
+__global__ void dot_kernel(const double* a, const float* b, const float* b2, int64_t n, int ldb, double* out) {
   double acc = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    acc += (double)a[i] * (double)b[i];
+    acc += a[i] * ((double)b[i * ldb] + (b2 ? (double)b2[i * ldb] : 0.0));
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  __shared__ double red[8];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += red[w];
+    atomicAdd(out, s);
+  }
+}
+
+__global__ void dot64_kernel(const double* a, const double* b, int64_t n, double* out) {
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc += a[i] * b[i];
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   __shared__ double red[8];
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
@@ -176,7 +239,7 @@ struct PcgProblem {
   std::vector<double> lam, mu;
   int adaptive = 1;
   const float* B = nullptr;
-  float* Xout = nullptr;
+  double* Xout = nullptr;
   double tol = 1e-6;
   int maxit = 1000, refine_every = 0, inner_mode = KOP_FAST, refine_mode = KOP_ACCURATE;
   int32_t* iters = nullptr;
@@ -206,29 +269,35 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
   const int r = pb.ny ? pb.ny->r : 0;
   Workspace ws;
   ws.st = st;
-  const size_t fbytes = sizeof(float) * (5 * nc + (size_t)r * cols + cols);
-  const size_t dbytes = sizeof(double) * (9 * (size_t)cols + (size_t)r * cols);
+  const size_t fbytes = sizeof(float) * (8 * nc + (size_t)r * cols + cols);
+  const size_t dbytes = sizeof(double) * (12 * (size_t)cols + (size_t)r * cols);
   const size_t ibytes = sizeof(int) * (size_t)cols;
-  KOP_CUDA_TRY(cudaMallocAsync(&ws.p, dbytes + fbytes + ibytes + 256, st));
-  double* lam = (double*)ws.p;
+  const size_t xbytes = pb.refine_mode == KOP_EXACT ? sizeof(double) * nc : 0;
+  KOP_CUDA_TRY(cudaMallocAsync(&ws.p, xbytes + dbytes + fbytes + ibytes + 256, st));
+  double* T64 = (double*)ws.p;
+  double* lam = T64 + (xbytes / sizeof(double));
   double* mu = lam + cols;
   double* alpha = mu + cols;
   double* beta = alpha + cols;
   double* rz = beta + cols;
   double* acc = rz + cols;
   double* acc2 = acc + cols;
-  double* spare = acc2 + cols;
+  double* pq = acc2 + cols;
+  double* qz = pq + cols;
+  double* palpha = qz + cols;
+  double* spare = palpha + cols;
   double* spare2 = spare + cols;
   double* Wd = spare2 + cols;
   float* R = (float*)(Wd + (size_t)r * cols);
   float* Z = R + nc;
   float* P = Z + nc;
   float* Q = P + nc;
-  float* T = Q + nc;
-  float* Wf = T + nc;
+  float* T = Q + nc;      // n x 2 cols
+  float* V2 = T + 2 * nc; // n x 2 cols
+  float* Wf = V2 + 2 * nc;
   float* acol = Wf + (size_t)r * cols;
   int* active = (int*)(acol + cols);
-  float* X = pb.Xout;
+  double* X = pb.Xout;
 
   std::vector<int> act(cols, 1);
   std::vector<double> hb(cols), nb(cols), rel(cols, 0.0);
@@ -247,21 +316,28 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
   va.Q = Q;
   va.B = pb.B;
   va.T = T;
+  va.T64 = T64;
+  va.V2 = V2;
   va.lam = lam;
   va.alpha = alpha;
   va.beta = beta;
   va.acc = acc;
+  va.acc2 = acc2;
   int rc;
   auto apply_prec = [&]() -> int {
     if (!pb.ny) {
       KOP_CUDA_TRY(cudaMemcpyAsync(Z, R, sizeof(float) * nc, cudaMemcpyDeviceToDevice, st));
       return KOP_OK;
     }
-    return nys_apply_dev(pb.ny, mu, pb.adaptive, R, cols, Z, Wd, Wf, acol, st);
+    return nys_apply_dev(pb.ny, mu, pb.adaptive, R, cols, Z, Wd, palpha, Wf, acol, st);
   };
   const KConst kc = kernel_constants(op->kernel, op->bw);
   auto matvec = [&](const float* V, float* O, int mode) -> int {
     return op_matvec(op->pts, op->pts, true, op->kernel, kc, mode, V, cols, cols, O, cols, op->status, st);
+  };
+  auto matvec2 = [&](const float* V, float* O, int mode) -> int {
+    return op_matvec(op->pts, op->pts, true, op->kernel, kc, mode, V, 2 * cols, 2 * cols, O, 2 * cols, op->status,
+                     st);
   };
 
   // x0 = 0, r0 = b, ||b|| per column
@@ -294,9 +370,9 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
   std::vector<char> cand(cols);
   for (it = 1; any && it <= pb.maxit; ++it) {
     if ((rc = matvec(P, Q, pb.inner_mode))) return rc;
-    va.acc = acc2;
+    va.acc = pq;
     if ((rc = vec_launch<OP_PQ>(va, st))) return rc;
-    fin_alpha_kernel<<<(cols + 127) / 128, 128, 0, st>>>(cols, rz, acc2, active, alpha, op->status);
+    fin_alpha_kernel<<<(cols + 127) / 128, 128, 0, st>>>(cols, rz, pq, active, alpha, op->status);
     KOP_LAUNCHED();
     va.acc = acc;
     if ((rc = vec_launch<OP_XR>(va, st))) return rc;
@@ -322,8 +398,14 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
     const bool refine = any_cand || (pb.refine_every > 0 && it % pb.refine_every == 0) || it == pb.maxit;
     if (refine) {
       // true residual with the accurate operator replaces the recursive one
-      if ((rc = matvec(X, T, pb.refine_mode))) return rc;
-      if ((rc = vec_launch<OP_RES>(va, st))) return rc;
+      if (pb.refine_mode == KOP_EXACT) {
+        if ((rc = exact_matvec(op->pts, op->pts, op->kernel, op->bw, X, cols, cols, T64, cols, st))) return rc;
+        if ((rc = vec_launch<OP_RES64>(va, st))) return rc;
+      } else {
+        if ((rc = vec_launch<OP_SPLIT>(va, st))) return rc;
+        if ((rc = matvec2(V2, T, pb.refine_mode))) return rc;
+        if ((rc = vec_launch<OP_RES>(va, st))) return rc;
+      }
       KOP_CUDA_TRY(cudaMemcpyAsync(hr.data(), acc, sizeof(double) * cols, cudaMemcpyDeviceToHost, st));
       KOP_CUDA_TRY(cudaStreamSynchronize(st));
       any = false;
@@ -341,9 +423,10 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
       if (!any) break;
     }
     if ((rc = apply_prec())) return rc;
-    va.acc = acc2;
-    if ((rc = vec_launch<OP_DOT>(va, st))) return rc;
-    fin_beta_kernel<<<(cols + 127) / 128, 128, 0, st>>>(cols, rz, acc2, beta);
+    va.acc = acc;
+    va.acc2 = qz;
+    if ((rc = vec_launch<OP_DOT2>(va, st))) return rc;
+    fin_beta_kernel<<<(cols + 127) / 128, 128, 0, st>>>(cols, rz, acc, qz, pq, beta);
     KOP_LAUNCHED();
     va.acc = acc;
     if ((rc = vec_launch<OP_P>(va, st))) return rc;
@@ -363,11 +446,11 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
 
 using namespace kop;
 
-static bool valid_mode(int m) { return m == KOP_FAST || m == KOP_ACCURATE || m == KOP_PLAIN; }
+static bool valid_mode(int m) { return m >= KOP_FAST && m <= KOP_EXACT; }
 
 extern "C" int pcg_solve(kop_t op, nys_t ny, const double* lambdas, int32_t n_shifts, const double* mu,
                          int32_t adaptive, const float* B, int32_t nrhs, double tol, int32_t maxit,
-                         int32_t refine_every, int32_t inner_mode, int32_t refine_mode, float* Xout, int32_t* iters,
+                         int32_t refine_every, int32_t inner_mode, int32_t refine_mode, double* Xout, int32_t* iters,
                          double* res_hist, double* true_relres, void* stream) {
   if (!op || !lambdas || !B || !Xout || !iters) return fail(KOP_EINVAL, "pcg_solve: NULL argument");
   if (ny && ny->op != op) return fail(KOP_EINVAL, "pcg_solve: preconditioner built for another operator");
@@ -404,15 +487,41 @@ extern "C" int pcg_solve(kop_t op, nys_t ny, const double* lambdas, int32_t n_sh
   return pcg_core(pb, (cudaStream_t)stream);
 }
 
-extern "C" int pcg_adjoint(kop_t op, nys_t ny, double lam, int32_t adaptive, const float* x, const float* dLdx,
+__global__ void d2f_vec_kernel(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+// x (FP64) -> [hi | lo] FP32 columns (n x 2).
+__global__ void split_vec_kernel(const double* __restrict__ x, float* __restrict__ v2, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float hi = (float)x[i];
+  v2[2 * i] = hi;
+  v2[2 * i + 1] = (float)(x[i] - (double)hi);
+}
+
+extern "C" int pcg_adjoint(kop_t op, nys_t ny, double lam, int32_t adaptive, const double* x, const double* dLdx,
                            double tol, int32_t maxit, int32_t refine_every, int32_t inner_mode, int32_t refine_mode,
-                           float* g_out, int32_t* iters, double* dLdlam, double* dLdbw, void* stream) {
+                           double* g_out, int32_t* iters, double* dLdlam, double* dLdbw, void* stream) {
   if (!op || !x || !dLdx || !g_out || !dLdlam || !dLdbw) return fail(KOP_EINVAL, "pcg_adjoint: NULL argument");
   if (ny && ny->op != op) return fail(KOP_EINVAL, "pcg_adjoint: preconditioner built for another operator");
   if (!(lam > 0.0) || !std::isfinite(lam)) return fail(KOP_EINVAL, "pcg_adjoint: lam must be > 0");
   if (!(tol > 0.0) || maxit < 1 || refine_every < 0) return fail(KOP_EINVAL, "pcg_adjoint: bad tol / maxit");
   if (!valid_mode(inner_mode) || !valid_mode(refine_mode)) return fail(KOP_EINVAL, "pcg_adjoint: bad mode");
   cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = op->pts.n;
+  Workspace ws;
+  ws.st = st;
+  // Bf (n) | V2 (2n) | T2 (2n) floats, acc (2) doubles
+  KOP_CUDA_TRY(cudaMallocAsync(&ws.p, sizeof(float) * 5 * (size_t)n + 2 * sizeof(double) + 64, st));
+  float* Bf = (float*)ws.p;
+  float* V2 = Bf + n;
+  float* T2 = V2 + 2 * n;
+  double* acc = (double*)(((uintptr_t)(T2 + 2 * n) + 15) & ~(uintptr_t)15);
+  const unsigned nb = (unsigned)((n + 255) / 256);
+  d2f_vec_kernel<<<nb, 256, 0, st>>>(dLdx, Bf, n);
+  KOP_LAUNCHED();
   PcgProblem pb;
   pb.op = op;
   pb.ny = ny;
@@ -420,7 +529,7 @@ extern "C" int pcg_adjoint(kop_t op, nys_t ny, double lam, int32_t adaptive, con
   pb.lam = {lam};
   pb.mu = {lam};
   pb.adaptive = adaptive ? 1 : 0;
-  pb.B = dLdx;
+  pb.B = Bf;
   pb.Xout = g_out;
   pb.tol = tol;
   pb.maxit = maxit;
@@ -432,20 +541,31 @@ extern "C" int pcg_adjoint(kop_t op, nys_t ny, double lam, int32_t adaptive, con
   const int rc = pcg_core(pb, st);
   if (iters) *iters = it;
   if (rc < 0) return rc;
-  const int64_t n = op->pts.n;
-  Workspace ws;
-  ws.st = st;
-  KOP_CUDA_TRY(cudaMallocAsync(&ws.p, sizeof(float) * n + 2 * sizeof(double), st));
-  float* T = (float*)ws.p;
-  double* acc = (double*)(T + ((n + 1) / 2) * 2);
-  // dL/dbw = -g^T (dK/dbw) x,  dL/dlam = -g^T x
-  const KConst kc = kernel_constants(op->kernel + 3, op->bw);
-  int r2 = op_matvec(op->pts, op->pts, true, op->kernel + 3, kc, refine_mode, x, 1, 1, T, 1, op->status, st);
-  if (r2) return r2;
-  KOP_CUDA_TRY(cudaMemsetAsync(acc, 0, 2 * sizeof(double), st));
-  dot_kernel<<<4 * num_sms(), 256, 0, st>>>(g_out, x, n, acc);
-  dot_kernel<<<4 * num_sms(), 256, 0, st>>>(g_out, T, n, acc + 1);
+  // dL/dbw = -g^T (dK/dbw) x with x split exactly into two FP32 columns,  dL/dlam = -g^T x
+  split_vec_kernel<<<nb, 256, 0, st>>>(x, V2, n);
   KOP_LAUNCHED();
+  KOP_CUDA_TRY(cudaMemsetAsync(acc, 0, 2 * sizeof(double), st));
+  // g^T x through the exact split of x; g^T (dK/dbw) x through the two product
+  // columns of the split (or one FP64 product in exact mode)
+  dot_kernel<<<4 * num_sms(), 256, 0, st>>>(g_out, V2, V2 + 1, n, 2, acc);
+  KOP_LAUNCHED();
+  if (refine_mode == KOP_EXACT) {
+    double* t64 = nullptr;
+    KOP_CUDA_TRY(cudaMallocAsync((void**)&t64, sizeof(double) * n, st));
+    int r2 = exact_matvec(op->pts, op->pts, op->kernel + 3, op->bw, x, 1, 1, t64, 1, st);
+    if (r2 == KOP_OK) {
+      dot64_kernel<<<4 * num_sms(), 256, 0, st>>>(g_out, t64, n, acc + 1);
+      note_launch();
+    }
+    cudaFreeAsync(t64, st);
+    if (r2) return r2;
+  } else {
+    const KConst kc = kernel_constants(op->kernel + 3, op->bw);
+    int r2 = op_matvec(op->pts, op->pts, true, op->kernel + 3, kc, refine_mode, V2, 2, 2, T2, 2, op->status, st);
+    if (r2) return r2;
+    dot_kernel<<<4 * num_sms(), 256, 0, st>>>(g_out, T2, T2 + 1, n, 2, acc + 1);
+    KOP_LAUNCHED();
+  }
   double h[2];
   KOP_CUDA_TRY(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, st));
   KOP_CUDA_TRY(cudaStreamSynchronize(st));

@@ -44,25 +44,40 @@ int num_sms() {
 
 KConst kernel_constants(int kind, double bw) {
   const double log2e = 1.4426950408889634;
-  KConst k{0.f, 0.f, 0.f, bw};
+  KConst k{0.f, 0.f, bw};
+  double scale = 0.0;
   switch (kind) {
     case KF_RBF:
     case KF_DRBF:
-      k.c0 = (float)(-log2e / (2.0 * bw * bw));
-      k.c2 = (float)(1.0 / (bw * bw * bw));
+      scale = -log2e / (2.0 * bw * bw);
+      k.c2 = (float)(1.0 / (scale * bw * bw * bw));
       break;
     case KF_LAPLACE:
     case KF_DLAPLACE:
-      k.c0 = (float)(-log2e / bw);
-      k.c2 = (float)(1.0 / (bw * bw));
+      scale = (log2e / bw) * (log2e / bw);
+      k.c2 = (float)(1.0 / ((log2e / bw) * bw * bw));
       break;
     default:
-      k.c0 = (float)(-log2e);
-      k.c1 = (float)(2.23606797749979 / bw);
+      scale = 5.0 / (bw * bw);
       k.c2 = (float)(1.0 / bw);
       break;
   }
+  k.scale = (float)scale;
   return k;
+}
+
+__global__ void scale_norms_kernel(const float* __restrict__ nrm, int64_t n, float s, float* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = s * nrm[i];
+}
+
+int ensure_scaled_norms(PointSet& ps, float scale, cudaStream_t st) {
+  if (ps.snorm && ps.snorm_scale == scale) return KOP_OK;
+  if (!ps.snorm) KOP_CUDA_TRY(cudaMallocAsync((void**)&ps.snorm, sizeof(float) * ps.n_pad, st));
+  scale_norms_kernel<<<(unsigned)((ps.n_pad + 255) / 256), 256, 0, st>>>(ps.norms, ps.n_pad, scale, ps.snorm);
+  KOP_LAUNCHED();
+  ps.snorm_scale = scale;
+  return KOP_OK;
 }
 
 int padded_dim(int d) {
@@ -117,7 +132,7 @@ int pointset_alloc(PointSet& ps, int64_t n, int d, cudaStream_t st) {
   ps.dp = padded_dim(d);
   ps.n_pad = ((n + 127) / 128) * 128;
   const size_t nx = (size_t)ps.n_pad * ps.dp;
-  const size_t bytes = nx * 4 + (size_t)ps.n_pad * 4 + 3 * nx * 2 + 1024;
+  const size_t bytes = nx * 4 + (size_t)ps.n_pad * 4 + 3 * nx * 2 + (size_t)n * d * 4 + 2048;
   void* p = nullptr;
   KOP_CUDA_TRY(cudaMallocAsync(&p, bytes, st));
   ps.block = p;
@@ -131,6 +146,8 @@ int pointset_alloc(PointSet& ps, int64_t n, int d, cudaStream_t st) {
     ps.sp[s] = (__nv_bfloat16*)b;
     b += nx * 2;
   }
+  b = (uint8_t*)(((uintptr_t)b + 255) & ~(uintptr_t)255);
+  ps.xorig = (float*)b;
   const int box_cols = ps.dp >= 64 ? 64 : ps.dp;
   for (int s = 0; s < 3; ++s) {
     int rc = encode_tmap_bf16(&ps.tm[s][0], ps.sp[s], ps.n_pad, ps.dp, box_cols, 128);
@@ -145,8 +162,11 @@ int pointset_alloc(PointSet& ps, int64_t n, int d, cudaStream_t st) {
 
 void pointset_free(PointSet& ps, cudaStream_t st) {
   if (ps.block) cudaFreeAsync(ps.block, st);
+  if (ps.snorm) cudaFreeAsync(ps.snorm, st);
+  ps.snorm = nullptr;
+  ps.snorm_scale = 0.0f;
   ps.block = nullptr;
-  ps.xc = ps.norms = nullptr;
+  ps.xc = ps.norms = ps.xorig = nullptr;
   ps.sp[0] = ps.sp[1] = ps.sp[2] = nullptr;
 }
 
@@ -207,6 +227,7 @@ __global__ void fill_kernel(const float* __restrict__ X, const double* __restric
 }
 
 int pointset_fill(PointSet& ps, const float* X, const double* mean, cudaStream_t st) {
+  KOP_CUDA_TRY(cudaMemcpyAsync(ps.xorig, X, sizeof(float) * (size_t)ps.n * ps.d, cudaMemcpyDeviceToDevice, st));
   const int64_t threads = ps.n_pad * 32;
   const int bs = 256;
   fill_kernel<<<(unsigned)((threads + bs - 1) / bs), bs, 0, st>>>(X, mean, ps.n, ps.d, ps.dp, ps.n_pad, ps.xc,

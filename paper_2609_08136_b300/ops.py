@@ -13,7 +13,7 @@ from . import _ffi
 from ._ffi import check
 
 RBF, LAPLACE, MATERN52 = 0, 1, 2
-FAST, ACCURATE, PLAIN = 0, 1, 2
+FAST, ACCURATE, PLAIN, EXACT = 0, 1, 2, 3
 KERNELS = {"rbf": RBF, "laplace": LAPLACE, "matern52": MATERN52}
 
 
@@ -82,6 +82,15 @@ class KernelOperator:
         check(_ffi.lib().kop_matvec(self._h, _ptr(V2), V2.shape[1], _ptr(O), int(mode), _stream(stream)),
               "kop_matvec")
         return O[:, 0] if vec and out is None else O
+
+    def matvec_f64(self, V: torch.Tensor, deriv: bool = False, stream=None):
+        """FP64 product with the exact (FP64 CUDA-core) operator."""
+        vec = V.dim() == 1
+        V2 = (V.unsqueeze(1) if vec else V).to(torch.float64).contiguous()
+        O = torch.empty_like(V2)
+        check(_ffi.lib().kop_matvec_f64(self._h, _ptr(V2), V2.shape[1], _ptr(O), int(bool(deriv)), _stream(stream)),
+              "kop_matvec_f64")
+        return O[:, 0] if vec else O
 
     def dbw_matvec(self, V: torch.Tensor, mode: int = FAST, stream=None):
         vec = V.dim() == 1
@@ -187,7 +196,7 @@ def pcg_solve(op: KernelOperator, B: torch.Tensor, lambdas, nys: Nystrom | None 
     if mu is not None:
         mus = [float(mu)] * ns if not hasattr(mu, "__len__") else [float(x) for x in mu]
         mu_arr = (ctypes.c_double * ns)(*mus)
-    X = torch.empty((op.n, cols), dtype=torch.float32, device=B2.device)
+    X = torch.empty((op.n, cols), dtype=torch.float64, device=B2.device)
     iters = (ctypes.c_int32 * cols)()
     hist = (ctypes.c_double * ((maxit + 1) * cols))() if history else None
     tr = (ctypes.c_double * cols)()
@@ -206,9 +215,12 @@ def pcg_solve(op: KernelOperator, B: torch.Tensor, lambdas, nys: Nystrom | None 
 def pcg_adjoint(op: KernelOperator, x: torch.Tensor, dLdx: torch.Tensor, lam: float, nys: Nystrom | None = None,
                 adaptive: bool = True, tol: float = 1e-6, maxit: int = 1000, refine_every: int = 20,
                 inner_mode: int = FAST, refine_mode: int = ACCURATE, stream=None):
-    """g = (K + lam I)^{-1} dL/dx, and dL/dlam = -g^T x, dL/dbw = -g^T (dK/dbw) x."""
-    x2 = _dev_f32(x, "x").reshape(-1).contiguous()
-    d2 = _dev_f32(dLdx, "dLdx").reshape(-1).contiguous()
+    """g = (K + lam I)^{-1} dL/dx, and dL/dlam = -g^T x, dL/dbw = -g^T (dK/dbw) x.
+    x, dL/dx and g are FP64 device vectors."""
+    x2 = x.detach().reshape(-1).to(torch.float64).contiguous()
+    d2 = dLdx.detach().reshape(-1).to(torch.float64).contiguous()
+    if not (x2.is_cuda and d2.is_cuda):
+        raise TypeError("x and dLdx must be CUDA tensors")
     g = torch.empty_like(x2)
     it = ctypes.c_int32()
     dl = ctypes.c_double()
@@ -221,28 +233,25 @@ def pcg_adjoint(op: KernelOperator, x: torch.Tensor, dLdx: torch.Tensor, lam: fl
 
 
 class _KRRSolve(torch.autograd.Function):
-    """x = (K(bw) + lam I)^{-1} b with an adjoint backward (pcg_adjoint)."""
+    """x = (K(bw) + lam I)^{-1} b (FP64 x) with an adjoint backward (pcg_adjoint)."""
 
     @staticmethod
     def forward(ctx, b, bw, lam, op, nys, kw):
         op.set_bandwidth(float(bw))
-        res = pcg_solve(op, b.detach(), [float(lam)], nys=nys, **kw)
-        if res.status < 0:
-            raise RuntimeError("pcg_solve failed")
+        res = pcg_solve(op, b.detach().to(torch.float32), [float(lam)], nys=nys, **kw)
         x = res.x.reshape(b.shape)
         ctx.save_for_backward(x)
         ctx.op, ctx.nys, ctx.kw, ctx.lam = op, nys, kw, float(lam)
-        ctx.bw_dtype, ctx.lam_dtype = bw.dtype, lam.dtype
+        ctx.b_dtype, ctx.bw_dtype, ctx.lam_dtype = b.dtype, bw.dtype, lam.dtype
         return x
 
     @staticmethod
     def backward(ctx, gx):
         (x,) = ctx.saved_tensors
-        kw = dict(ctx.kw)
-        kw.pop("history", None)
-        g, dlam, dbw, _ = pcg_adjoint(ctx.op, x, gx.contiguous(), ctx.lam, nys=ctx.nys, **kw)
-        return (g.reshape(x.shape), torch.tensor(dbw, dtype=ctx.bw_dtype), torch.tensor(dlam, dtype=ctx.lam_dtype),
-                None, None, None)
+        kw = {k: v for k, v in ctx.kw.items() if k != "history"}
+        g, dlam, dbw, _ = pcg_adjoint(ctx.op, x, gx, ctx.lam, nys=ctx.nys, **kw)
+        return (g.reshape(x.shape).to(ctx.b_dtype), torch.tensor(dbw, dtype=ctx.bw_dtype),
+                torch.tensor(dlam, dtype=ctx.lam_dtype), None, None, None)
 
 
 def krr_solve(op: KernelOperator, b: torch.Tensor, bw: torch.Tensor, lam: torch.Tensor, nys: Nystrom | None = None,
@@ -261,13 +270,18 @@ def krr_val_loss_and_grad(op: KernelOperator, nys: Nystrom | None, y: torch.Tens
     res = pcg_solve(op, y, [lam], nys=nys, tol=tol, maxit=maxit, refine_every=refine_every, inner_mode=inner_mode,
                     refine_mode=refine_mode)
     x = res.x.reshape(-1)
+    # products with the FP64 x go through its exact two-column FP32 split
+    x_hi = x.float()
+    x2 = torch.stack([x_hi, (x - x_hi.double()).float()], dim=1).contiguous()
     nv = Xv.shape[0]
-    e = op.cross_matvec(Xv, x, mode=refine_mode) - yv.reshape(-1)
-    e64 = e.double()
+    kx = op.cross_matvec(Xv, x2, mode=refine_mode).double().sum(dim=1)
+    e64 = kx - yv.reshape(-1).double()
     loss = float(e64 @ e64) / nv
-    dLdx = op.cross_matvec(Xv, e, transpose=True, mode=refine_mode) * (2.0 / nv)
+    e_hi = e64.float()
+    e2 = torch.stack([e_hi, (e64 - e_hi.double()).float()], dim=1).contiguous()
+    dLdx = op.cross_matvec(Xv, e2, transpose=True, mode=refine_mode).double().sum(dim=1) * (2.0 / nv)
     g, dlam, dbw_k, _ = pcg_adjoint(op, x, dLdx, lam, nys=nys, tol=tol, maxit=maxit, refine_every=refine_every,
                                     inner_mode=inner_mode, refine_mode=refine_mode)
-    dkv = op.cross_matvec(Xv, x, deriv=True, mode=refine_mode).double()
+    dkv = op.cross_matvec(Xv, x2, deriv=True, mode=refine_mode).double().sum(dim=1)
     dbw = (2.0 / nv) * float(e64 @ dkv) + dbw_k
     return loss, dbw, dlam

@@ -16,7 +16,7 @@ from paper_2609_08136_b300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-TOL = {ops.FAST: 3e-4, ops.ACCURATE: 4e-6, ops.PLAIN: 4e-6}
+TOL = {ops.FAST: 3e-4, ops.ACCURATE: 4e-6, ops.PLAIN: 4e-6, ops.EXACT: 1e-12}
 
 
 def _rel_err(kind, Xq, Xk, V, bw, got, deriv=False):
@@ -46,6 +46,23 @@ def test_matvec_parity(n, d, m, kind, mode):
     got = op.matvec(torch.from_numpy(V).cuda(), mode=mode).cpu().numpy()
     op.sync()
     assert _rel_err(kind, X, X, V, bw, got) < TOL[mode]
+
+
+@pytest.mark.parametrize("kind", [ops.RBF, ops.LAPLACE, ops.MATERN52])
+@pytest.mark.parametrize("n,d,m", [(1, 3, 1), (129, 16, 2), (300, 64, 9), (257, 5, 1)])
+def test_exact_fp64_operator(n, d, m, kind):
+    X = W.random_points(n, d, seed=n + 3 * d, shift=2.0)
+    V = np.random.default_rng(n).standard_normal((n, m))
+    bw = float(np.sqrt(d))
+    op = ops.KernelOperator(torch.from_numpy(X).cuda(), kind, bw)
+    for deriv in (False, True):
+        got = op.matvec_f64(torch.from_numpy(V).cuda(), deriv=deriv).cpu().numpy()
+        f = O.dkernel_dbw_from_sqdist if deriv else O.kernel_from_sqdist
+        Km = f(kind, O.sqdist(X, X), bw)
+        ref = Km @ V
+        assert np.max(np.abs(got - ref) / (np.abs(Km) @ np.abs(V) + 1e-300)) < TOL[ops.EXACT]
+    got32 = op.matvec(torch.from_numpy(V.astype(np.float32)).cuda(), mode=ops.EXACT).cpu().numpy()
+    assert _rel_err(kind, X, X, V.astype(np.float32), bw, got32) < 1e-6
 
 
 @pytest.mark.parametrize("mode", [ops.FAST, ops.ACCURATE])

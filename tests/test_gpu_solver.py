@@ -3,9 +3,10 @@
 Acceptance per solved column (the paper's accuracy check, App. B.2): the true
 relative residual ||(K + lam I) x - b|| / ||b||, computed by the oracle in
 FP64, is <= 1e-6, and ||x - x*|| / ||x*|| <= 1e-4 against a dense FP64
-Cholesky solve.  The solver runs with tol = 5e-7 so that the FP32 rounding of
-its own accurate operator (a few 1e-7 on these problems) stays inside the
-acceptance bound."""
+Cholesky solve.  These problems are small and badly conditioned (kappa up to
+4e3), where FP32 kernel values alone leave an FP64 residual floor near 1e-6,
+so the true residual of the refinement uses the FP64 operator (KOP_EXACT);
+the large-n path with the FP32 accurate operator is covered separately."""
 import numpy as np
 import pytest
 import scipy.linalg as sla
@@ -46,8 +47,10 @@ def test_nystrom_matches_oracle():
     K = O.kernel_matrix(O.RBF, wl.X, wl.X, wl.bandwidth)
     U_o, lam_o, nu_o = O.nystrom(K @ Om.astype(np.float64), Om, nu_rel=nu_rel)
     assert abs(nu_g - nu_o) <= 1e-6 * nu_o
+    # Weyl: |lam_gpu - lam_oracle| <= ||E||, E the sketch's operator error
+    # (FP32-level, ~1e-6 of ||K||), so the bound is absolute in lam_1
     big = lam_o > 1e3 * nu_o
-    np.testing.assert_allclose(lam_g.numpy()[big], lam_o[big], rtol=2e-5)
+    np.testing.assert_allclose(lam_g.numpy()[big], lam_o[big], rtol=1e-5, atol=2e-6 * lam_o[0])
     U = ny.factor().cpu().numpy().astype(np.float64)
     assert np.linalg.norm(U.T @ U - np.eye(r)) < 1e-5
     # preconditioner action against the oracle's, both damping modes
@@ -74,9 +77,8 @@ def test_preconditioner_spd_small():
     assert ev[0] > 0.99 * lo and ev[-1] < 1.01 / mu
 
 
-@pytest.mark.parametrize("inner,refine", [(ops.FAST, ops.ACCURATE), (ops.PLAIN, ops.PLAIN),
-                                          (ops.ACCURATE, ops.ACCURATE)])
-def test_krr_rbf_small_full_size(inner, refine):
+@pytest.mark.parametrize("inner", [ops.FAST, ops.PLAIN, ops.ACCURATE])
+def test_krr_rbf_small_full_size(inner):
     # the 4096 x 16 RBF workload at its full size, direct FP64 solve as reference
     wl = W.krr_rbf_small(seed=0)
     lam = float(wl.lambdas[0])
@@ -85,11 +87,12 @@ def test_krr_rbf_small_full_size(inner, refine):
     Om = torch.from_numpy(W.gaussian_sketch(wl.n, wl.rank, seed=0)).cuda()
     ny = ops.Nystrom(op, Om, mode=inner if inner != ops.ACCURATE else ops.FAST)
     res = ops.pcg_solve(op, torch.from_numpy(wl.B).cuda(), [lam], nys=ny, tol=5e-7, maxit=500, refine_every=20,
-                        inner_mode=inner, refine_mode=refine)
+                        inner_mode=inner, refine_mode=ops.EXACT)
     assert res.converged
     _check_cols(K, [lam], wl.B, res.x.cpu().numpy(), [xs])
     # preconditioning pays off: plain CG needs more iterations
-    cg = ops.pcg_solve(op, torch.from_numpy(wl.B).cuda(), [lam], nys=None, tol=5e-7, maxit=3000)
+    cg = ops.pcg_solve(op, torch.from_numpy(wl.B).cuda(), [lam], nys=None, tol=5e-7, maxit=3000,
+                       refine_mode=ops.EXACT)
     assert cg.converged and cg.iters[0] > res.iters[0]
 
 
@@ -102,7 +105,7 @@ def test_block_shifts_ragged(kind):
     lams = [0.05, 0.5]
     op = ops.KernelOperator(torch.from_numpy(X).cuda(), kind, bw)
     ny = ops.Nystrom(op, torch.from_numpy(W.gaussian_sketch(n, 50, seed=3)).cuda())
-    res = ops.pcg_solve(op, torch.from_numpy(B).cuda(), lams, nys=ny, tol=5e-7, maxit=800)
+    res = ops.pcg_solve(op, torch.from_numpy(B).cuda(), lams, nys=ny, tol=5e-7, maxit=800, refine_mode=ops.EXACT)
     assert res.converged
     Xg = res.x.cpu().numpy()
     K = O.kernel_matrix(kind, X, X, bw)
@@ -118,7 +121,8 @@ def test_identity_preconditioner_is_cg_and_edge_cases():
     B = W.random_block(n, 2, seed=3)
     B[:, 1] = 0.0
     op = ops.KernelOperator(torch.from_numpy(X).cuda(), ops.RBF, 1.0)
-    res = ops.pcg_solve(op, torch.from_numpy(B).cuda(), [0.3], nys=None, tol=1e-6, maxit=300)
+    res = ops.pcg_solve(op, torch.from_numpy(B).cuda(), [0.3], nys=None, tol=1e-7, maxit=600,
+                        refine_mode=ops.EXACT)
     assert res.converged
     assert res.iters[1] == 0 and np.all(res.x.cpu().numpy()[:, 1] == 0.0)
     K = O.kernel_matrix(O.RBF, X, X, 1.0)
@@ -126,7 +130,8 @@ def test_identity_preconditioner_is_cg_and_edge_cases():
     x = res.x.cpu().numpy()[:, 0]
     assert np.linalg.norm(x - xo) / np.linalg.norm(xo) < 1e-5
     # maxit reached: warning status, iterate written
-    r1 = ops.pcg_solve(op, torch.from_numpy(B[:, :1].copy()).cuda(), [0.3], tol=1e-12, maxit=2)
+    r1 = ops.pcg_solve(op, torch.from_numpy(B[:, :1].copy()).cuda(), [0.3], tol=1e-12, maxit=2,
+                       refine_mode=ops.EXACT)
     assert r1.status == 1 and r1.iters[0] == 2
     assert np.all(np.isfinite(r1.x.cpu().numpy()))
 
@@ -137,3 +142,21 @@ def test_single_point():
     res = ops.pcg_solve(op, torch.tensor([[2.0]], device="cuda"), [1.0], tol=1e-6, maxit=5)
     assert res.converged
     assert abs(res.x.cpu().item() - 1.0) < 1e-6  # (1 + 1) x = 2
+
+
+def test_laplace_mixture_accurate_refinement_n20000():
+    # the benchmark workload's distribution at n = 20000 (same lam): the FP32
+    # accurate operator with compensated sums is enough for the true residual;
+    # the FP64 residual is checked with the host oracle on all rows
+    from oracle import cmatvec
+    wl = W.krr_laplace_mix(seed=0, n=20000, rank=200)
+    lam = 1e-6 * 200000
+    op = ops.KernelOperator(torch.from_numpy(wl.X).cuda(), ops.LAPLACE, wl.bandwidth)
+    ny = ops.Nystrom(op, torch.from_numpy(W.gaussian_sketch(wl.n, 200, seed=0)).cuda())
+    res = ops.pcg_solve(op, torch.from_numpy(wl.B).cuda(), [lam], nys=ny, tol=5e-7, maxit=500,
+                        inner_mode=ops.FAST, refine_mode=ops.ACCURATE)
+    assert res.converged
+    x = res.x.cpu().numpy()[:, 0]
+    b = wl.B[:, 0].astype(np.float64)
+    kx = cmatvec.kernel_matvec(O.LAPLACE, wl.X, x, wl.bandwidth)
+    assert np.linalg.norm(kx + lam * x - b) / np.linalg.norm(b) <= 1e-6
