@@ -150,6 +150,20 @@ int nys_destroy(nys_t ny);
 int nys_apply(nys_t ny, const double* mu, int32_t adaptive, const float* V, int32_t m, float* O,
               void* stream);
 
+/* Same result as nys_apply for 1 <= m <= 8 columns, but without allocating
+ * any device memory.  There is no counterpart in the paper: this exists for
+ * callers that cannot allocate on this path (a latency-critical loop that must
+ * avoid the device-wide synchronization of cudaMalloc/cudaFree, or an
+ * application whose device memory is owned by its own allocator).  Its scratch
+ * is a fixed array of 16448 doubles (128.5 KB) inside the library's device
+ * image, held on every GPU that loads the library until the process exits;
+ * r * m + m must fit in it (r <= 2048 with m <= 8 always does), else
+ * KOP_EINVAL.  All calls share that array: calls whose GPU work overlaps race,
+ * so order them on one stream.  The first call on a device looks up the
+ * array's address and should come before any stream capture.               */
+int nys_apply_noalloc(nys_t ny, const double* mu, int32_t adaptive, const float* V, int32_t m,
+                      float* O, void* stream);
+
 /* Host copies: lam_hat (r doubles, descending), nu (1 double), r (int). */
 int nys_eigs(nys_t ny, double* lam_hat, double* nu, int32_t* r);
 /* Device copy of U (n x r FP32 row-major) into U_out. */
