@@ -106,6 +106,22 @@ def _dist():
     return world, rank, local
 
 
+def replica_seed(seed: int, rank: int) -> int:
+    """Each rank solves its own independent problem (weak scaling replicas)."""
+    return seed + rank
+
+
+def max_over_ranks(value: float, dist=None, device=None) -> float:
+    """The job's step time is the slowest rank's (no data-path collective:
+    this reduction of one scalar is the only communication)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _cpu_oracle_rate(wl, iters, rank_r, budget_s=15.0):
     """FP64 oracle (host C, all cores): matvec and sketch times extrapolated
     from a bounded sample of rows.  Returns (solve_seconds, sample text, cores)."""
@@ -176,11 +192,12 @@ def run_native(a):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     # each rank solves its own independent problem (weak scaling, no data-path collective)
-    wl = W.krr_laplace_mix(seed=a.seed + rank, n=a.n, rank=a.rank)
+    seed = replica_seed(a.seed, rank)
+    wl = W.krr_laplace_mix(seed=seed, n=a.n, rank=a.rank)
     lam = float(wl.lambdas[0])
     Xh = torch.from_numpy(wl.X).pin_memory()
     Bh = torch.from_numpy(wl.B).pin_memory()
-    Omh = torch.from_numpy(W.gaussian_sketch(wl.n, a.rank, seed=a.seed + rank)).pin_memory()
+    Omh = torch.from_numpy(W.gaussian_sketch(wl.n, a.rank, seed=seed)).pin_memory()
     X = Xh.to(dev)
     B = Bh.to(dev)
     Om = Omh.to(dev)
@@ -217,11 +234,7 @@ def run_native(a):
         last = (op, ny, res)
         del ny, op
     clocks = clk.stop()
-    t_step = statistics.mean(times)
-    if dist:
-        tt = torch.tensor([t_step], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = tt.item()
+    t_step = max_over_ranks(statistics.mean(times), dist, dev)
     op, ny, res = last
     value = world / t_step
 
@@ -247,11 +260,11 @@ def run_native(a):
     flops = 2.0 * n * n * (d + 1)  # distance GEMM + contraction per K v
     peaks, peak_src = _peaks()
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0)
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    # SFU (MUFU) roofline of the m = 1 product: Laplace needs sqrt + ex2 per entry
-    mufu_per_entry = 2
-    sfu_peak = 16.0 * sms * sm_mhz * 1e6  # MUFU ops/s at the sampled clock
-    achieved_ops = mufu_per_entry * n * n / t_fast
+    # SFU roofline of the m = 1 product, with the SFU rates measured live on
+    # this GPU: a Laplace entry needs one sqrt and one ex2
+    rates = ops.sfu_rates()
+    peak_entries = 1.0 / (1.0 / rates["ex2"] + 1.0 / rates["sqrt"])
+    achieved_entries = n * n / t_fast
     out = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -265,11 +278,12 @@ def run_native(a):
         "matvec_ms": {"fused_fast": t_fast * 1e3, "plain_fp32": None if t_plain is None else t_plain * 1e3},
         "matvec_tflops": {"fused_fast": flops / t_fast / 1e12,
                           "plain_fp32": None if t_plain is None else flops / t_plain / 1e12},
-        "kernel_evals_per_s": n * n / t_fast,
-        "roofline": {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": sfu_peak / 1e12, "unit": "Tops/s",
-                     "frac": achieved_ops / sfu_peak, "traffic": None,
+        "kernel_evals_per_s": achieved_entries,
+        "roofline": {"bound": "alu", "achieved": achieved_entries / 1e12, "peak": peak_entries / 1e12,
+                     "unit": "Tentries/s", "frac": achieved_entries / peak_entries, "traffic": None,
                      "kernel": "k1_fma_kernel<LAPLACE,2,1,128> (K v, m = 1)",
-                     "peak_source": f"16 MUFU ops/clk/SM x {sms} SMs x {sm_mhz:.0f} MHz (sampled)"},
+                     "peak_source": ("SFU rates measured live by kop_sfu_rates (ex2 %.2f, sqrt %.2f Tops/s); "
+                                     "one Laplace entry = 1 sqrt + 1 ex2" % (rates["ex2"] / 1e12, rates["sqrt"] / 1e12))},
         "clocks": clocks,
         "gpu_launches": int(statistics.mean(launches)),
         "peaks_source": peak_src,

@@ -85,6 +85,13 @@ const char* kop_last_error(void);
  * reports on the library itself. */
 int64_t kop_launch_count(void);
 
+/* Measured SFU throughput of the current device, in operations per second:
+ * rates[0] = ex2.approx, rates[1] = sqrt.approx, rates[2] = rsqrt.approx
+ * (host array of 3).  The m = 1 operator product is bound by these units, so
+ * they are the denominators of its roofline.  Runs three short probe kernels
+ * on `stream` and synchronizes it.  Not in the paper: a measurement helper. */
+int kop_sfu_rates(double* rates, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Kernel operator (the matrix-free linear operator of Sec. 4.3; K of
  * Sec. 2.1 Eq. "rlaopt-krr").
@@ -130,7 +137,8 @@ int kop_sync(kop_t op, void* stream);
  *
  * nys_build: Omega (device, n x r FP32) is the caller's test matrix (the
  * library does not orthonormalize it; Gaussian N(0,1)/sqrt(n) entries are
- * expected).  Steps: Y = K Omega (fused operator, `mode`),
+ * expected).  It is rounded to BF16 once and the rounded matrix is used in
+ * every step (the result is the exact Nystrom approximation for it).  Steps: Y = K Omega (fused operator, `mode`),
  * nu = nu_rel * ||Y||_2 (nu_rel <= 0 selects 2^-16 for KOP_FAST and 2^-21
  * otherwise), Y_nu = Y + nu Omega, C = chol(sym(Omega^T Y_nu)) in FP64 (on a
  * failed pivot nu grows 10x, at most 3 times, then KOP_ENOTPD),
@@ -176,10 +184,13 @@ int nys_factor(nys_t ny, float* U_out, void* stream);
  * with its own alpha and beta; each column stops when its recursive residual
  * satisfies ||r|| <= tol ||b|| (PCGStoppingCriteria, App. A.1: the
  * condition must hold for every right-hand side) AND the true residual,
- * recomputed with `refine_mode`, does too.  Every `refine_every` iterations
- * (0 = only at the end) the recursive residual is replaced by the true one
- * (iterative refinement: inner products with `inner_mode`, accuracy from
- * `refine_mode`).  ny = NULL gives plain CG (IdentityConfig, App. A.1).
+ * recomputed with `check_mode`, does too.  Every `refine_every` iterations
+ * (0 = only at candidate stops and at maxit) the recursive residual is
+ * replaced by the true one computed with `refine_mode` (iterative refinement:
+ * operator products with `inner_mode`).  Recommended: inner KOP_FAST, refine
+ * KOP_ACCURATE, check KOP_PLAIN (direct differences with error-free sums) or
+ * KOP_EXACT for small badly conditioned systems.  ny = NULL gives plain CG
+ * (IdentityConfig, App. A.1).
  * The preconditioner of column c uses damping mu[s] (host; NULL: mu = lambdas).
  *   lambdas      host, n_shifts values > 0
  *   B            device, n x nrhs
@@ -194,8 +205,8 @@ int nys_factor(nys_t ny, float* U_out, void* stream);
  * breakdown.  Synchronizes `stream`.                                         */
 int pcg_solve(kop_t op, nys_t ny, const double* lambdas, int32_t n_shifts, const double* mu,
               int32_t adaptive, const float* B, int32_t nrhs, double tol, int32_t maxit,
-              int32_t refine_every, int32_t inner_mode, int32_t refine_mode, double* Xout,
-              int32_t* iters, double* res_hist, double* true_relres, void* stream);
+              int32_t refine_every, int32_t inner_mode, int32_t refine_mode, int32_t check_mode,
+              double* Xout, int32_t* iters, double* res_hist, double* true_relres, void* stream);
 
 /* Adjoint of one solve (the paper differentiates through the solver,
  * Sec. 3.2, Eq. "rlaopt-bilevel"; here by an adjoint solve instead of
@@ -205,11 +216,12 @@ int pcg_solve(kop_t op, nys_t ny, const double* lambdas, int32_t n_shifts, const
  * with the same preconditioner (mu = lam), writes g (device, n, FP64) and the
  * host scalars
  *     dL/dlam = -g^T x,        dL/dbw|_K = -g^T (dK/dbw) x,
- * (dL/db = g).  iters: host int (may be NULL).                              */
+ * (dL/db = g), the derivative product taken with `check_mode`.  iters: host
+ * int (may be NULL).                              */
 int pcg_adjoint(kop_t op, nys_t ny, double lam, int32_t adaptive, const double* x,
                 const double* dLdx, double tol, int32_t maxit, int32_t refine_every,
-                int32_t inner_mode, int32_t refine_mode, double* g_out, int32_t* iters,
-                double* dLdlam, double* dLdbw, void* stream);
+                int32_t inner_mode, int32_t refine_mode, int32_t check_mode, double* g_out,
+                int32_t* iters, double* dLdlam, double* dLdbw, void* stream);
 
 #ifdef __cplusplus
 }

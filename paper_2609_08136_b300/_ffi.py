@@ -18,6 +18,7 @@ P = ctypes.POINTER
 SIGNATURES = {
     "kop_last_error": (ctypes.c_char_p, []),
     "kop_launch_count": (c_i64, []),
+    "kop_sfu_rates": (c_int, [P(c_dbl), c_vp]),
     "kop_create": (c_int, [c_vp, c_i64, c_i32, c_i32, c_dbl, c_vp, P(c_vp)]),
     "kop_destroy": (c_int, [c_vp]),
     "kop_set_bandwidth": (c_int, [c_vp, c_dbl]),
@@ -33,8 +34,8 @@ SIGNATURES = {
     "nys_eigs": (c_int, [c_vp, P(c_dbl), P(c_dbl), P(c_i32)]),
     "nys_factor": (c_int, [c_vp, c_vp, c_vp]),
     "pcg_solve": (c_int, [c_vp, c_vp, P(c_dbl), c_i32, P(c_dbl), c_i32, c_vp, c_i32, c_dbl, c_i32, c_i32,
-                          c_i32, c_i32, c_vp, P(c_i32), P(c_dbl), P(c_dbl), c_vp]),
-    "pcg_adjoint": (c_int, [c_vp, c_vp, c_dbl, c_i32, c_vp, c_vp, c_dbl, c_i32, c_i32, c_i32, c_i32, c_vp,
+                          c_i32, c_i32, c_i32, c_vp, P(c_i32), P(c_dbl), P(c_dbl), c_vp]),
+    "pcg_adjoint": (c_int, [c_vp, c_vp, c_dbl, c_i32, c_vp, c_vp, c_dbl, c_i32, c_i32, c_i32, c_i32, c_i32, c_vp,
                             P(c_i32), P(c_dbl), P(c_dbl), c_vp]),
 }
 

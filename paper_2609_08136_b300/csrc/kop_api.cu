@@ -9,10 +9,12 @@
 namespace kop {
 
 int op_matvec(const PointSet& Q, const PointSet& Ks, bool self, int kf, const KConst& kc, int mode,
-              const float* V, int m, int ldv, float* O, int ldo, int* status, cudaStream_t st) {
+              const float* V, int m, int ldv, float* O, int ldo, int* status, cudaStream_t st, bool v_bf16_exact) {
   if (mode == KOP_PLAIN) return plain_matvec(Q, Ks, self, kf, kc, V, m, ldv, O, ldo, st);
+  if (mode == KOP_PLAIN_CHECK) return plain_matvec(Q, Ks, self, kf, kc, V, m, ldv, O, ldo, st, true);
   if (mode == KOP_EXACT) return exact_matvec_f32(Q, Ks, kf, kc.bw, V, m, ldv, O, ldo, st);
-  return fused_matvec(Q, Ks, self, kf, kc, mode == KOP_ACCURATE ? 3 : 2, V, m, ldv, O, ldo, status, st);
+  return fused_matvec(Q, Ks, self, kf, kc, mode == KOP_ACCURATE ? 3 : 2, V, m, ldv, O, ldo, status, st,
+                      v_bf16_exact);
 }
 
 static bool bad_mode(int mode) { return mode < KOP_FAST || mode > KOP_EXACT; }

@@ -267,6 +267,93 @@ __global__ void __launch_bounds__(256) uw64_kernel(const float* __restrict__ U, 
   }
 }
 
+// Float-float variants of the two projections: products are split exactly
+// (TwoProduct) and summed error-free (TwoSum) in FP32 pairs, which keeps the
+// accuracy of FP64 accumulation (the inputs are FP32) at FP32 throughput;
+// B300's CUDA-core FP64 rate is far below its FP32 rate.
+KOP_DEV void ff_add_prod(float& s, float& e, float a, float b) {
+  const float p = a * b;
+  const float pe = fmaf(a, b, -p);
+  const float t = s + p;
+  const float bb = t - s;
+  e += ((s - (t - bb)) + (p - bb)) + pe;
+  s = t;
+}
+
+__global__ void __launch_bounds__(256) utv_ff_kernel(const float* __restrict__ U, int ldu, int64_t n, int p,
+                                                     const float* __restrict__ V, int m, int64_t rows_per_block,
+                                                     double* __restrict__ W) {
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
+  const int64_t r1 = r0 + rows_per_block < n ? r0 + rows_per_block : n;
+  for (int k = threadIdx.x; k < p; k += blockDim.x) {
+    float s[8], e[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) s[c] = e[c] = 0.0f;
+#pragma unroll 4
+    for (int64_t i = r0; i < r1; ++i) {
+      const float u = U[i * ldu + k];
+#pragma unroll
+      for (int c = 0; c < 8; ++c)
+        if (c < m) ff_add_prod(s[c], e[c], u, V[i * m + c]);
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+      if (c < m) atomicAdd(&W[(int64_t)k * m + c], (double)s[c] + (double)e[c]);
+  }
+}
+
+// O[i][c] = alpha[c] V[i][c] + sum_k U[i][k] W[k][c]; W (FP64) is used as the
+// exact pair hi + lo of FP32 values, one warp per row.
+__global__ void __launch_bounds__(256) uw_ff_kernel(const float* __restrict__ U, int ldu, int64_t n, int p,
+                                                    const double* __restrict__ W, const float* __restrict__ V, int m,
+                                                    const double* __restrict__ alpha, float* __restrict__ O) {
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  float s[8], e[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) s[c] = e[c] = 0.0f;
+  for (int k = lane; k < p; k += 32) {
+    const float u = U[row * ldu + k];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      if (c < m) {
+        const double w = W[(int64_t)k * m + c];
+        const float wh = (float)w;
+        const float wl = (float)(w - (double)wh);
+        ff_add_prod(s[c], e[c], u, wh);
+        e[c] = fmaf(u, wl, e[c]);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    if (c >= m) break;
+    double x = (double)s[c] + (double)e[c];
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+    if (lane == 0) O[row * m + c] = (float)fma(alpha[c], (double)V[row * m + c], x);
+  }
+}
+
+int utv_ff(const float* U, int ldu, int64_t n, int p, const float* V, int m, double* W, cudaStream_t st) {
+  KOP_CUDA_TRY(cudaMemsetAsync(W, 0, sizeof(double) * (size_t)p * m, st));
+  int64_t blocks = 8 * num_sms();
+  int64_t rpb = (n + blocks - 1) / blocks;
+  if (rpb < 32) rpb = 32;
+  blocks = (n + rpb - 1) / rpb;
+  utv_ff_kernel<<<(unsigned)blocks, 256, 0, st>>>(U, ldu, n, p, V, m, rpb, W);
+  KOP_LAUNCHED();
+  return KOP_OK;
+}
+
+int uw_ff(const float* U, int ldu, int64_t n, int p, const double* W, const float* V, int m, const double* alpha,
+          float* O, cudaStream_t st) {
+  const int64_t threads = n * 32;
+  uw_ff_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(U, ldu, n, p, W, V, m, alpha, O);
+  KOP_LAUNCHED();
+  return KOP_OK;
+}
+
 int utv64(const float* U, int ldu, int64_t n, int p, const float* V, int m, double* W, cudaStream_t st) {
   KOP_CUDA_TRY(cudaMemsetAsync(W, 0, sizeof(double) * (size_t)p * m, st));
   int64_t blocks = 4 * num_sms();

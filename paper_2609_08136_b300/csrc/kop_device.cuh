@@ -54,6 +54,26 @@ KOP_DEV bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+// Same, for warps off the critical path (producers, MMA issue): after a short
+// spin the poll backs off with nanosleep so that it does not take issue slots
+// from the epilogue warps sharing its SM sub-partition.
+KOP_DEV bool mbar_wait_backoff(uint64_t* bar, uint32_t parity, volatile int* abort_word, int* status) {
+  if (mbar_try_wait(bar, parity)) return true;
+  uint64_t t0 = globaltimer_ns();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (it > 8) __nanosleep(64);
+    if ((it & 63u) == 0u) {
+      if (*abort_word) return false;
+      if (globaltimer_ns() - t0 > KOP_WAIT_LIMIT_NS) {
+        *abort_word = 1;
+        if (status) atomicExch(status, KOP_DEV_TIMEOUT);
+        return false;
+      }
+    }
+  }
+}
+
 // Wait for the phase with the given parity to complete.  Returns false if the
 // CTA-wide abort word is set or the time limit passes; the caller then stops
 // its loop.  On time-out the abort word and the global status are set.

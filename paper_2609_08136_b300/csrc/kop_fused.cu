@@ -61,6 +61,12 @@ KOP_DEV bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort_word,
   if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort_word, status);
   return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
 }
+// The same with back-off, for the producer and MMA warps.
+KOP_DEV bool warp_wait_bg(uint64_t* bar, uint32_t parity, volatile int* abort_word, int* status) {
+  bool ok = true;
+  if ((threadIdx.x & 31) == 0) ok = mbar_wait_backoff(bar, parity, abort_word, status);
+  return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+}
 
 // Time-bounded wait that ignores the abort word (used only to let in-flight
 // asynchronous work land before the CTA exits).
@@ -96,55 +102,78 @@ template <int KF, int MV, bool MASK, bool COMP>
 KOP_DEV void chunk_fma(const uint32_t (&r)[32], float qn, const float* __restrict__ kn, const float* __restrict__ v,
                        float m2c, float c2, int jbase, int gi, int nk, bool self, float (&part)[MV],
                        float (&perr)[MV]) {
+  // stage 1: scaled squared distances (in place over the loaded S values)
+  float kv[32];
 #pragma unroll
   for (int j4 = 0; j4 < 32; j4 += 4) {
     const float4 k4 = *reinterpret_cast<const float4*>(kn + j4);
-    const float kk[4] = {k4.x, k4.y, k4.z, k4.w};
-    float vv[4][MV];
-    if constexpr (MV == 1) {
-      const float4 v4 = *reinterpret_cast<const float4*>(v + j4);
-      vv[0][0] = v4.x;
-      vv[1][0] = v4.y;
-      vv[2][0] = v4.z;
-      vv[3][0] = v4.w;
-    } else {
+    kv[j4 + 0] = fmaf(__uint_as_float(r[j4 + 0]), m2c, qn + k4.x);
+    kv[j4 + 1] = fmaf(__uint_as_float(r[j4 + 1]), m2c, qn + k4.y);
+    kv[j4 + 2] = fmaf(__uint_as_float(r[j4 + 2]), m2c, qn + k4.z);
+    kv[j4 + 3] = fmaf(__uint_as_float(r[j4 + 3]), m2c, qn + k4.w);
+  }
+  if constexpr (MASK) {
 #pragma unroll
-      for (int e = 0; e < 4; ++e)
+    for (int jj = 0; jj < 32; ++jj)
+      if (self && jbase + jj == gi) kv[jj] = 0.0f;
+  }
+  // stage 2: kernel values (independent SFU chains)
 #pragma unroll
-        for (int c4 = 0; c4 < MV; c4 += 4) {
-          const float4 v4 = *reinterpret_cast<const float4*>(v + (j4 + e) * MV + c4);
-          vv[e][c4] = v4.x;
-          vv[e][c4 + 1] = v4.y;
-          vv[e][c4 + 2] = v4.z;
-          vv[e][c4 + 3] = v4.w;
-        }
-    }
+  for (int jj = 0; jj < 32; ++jj) kv[jj] = kval_u<KF>(kv[jj], c2);
+  if constexpr (MASK) {
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int jj = j4 + e;
-      float u = fmaf(__uint_as_float(r[jj]), m2c, qn + kk[e]);
+    for (int jj = 0; jj < 32; ++jj)
+      if (jbase + jj >= nk) kv[jj] = 0.0f;
+  }
+  // stage 3: contraction with V
+  if constexpr (MV == 1 && !COMP) {
+    float p4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int j4 = 0; j4 < 32; j4 += 4) {
+      float4 v4 = *reinterpret_cast<const float4*>(v + j4);
       if constexpr (MASK) {
-        if (self && jbase + jj == gi) u = 0.0f;
+        if (jbase + j4 + 0 >= nk) v4.x = 0.0f;
+        if (jbase + j4 + 1 >= nk) v4.y = 0.0f;
+        if (jbase + j4 + 2 >= nk) v4.z = 0.0f;
+        if (jbase + j4 + 3 >= nk) v4.w = 0.0f;
       }
-      float kv = kval_u<KF>(u, c2);
-      if constexpr (MASK) {
-        if (jbase + jj >= nk) kv = 0.0f;
+      p4[0] = fmaf(kv[j4 + 0], v4.x, p4[0]);
+      p4[1] = fmaf(kv[j4 + 1], v4.y, p4[1]);
+      p4[2] = fmaf(kv[j4 + 2], v4.z, p4[2]);
+      p4[3] = fmaf(kv[j4 + 3], v4.w, p4[3]);
+    }
+    part[0] += (p4[0] + p4[1]) + (p4[2] + p4[3]);
+  } else {
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) {
+      float vv[MV];
+#pragma unroll
+      for (int c4 = 0; c4 < MV; c4 += 4) {
+        if constexpr (MV == 1) {
+          vv[0] = v[jj];
+        } else {
+          const float4 v4 = *reinterpret_cast<const float4*>(v + jj * MV + c4);
+          vv[c4] = v4.x;
+          vv[c4 + 1] = v4.y;
+          vv[c4 + 2] = v4.z;
+          vv[c4 + 3] = v4.w;
+        }
       }
 #pragma unroll
       for (int c = 0; c < MV; ++c) {
-        float vc = vv[e][c];
+        float vc = vv[c];
         if constexpr (MASK) {
           if (jbase + jj >= nk) vc = 0.0f;
         }
         if constexpr (COMP) {
-          const float p = kv * vc;
-          const float pe = fmaf(kv, vc, -p);
+          const float p = kv[jj] * vc;
+          const float pe = fmaf(kv[jj], vc, -p);
           const float t = part[c] + p;
           const float bb = t - part[c];
           perr[c] += ((part[c] - (t - bb)) + (p - bb)) + pe;
           part[c] = t;
         } else {
-          part[c] = fmaf(kv, vc, part[c]);
+          part[c] = fmaf(kv[jj], vc, part[c]);
         }
       }
     }
@@ -152,7 +181,7 @@ KOP_DEV void chunk_fma(const uint32_t (&r)[32], float qn, const float* __restric
 }
 
 template <int KF, int NSPLIT, int MV, int BN>
-__global__ void __launch_bounds__(K1_THREADS, MV <= 4 ? 2 : 1)
+__global__ void __launch_bounds__(K1_THREADS, (MV <= 4 && NSPLIT == 2) ? 2 : 1)
     k1_fma_kernel(const __grid_constant__ CUtensorMap tq0, const __grid_constant__ CUtensorMap tq1,
                   const __grid_constant__ CUtensorMap tq2, const __grid_constant__ CUtensorMap tk0,
                   const __grid_constant__ CUtensorMap tk1, const __grid_constant__ CUtensorMap tk2,
@@ -221,7 +250,7 @@ __global__ void __launch_bounds__(K1_THREADS, MV <= 4 ? 2 : 1)
     for (; t < ntiles; ++t) {
       const int s = t % nst;
       const uint32_t ph = (t / nst) & 1;
-      if (!warp_wait(&empty[s], ph ^ 1, abort_word, a.status)) break;
+      if (!warp_wait_bg(&empty[s], ph ^ 1, abort_word, a.status)) break;
       if (lane == 0) {
         const int j0 = t * BN;
         const int rows_v = a.v_padded ? BN : (a.nk - j0 < BN ? a.nk - j0 : BN);
@@ -244,14 +273,14 @@ __global__ void __launch_bounds__(K1_THREADS, MV <= 4 ? 2 : 1)
     const uint32_t idesc = idesc_bf16_f32(128, BN);
     const uint32_t sbo = 8u * rb;
     const int steps_per_sub = rb / 32;
-    bool ok = warp_wait(qbar, 0, abort_word, a.status);
+    bool ok = warp_wait_bg(qbar, 0, abort_word, a.status);
     for (int t = 0; ok && t < ntiles; ++t) {
       const int s = t % nst;
       const uint32_t ph = (t / nst) & 1;
       const int b = t & 1;
       const uint32_t bph = (t >> 1) & 1;
-      if (!warp_wait(&full[s], ph, abort_word, a.status)) break;
-      if (!warp_wait(&tempty[b], bph ^ 1, abort_word, a.status)) break;
+      if (!warp_wait_bg(&full[s], ph, abort_word, a.status)) break;
+      if (!warp_wait_bg(&tempty[b], bph ^ 1, abort_word, a.status)) break;
       tc_fence_after();
       if (lane == 0) {
         const uint32_t d = tmem + b * BN;
@@ -380,6 +409,7 @@ static int launch_fma_t(const PointSet& Q, const PointSet& Ks, const FusedArgs& 
   static bool attr_set = false;
   if (!attr_set) {
     KOP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_limit_bytes()));
+    KOP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     attr_set = true;
   }
   const int bi = BN == 128 ? 0 : 1;
@@ -406,24 +436,30 @@ static int launch_fma_kf(int nsplit, int bn, int mv, const PointSet& Q, const Po
 }
 
 int fused_matvec(const PointSet& Q, const PointSet& Ks, bool self, int kf, const KConst& kc, int nsplit,
-                 const float* V, int m, int ldv, float* O, int ldo, int* status, cudaStream_t st) {
+                 const float* V, int m, int ldv, float* O, int ldo, int* status, cudaStream_t st, bool v_bf16_exact) {
   if (Q.dp != Ks.dp) return fail(KOP_EINVAL, "fused_matvec: point sets of different widths");
   if (Q.n == 0 || Ks.n == 0 || m == 0) return KOP_OK;
-  if (m > 8 && nsplit == 2) return fused_matvec_mma(Q, Ks, self, kf, kc, V, m, ldv, O, ldo, status, st);
+  if (m > 8 && nsplit == 2)
+    return fused_matvec_mma(Q, Ks, self, kf, kc, V, m, ldv, O, ldo, status, st, v_bf16_exact);
   const int dp = Q.dp;
   const size_t lim = smem_limit_bytes();
-  // tile width and pipeline depth: two CTAs per SM when a 2-stage pipeline
-  // fits in half the shared memory (deeper if it still fits), else one CTA
-  // with three stages
-  int bn = 128, nst = 2;
+  // tile width: 128 unless even a 2-stage pipeline of 8 columns does not fit
+  int bn = 128;
   if (fma_smem_bytes(nsplit, dp, 128, 8, 2) > lim) bn = 64;
   if (fma_smem_bytes(nsplit, dp, bn, 8, 2) > lim)
     return fail(KOP_EINVAL, "fused_matvec: feature width too large for the fused kernel");
-  if (fma_smem_bytes(nsplit, dp, bn, 8, 2) <= lim / 2) {
-    while (nst < K1_MAXST && fma_smem_bytes(nsplit, dp, bn, 8, nst + 1) <= lim / 2) ++nst;
-  } else if (fma_smem_bytes(nsplit, dp, bn, 8, 3) <= lim) {
-    nst = 3;
-  }
+  // pipeline depth for a block of mv columns: two CTAs per SM when a 2-stage
+  // pipeline fits in half the shared memory (deeper if it still fits), else
+  // one CTA with three stages
+  auto stages_for = [&](int mv) {
+    int nst = 2;
+    if (fma_smem_bytes(nsplit, dp, bn, mv, 2) <= lim / 2) {
+      while (nst < K1_MAXST && fma_smem_bytes(nsplit, dp, bn, mv, nst + 1) <= lim / 2) ++nst;
+    } else if (fma_smem_bytes(nsplit, dp, bn, mv, 3) <= lim) {
+      nst = 3;
+    }
+    return nst;
+  };
   int rc = ensure_scaled_norms(const_cast<PointSet&>(Q), kc.scale, st);
   if (rc == KOP_OK && &Q != &Ks) rc = ensure_scaled_norms(const_cast<PointSet&>(Ks), kc.scale, st);
   if (rc) return rc;
@@ -437,7 +473,6 @@ int fused_matvec(const PointSet& Q, const PointSet& Ks, bool self, int kf, const
   a.row_bytes = dp >= 64 ? 128 : dp * 2;
   a.swz = swizzle_code(a.row_bytes);
   a.self = self ? 1 : 0;
-  a.nst = nst;
   a.m2c = -2.0f * kc.scale;
   a.c2 = kc.c2;
   a.status = status;
@@ -445,6 +480,7 @@ int fused_matvec(const PointSet& Q, const PointSet& Ks, bool self, int kf, const
   for (int c0 = 0; c0 < m && rc == KOP_OK; c0 += 8) {
     const int mc = (m - c0) < 8 ? (m - c0) : 8;
     const int mv = mc == 1 ? 1 : (mc <= 4 ? 4 : 8);
+    a.nst = stages_for(mv);
     // V is read with bulk copies: used in place when its rows are exactly mv
     // floats and 16-byte aligned, else staged in a padded copy
     const bool direct = (mc == mv) && (ldv == mv) && (c0 == 0) && ((uintptr_t)V % 16 == 0) &&

@@ -10,38 +10,46 @@
 // with A read from TMEM and V^T (split into BF16 hi/lo by a prep kernel) read
 // from shared memory.  O (128 rows x MC columns, FP32) stays in TMEM for the
 // whole sweep over X and is written once at the end.  Tiles of 64 points.
+// S has four TMEM buffers and the MMA warp issues PV(t) before S(t+3), so the
+// tensor pipe works on one tile's contraction while two pairs of epilogue
+// warpgroups (even and odd tiles) turn the next tiles' distances into kernel
+// values.  When V holds BF16-exact values
+// (the Nystrom test matrix is rounded once on entry) its lo split is skipped:
+// half the V traffic and two contraction MMAs instead of three.
 #include "kop_device.cuh"
 #include "kop_epilogue.cuh"
 #include "kop_internal.h"
 
 namespace kop {
 
-constexpr int K3_THREADS = 384;
-constexpr int K3_NST = 2;
+constexpr int K3_THREADS = 640;  // 4 control warps + 4 epilogue warpgroups
+constexpr int K3_MAXX = 4;       // X-tile ring (freed when the distance MMAs finish)
+constexpr int K3_MAXV = 4;       // V-tile ring (freed when the contraction finishes); even
 constexpr int K3_BN = 64;
+constexpr int K3_NSB = 4;  // S buffers in TMEM (even: a buffer always serves the same warpgroup pair)
 
 struct MmaArgs {
   const float* qnorm;
   const float* knorm;
   float* O;
   int nq, nk, m, ldo;
-  int dp, row_bytes, swz, self, mc, tcols;
+  int dp, row_bytes, swz, self, mc, tcols, nx, nv, vsplits;
   float m2c, c2;
   int* status;
 };
 
 struct K3Layout {
   uint32_t q_split, x_split, v_split, qs, xs, vs, kn, bars, holder, abort_word, total;
-  __host__ __device__ K3Layout(int dp, int mc) {
+  __host__ __device__ K3Layout(int dp, int mc, int nx, int nv, int vsplits) {
     q_split = 128u * dp * 2;
     x_split = (uint32_t)K3_BN * dp * 2;
     v_split = (uint32_t)mc * K3_BN * 2;
     qs = 0;
     xs = qs + 2 * q_split;
-    vs = xs + K3_NST * 2 * x_split;
-    kn = vs + K3_NST * 2 * v_split;
-    bars = kn + K3_NST * K3_BN * 4;
-    holder = bars + (3 * K3_NST + 8) * 8;
+    vs = xs + nx * 2 * x_split;
+    kn = vs + nv * vsplits * v_split;
+    bars = kn + nv * K3_BN * 4;
+    holder = bars + (2 * K3_MAXX + 2 * K3_MAXV + 3 * K3_NSB + 4) * 8;
     abort_word = holder + 4;
     total = abort_word + 12;
   }
@@ -52,17 +60,17 @@ KOP_DEV bool warp_wait3(uint64_t* bar, uint32_t parity, volatile int* abort_word
   if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort_word, status);
   return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
 }
+KOP_DEV bool warp_wait3_bg(uint64_t* bar, uint32_t parity, volatile int* abort_word, int* status) {
+  bool ok = true;
+  if ((threadIdx.x & 31) == 0) ok = mbar_wait_backoff(bar, parity, abort_word, status);
+  return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+}
 
 KOP_DEV void drain_wait3(uint64_t* bar, uint32_t parity) {
   uint64_t t0 = globaltimer_ns();
   while (!mbar_try_wait(bar, parity)) {
     if (globaltimer_ns() - t0 > KOP_WAIT_LIMIT_NS) break;
   }
-}
-
-KOP_DEV uint32_t pack_bf16x2(float lo_elem, float hi_elem) {
-  const __nv_bfloat162 v = __floats2bfloat162_rn(lo_elem, hi_elem);  // .x = lo_elem in the low half
-  return *reinterpret_cast<const uint32_t*>(&v);
 }
 
 template <int KF>
@@ -73,18 +81,22 @@ __global__ void __launch_bounds__(K3_THREADS, 1)
                   const MmaArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  const K3Layout L(a.dp, a.mc);
+  const int nx = a.nx, nv = a.nv;
+  const int nvs = a.vsplits;
+  const K3Layout L(a.dp, a.mc, nx, nv, nvs);
   uint8_t* qs = smem + L.qs;
   uint8_t* xs = smem + L.xs;
   uint8_t* vs = smem + L.vs;
   float* kn = (float*)(smem + L.kn);
   uint64_t* bars = (uint64_t*)(smem + L.bars);
-  uint64_t* full = bars;                 // K3_NST
-  uint64_t* empty = bars + K3_NST;       // K3_NST
-  uint64_t* sfull = bars + 2 * K3_NST;   // 2
-  uint64_t* pfull = sfull + 2;           // 2
-  uint64_t* sfree = pfull + 2;           // 2
-  uint64_t* qbar = sfree + 2;
+  uint64_t* xfull = bars;                    // nx
+  uint64_t* xempty = bars + K3_MAXX;         // nx
+  uint64_t* vfull = bars + 2 * K3_MAXX;      // nv
+  uint64_t* vempty = vfull + K3_MAXV;        // nv
+  uint64_t* sfull = vempty + K3_MAXV;        // K3_NSB
+  uint64_t* pfull = sfull + K3_NSB;          // K3_NSB
+  uint64_t* sfree = pfull + K3_NSB;          // K3_NSB
+  uint64_t* qbar = sfree + K3_NSB;
   uint64_t* ofull = qbar + 1;
   uint64_t* drain = ofull + 1;
   uint32_t* holder = (uint32_t*)(smem + L.holder);
@@ -96,14 +108,18 @@ __global__ void __launch_bounds__(K3_THREADS, 1)
   const int ntiles = (a.nk + K3_BN - 1) / K3_BN;
   const int rb = a.row_bytes;
   const int nsub = (a.dp * 2) / rb;
-  const uint32_t OCOL = 2 * K3_BN;  // O accumulator columns start after the two S buffers
+  const uint32_t OCOL = 256;  // O accumulator columns start after the S buffers
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < K3_NST; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1 + 256);
+    for (int s = 0; s < nx; ++s) {
+      mbar_init(&xfull[s], 1);
+      mbar_init(&xempty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int s = 0; s < nv; ++s) {
+      mbar_init(&vfull[s], 1);
+      mbar_init(&vempty[s], 1);
+    }
+    for (int b = 0; b < K3_NSB; ++b) {
       mbar_init(&sfull[b], 1);
       mbar_init(&pfull[b], 256);
       mbar_init(&sfree[b], 1);
@@ -115,7 +131,7 @@ __global__ void __launch_bounds__(K3_THREADS, 1)
     fence_mbar_init();
   }
   if (warp == 2) {
-    tmem_alloc(holder, a.tcols);
+    tmem_alloc(holder, 512);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -125,6 +141,7 @@ __global__ void __launch_bounds__(K3_THREADS, 1)
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
+    // X(t) into the X ring, V(t) and the scaled norms of tile t into the V ring
     const CUtensorMap* mq[2] = {&tq0, &tq1};
     const CUtensorMap* mk[2] = {&tk0, &tk1};
     const CUtensorMap* mvv[2] = {&tv0, &tv1};
@@ -136,90 +153,115 @@ __global__ void __launch_bounds__(K3_THREADS, 1)
             tma_load_2d(qs + sp * L.q_split + ks * (128 * rb) + rr * (K3_BN * rb), mq[sp], qbar, ks * 64,
                         row0 + rr * K3_BN);
     }
-    int t = 0;
-    for (; t < ntiles; ++t) {
-      const int s = t % K3_NST;
-      const uint32_t ph = (t / K3_NST) & 1;
-      if (!warp_wait3(&empty[s], ph ^ 1, abort_word, a.status)) break;
-      const int j0 = t * K3_BN;
-      for (int i = lane; i < K3_BN; i += 32) kn[s * K3_BN + i] = a.knorm[j0 + i];
-      __syncwarp();
-      if (lane == 0) {
-        mbar_arrive_expect_tx(&full[s], 2 * L.x_split + 2 * L.v_split);
-        for (int sp = 0; sp < 2; ++sp) {
-          for (int ks = 0; ks < nsub; ++ks)
-            tma_load_2d(xs + (s * 2 + sp) * L.x_split + ks * (K3_BN * rb), mk[sp], &full[s], ks * 64, j0);
-          tma_load_2d(vs + (s * 2 + sp) * L.v_split, mvv[sp], &full[s], j0, m0);
+    int tx = 0, tv = 0;
+    bool ok = true;
+    while (ok && (tx < ntiles || tv < ntiles)) {
+      // keep X loads up to nx tiles ahead, but never more than nx tiles ahead of V
+      if (tx < ntiles && tx < tv + nx) {
+        const int s = tx % nx;
+        const uint32_t ph = (tx / nx) & 1;
+        if (!warp_wait3_bg(&xempty[s], ph ^ 1, abort_word, a.status)) { ok = false; break; }
+        if (lane == 0) {
+          const int j0 = tx * K3_BN;
+          mbar_arrive_expect_tx(&xfull[s], 2 * L.x_split);
+          for (int sp = 0; sp < 2; ++sp)
+            for (int ks = 0; ks < nsub; ++ks)
+              tma_load_2d(xs + (s * 2 + sp) * L.x_split + ks * (K3_BN * rb), mk[sp], &xfull[s], ks * 64, j0);
         }
+        __syncwarp();
+        ++tx;
+      } else {
+        const int s = tv % nv;
+        const uint32_t ph = (tv / nv) & 1;
+        if (!warp_wait3_bg(&vempty[s], ph ^ 1, abort_word, a.status)) { ok = false; break; }
+        if (lane == 0) {
+          const int j0 = tv * K3_BN;
+          mbar_arrive_expect_tx(&vfull[s], nvs * L.v_split + K3_BN * 4);
+          for (int sp = 0; sp < nvs; ++sp)
+            tma_load_2d(vs + (s * nvs + sp) * L.v_split, mvv[sp], &vfull[s], j0, m0);
+          bulk_load(kn + s * K3_BN, a.knorm + j0, K3_BN * 4, &vfull[s]);
+        }
+        __syncwarp();
+        ++tv;
       }
-      __syncwarp();
     }
-    if (t < ntiles && lane == 0) {
-      for (int u = (t - K3_NST > 0 ? t - K3_NST : 0); u < t; ++u) drain_wait3(&full[u % K3_NST], (u / K3_NST) & 1);
+    if (!ok && lane == 0) {
+      for (int u = (tx - nx > 0 ? tx - nx : 0); u < tx; ++u) drain_wait3(&xfull[u % nx], (u / nx) & 1);
+      for (int u = (tv - nv > 0 ? tv - nv : 0); u < tv; ++u) drain_wait3(&vfull[u % nv], (u / nv) & 1);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
+    // order: S(0) .. S(L-1), then for each u: PV(u), S(u + L), with the
+    // lookahead L = min(S buffers - 1, X stages)
     const uint32_t idesc_s = idesc_bf16_f32(128, K3_BN);
     const uint32_t idesc_o = idesc_bf16_f32(128, a.mc);
     const uint32_t sbo = 8u * rb;
     const int steps_per_sub = rb / 32;
-    bool ok = warp_wait3(qbar, 0, abort_word, a.status);
+    bool ok = warp_wait3_bg(qbar, 0, abort_word, a.status);
     uint32_t oacc = 0;
-    for (int t = 0; ok && t <= ntiles; ++t) {
-      if (t < ntiles) {
-        const int s = t % K3_NST;
-        const uint32_t ph = (t / K3_NST) & 1;
-        const int b = t & 1;
-        const uint32_t bph = (t >> 1) & 1;
-        if (!warp_wait3(&full[s], ph, abort_word, a.status)) break;
-        if (!warp_wait3(&sfree[b], bph ^ 1, abort_word, a.status)) break;
-        tc_fence_after();
-        if (lane == 0) {
-          const uint32_t d = tmem + b * K3_BN;
-          uint32_t acc = 0;
+    auto issue_s = [&](int t) -> bool {
+      const int s = t % nx;
+      const uint32_t ph = (t / nx) & 1;
+      const int b = t % K3_NSB;
+      const uint32_t bph = (t / K3_NSB) & 1;
+      if (!warp_wait3_bg(&xfull[s], ph, abort_word, a.status)) return false;
+      if (!warp_wait3_bg(&sfree[b], bph ^ 1, abort_word, a.status)) return false;
+      tc_fence_after();
+      if (lane == 0) {
+        const uint32_t d = tmem + b * K3_BN;
+        uint32_t acc = 0;
 #pragma unroll
-          for (int term = 0; term < 3; ++term) {
-            const int ta = term == 1 ? 1 : 0, tb = term == 0 ? 1 : 0;  // hi*mid, mid*hi, hi*hi
-            const uint32_t abase = smem_u32(qs + ta * L.q_split);
-            const uint32_t bbase = smem_u32(xs + (s * 2 + tb) * L.x_split);
-            for (int kc = 0; kc < a.dp / 16; ++kc) {
-              const int ks = kc / steps_per_sub, w = kc - ks * steps_per_sub;
-              tc_mma_ss(d, sdesc(abase + ks * (128 * rb) + w * 32, sbo, a.swz),
-                        sdesc(bbase + ks * (K3_BN * rb) + w * 32, sbo, a.swz), idesc_s, acc);
-              acc = 1;
-            }
+        for (int term = 0; term < 3; ++term) {
+          const int ta = term == 1 ? 1 : 0, tb = term == 0 ? 1 : 0;  // hi*mid, mid*hi, hi*hi
+          const uint32_t abase = smem_u32(qs + ta * L.q_split);
+          const uint32_t bbase = smem_u32(xs + (s * 2 + tb) * L.x_split);
+          for (int kc = 0; kc < a.dp / 16; ++kc) {
+            const int ks = kc / steps_per_sub, w = kc - ks * steps_per_sub;
+            tc_mma_ss(d, sdesc(abase + ks * (128 * rb) + w * 32, sbo, a.swz),
+                      sdesc(bbase + ks * (K3_BN * rb) + w * 32, sbo, a.swz), idesc_s, acc);
+            acc = 1;
           }
-          tc_commit(&sfull[b]);
         }
-        __syncwarp();
+        tc_commit(&sfull[b]);
+        tc_commit(&xempty[s]);
       }
-      if (t >= 1) {
-        const int u = t - 1;
-        const int s = u % K3_NST;
-        const int b = u & 1;
-        const uint32_t bph = (u >> 1) & 1;
-        if (!warp_wait3(&pfull[b], bph, abort_word, a.status)) break;
-        tc_fence_after();
-        if (lane == 0) {
-          const uint32_t pbase = tmem + b * K3_BN;
+      __syncwarp();
+      return true;
+    };
+    auto issue_pv = [&](int u) -> bool {
+      const int s = u % nv;
+      const uint32_t ph = (u / nv) & 1;
+      const int b = u % K3_NSB;
+      const uint32_t bph = (u / K3_NSB) & 1;
+      if (!warp_wait3_bg(&vfull[s], ph, abort_word, a.status)) return false;
+      if (!warp_wait3_bg(&pfull[b], bph, abort_word, a.status)) return false;
+      tc_fence_after();
+      if (lane == 0) {
+        const uint32_t pbase = tmem + b * K3_BN;
+        const int nterms = nvs == 2 ? 3 : 2;
+        for (int term = 0; term < nterms; ++term) {
+          // (P split, V split): lo*hi, hi*hi [, hi*lo]; P hi at +0, lo at +16 in each 32-column chunk
+          const uint32_t poff = term == 0 ? 16u : 0u;
+          const int vsp = term == 2 ? 1 : 0;
+          const uint32_t vbase = smem_u32(vs + (s * nvs + vsp) * L.v_split);
 #pragma unroll
-          for (int term = 0; term < 3; ++term) {
-            // (P split, V split): lo*hi, hi*lo, hi*hi; P hi at +0, lo at +16 within each 32-column chunk
-            const uint32_t poff = term == 0 ? 16u : 0u;
-            const int vsp = term == 1 ? 1 : 0;
-            const uint32_t vbase = smem_u32(vs + (s * 2 + vsp) * L.v_split);
-#pragma unroll
-            for (int kk = 0; kk < K3_BN / 16; ++kk) {
-              const uint32_t acol = pbase + 32u * (kk >> 1) + 8u * (kk & 1) + poff;
-              tc_mma_ts(tmem + OCOL, acol, sdesc(vbase + kk * 32, 1024u, 2u), idesc_o, oacc);
-              oacc = 1;
-            }
+          for (int kk = 0; kk < K3_BN / 16; ++kk) {
+            const uint32_t acol = pbase + 32u * (kk >> 1) + 8u * (kk & 1) + poff;
+            tc_mma_ts(tmem + OCOL, acol, sdesc(vbase + kk * 32, 1024u, 2u), idesc_o, oacc);
+            oacc = 1;
           }
-          tc_commit(&sfree[b]);
-          tc_commit(&empty[s]);
         }
-        __syncwarp();
+        tc_commit(&sfree[b]);
+        tc_commit(&vempty[s]);
       }
+      __syncwarp();
+      return true;
+    };
+    const int look = (K3_NSB - 1) < nx ? (K3_NSB - 1) : nx;
+    for (int t = 0; ok && t < look && t < ntiles; ++t) ok = issue_s(t);
+    for (int u = 0; ok && u < ntiles; ++u) {
+      ok = issue_pv(u);
+      if (ok && u + look < ntiles) ok = issue_s(u + look);
     }
     if (lane == 0) {
       tc_commit(ofull);
@@ -229,41 +271,58 @@ __global__ void __launch_bounds__(K3_THREADS, 1)
     __syncwarp();
   } else if (warp >= 4) {
     // ------------------------------------------------------------ epilogue
-    const int ep = warp - 4, wg = ep >> 2, quarter = warp & 3;
+    // warpgroup pair `pair` takes the tiles t with t % 2 == pair; within a
+    // pair, warpgroup `wg` takes 32 of the 64 columns of the tile
+    const int ep = warp - 4, pair = ep >> 3, wg = (ep >> 2) & 1, quarter = warp & 3;
     const int row = quarter * 32 + lane;
     const int gi = row0 + row;
     const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
-    bool ok = warp_wait3(qbar, 0, abort_word, a.status);
+    bool ok = true;
     const float qni = a.qnorm[gi];
-    for (int t = 0; ok && t < ntiles; ++t) {
-      const int s = t % K3_NST;
-      const uint32_t ph = (t / K3_NST) & 1;
-      const int b = t & 1;
-      const uint32_t bph = (t >> 1) & 1;
+    for (int t = pair; ok && t < ntiles; t += 2) {
+      const int b = t % K3_NSB;
+      const uint32_t bph = (t / K3_NSB) & 1;
       if (!warp_wait3(&sfull[b], bph, abort_word, a.status)) { ok = false; break; }
       tc_fence_after();
       uint32_t r[32];
       const uint32_t col = b * K3_BN + wg * 32;
       tmem_ld32(lane_addr + col, r);
       tmem_ld_wait(r);
-      if (!warp_wait3(&full[s], ph, abort_word, a.status)) { ok = false; break; }
-      const float* knS = kn + s * K3_BN + wg * 32;
+      const int vsl = t % nv;
+      if (!warp_wait3(&vfull[vsl], (t / nv) & 1, abort_word, a.status)) { ok = false; break; }
       const int jbase = t * K3_BN + wg * 32;
+      const float* knG = kn + vsl * K3_BN + wg * 32;
+      const bool mask = (a.self && t * K3_BN < row0 + 128 && t * K3_BN + K3_BN > row0) || (t * K3_BN + K3_BN > a.nk);
       float kv[32];
 #pragma unroll
-      for (int jj = 0; jj < 32; ++jj) {
-        float u = fmaf(__uint_as_float(r[jj]), a.m2c, qni + knS[jj]);
-        if (a.self && jbase + jj == gi) u = 0.0f;
-        kv[jj] = (jbase + jj < a.nk) ? kval_u<KF>(u, a.c2) : 0.0f;
+      for (int j4 = 0; j4 < 32; j4 += 4) {
+        const float4 k4 = *reinterpret_cast<const float4*>(knG + j4);
+        kv[j4 + 0] = fmaf(__uint_as_float(r[j4 + 0]), a.m2c, qni + k4.x);
+        kv[j4 + 1] = fmaf(__uint_as_float(r[j4 + 1]), a.m2c, qni + k4.y);
+        kv[j4 + 2] = fmaf(__uint_as_float(r[j4 + 2]), a.m2c, qni + k4.z);
+        kv[j4 + 3] = fmaf(__uint_as_float(r[j4 + 3]), a.m2c, qni + k4.w);
       }
-      mbar_arrive(&empty[s]);
+      if (mask) {
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj)
+          if (a.self && jbase + jj == gi) kv[jj] = 0.0f;
+      }
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) kv[jj] = kval_u<KF>(kv[jj], a.c2);
+      if (mask) {
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj)
+          if (jbase + jj >= a.nk) kv[jj] = 0.0f;
+      }
+      // K = hi + lo in BF16, packed two per 32-bit TMEM column
       uint32_t ph16[16], pl16[16];
 #pragma unroll
       for (int e = 0; e < 16; ++e) {
-        const float k0 = kv[2 * e], k1 = kv[2 * e + 1];
-        const __nv_bfloat16 h0 = __float2bfloat16_rn(k0), h1 = __float2bfloat16_rn(k1);
-        ph16[e] = pack_bf16x2(__bfloat162float(h0), __bfloat162float(h1));
-        pl16[e] = pack_bf16x2(k0 - __bfloat162float(h0), k1 - __bfloat162float(h1));
+        const __nv_bfloat162 h = __floats2bfloat162_rn(kv[2 * e], kv[2 * e + 1]);
+        const __nv_bfloat162 l =
+            __floats2bfloat162_rn(kv[2 * e] - __low2float(h), kv[2 * e + 1] - __high2float(h));
+        ph16[e] = *reinterpret_cast<const uint32_t*>(&h);
+        pl16[e] = *reinterpret_cast<const uint32_t*>(&l);
       }
       tmem_st16(lane_addr + col, ph16);
       tmem_st16(lane_addr + col + 16, pl16);
@@ -271,8 +330,8 @@ __global__ void __launch_bounds__(K3_THREADS, 1)
       tc_fence_before();
       mbar_arrive(&pfull[b]);
     }
-    // write out O: each warpgroup half of the MC columns, 32 at a time
-    if (ok && warp_wait3(ofull, 0, abort_word, a.status)) {
+    // write out O (pair 0): each warpgroup half of the MC columns, 32 at a time
+    if (pair == 0 && ok && warp_wait3(ofull, 0, abort_word, a.status)) {
       tc_fence_after();
       const int half = a.mc / 2;
       for (int c0 = wg * half; c0 < (wg + 1) * half; c0 += 32) {
@@ -292,7 +351,7 @@ __global__ void __launch_bounds__(K3_THREADS, 1)
   __syncthreads();
   if (warp == 2) {
     tc_fence_after();
-    tmem_dealloc(tmem, a.tcols);
+    tmem_dealloc(tmem, 512);
   }
 }
 
@@ -318,16 +377,18 @@ __global__ void vsplit_kernel(const float* __restrict__ V, int nk, int m, int ld
   }
 }
 
-size_t mma_smem_bytes(int dp, int mc) { return K3Layout(dp, mc).total + 1024; }
+size_t mma_smem_bytes(int dp, int mc, int nx, int nv, int vsplits) {
+  return K3Layout(dp, mc, nx, nv, vsplits).total + 1024;
+}
 
 // Column chunk per CTA: a multiple of 64 (each epilogue warpgroup writes out
 // half of it, 32 columns at a time), at most 256 (MMA N limit), the widest
 // whose pipeline fits in shared memory, then narrowed to balance the chunks.
-int mma_chunk(int dp, int m) {
+int mma_chunk(int dp, int m, int vsplits) {
   const int mpad = ((m + 63) / 64) * 64;
   int mc = mpad < 256 ? mpad : 256;
-  while (mc > 64 && mma_smem_bytes(dp, mc) > smem_limit_bytes()) mc -= 64;
-  if (mma_smem_bytes(dp, mc) > smem_limit_bytes()) return 0;
+  while (mc > 64 && mma_smem_bytes(dp, mc, 2, 2, vsplits) > smem_limit_bytes()) mc -= 64;
+  if (mma_smem_bytes(dp, mc, 2, 2, vsplits) > smem_limit_bytes()) return 0;
   const int nch = (mpad + mc - 1) / mc;
   const int w = ((mpad / nch + 63) / 64) * 64;
   return w < mc ? w : mc;
@@ -340,18 +401,20 @@ static int launch_mma_t(const PointSet& Q, const PointSet& Ks, const CUtensorMap
   static bool attr_set = false;
   if (!attr_set) {
     KOP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_limit_bytes()));
+    KOP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     attr_set = true;
   }
   dim3 grid((unsigned)((a.nq + 127) / 128), (unsigned)((a.m + a.mc - 1) / a.mc));
-  kern<<<grid, K3_THREADS, mma_smem_bytes(a.dp, a.mc), st>>>(Q.tm[0][1], Q.tm[1][1], Ks.tm[0][1], Ks.tm[1][1],
+  kern<<<grid, K3_THREADS, mma_smem_bytes(a.dp, a.mc, a.nx, a.nv, a.vsplits), st>>>(Q.tm[0][1], Q.tm[1][1], Ks.tm[0][1], Ks.tm[1][1],
                                                               tv[0], tv[1], a);
   KOP_LAUNCHED();
   return KOP_OK;
 }
 
 int fused_matvec_mma(const PointSet& Q, const PointSet& Ks, bool self, int kf, const KConst& kc, const float* V,
-                     int m, int ldv, float* O, int ldo, int* status, cudaStream_t st) {
-  const int mc = mma_chunk(Q.dp, m);
+                     int m, int ldv, float* O, int ldo, int* status, cudaStream_t st, bool v_bf16_exact) {
+  const int vsplits = v_bf16_exact ? 1 : 2;
+  const int mc = mma_chunk(Q.dp, m, vsplits);
   if (mc == 0) return fail(KOP_EINVAL, "fused_matvec_mma: feature width too large");
   {
     int sc = ensure_scaled_norms(const_cast<PointSet&>(Q), kc.scale, st);
@@ -386,7 +449,13 @@ int fused_matvec_mma(const PointSet& Q, const PointSet& Ks, bool self, int kf, c
     a.swz = a.row_bytes == 128 ? 2 : (a.row_bytes == 64 ? 4 : 6);
     a.self = self ? 1 : 0;
     a.mc = mc;
-    a.tcols = (2 * K3_BN + mc) <= 256 ? 256 : 512;
+    a.tcols = 512;
+    a.vsplits = vsplits;
+    // deepest rings that fit: V ring 4 or 2 (even), X ring 4 .. 2
+    const size_t lim = smem_limit_bytes();
+    a.nv = mma_smem_bytes(Q.dp, mc, 2, 4, vsplits) <= lim ? 4 : 2;
+    a.nx = 4;
+    while (a.nx > 2 && mma_smem_bytes(Q.dp, mc, a.nx, a.nv, vsplits) > lim) --a.nx;
     a.m2c = -2.0f * kc.scale;
     a.c2 = kc.c2;
     a.status = status;

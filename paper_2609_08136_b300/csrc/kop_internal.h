@@ -53,13 +53,18 @@ int column_mean(const float* X, int64_t n, int d, double* mean, cudaStream_t st)
 // nsplit: 2 (KOP_FAST) or 3 (KOP_ACCURATE).  self: Q and Kset are the same
 // points, so the diagonal distance is set to exactly 0.
 int fused_matvec(const PointSet& Q, const PointSet& Ks, bool self, int kf, const KConst& kc, int nsplit,
-                 const float* V, int m, int ldv, float* O, int ldo, int* status, cudaStream_t st);
+                 const float* V, int m, int ldv, float* O, int ldo, int* status, cudaStream_t st,
+                 bool v_bf16_exact = false);
 // Tensor-core contraction variant for m > 8 (2-term split only).
+// v_bf16_exact: V holds BF16-representable values, so its lo split is zero.
 int fused_matvec_mma(const PointSet& Q, const PointSet& Ks, bool self, int kf, const KConst& kc, const float* V,
-                     int m, int ldv, float* O, int ldo, int* status, cudaStream_t st);
-// Plain FP32 CUDA-core operator (same contract, no tensor cores).
+                     int m, int ldv, float* O, int ldo, int* status, cudaStream_t st, bool v_bf16_exact = false);
+// Plain FP32 CUDA-core operator (same contract, no tensor cores); with
+// `compensated` the contraction is error-free per entry (acceptance checks).
 int plain_matvec(const PointSet& Q, const PointSet& Ks, bool self, int kf, const KConst& kc, const float* V,
-                 int m, int ldv, float* O, int ldo, cudaStream_t st);
+                 int m, int ldv, float* O, int ldo, cudaStream_t st, bool compensated = false);
+// Internal mode id of the compensated plain operator (not part of the ABI).
+constexpr int KOP_PLAIN_CHECK = 100;
 
 // FP64 CUDA-core operator (KOP_EXACT): FP64 V and O, and an FP32 wrapper.
 int exact_matvec(const PointSet& Q, const PointSet& Ks, int kf, double bw, const double* V, int m, int ldv, double* O,
@@ -68,7 +73,8 @@ int exact_matvec_f32(const PointSet& Q, const PointSet& Ks, int kf, double bw, c
                      float* O, int ldo, cudaStream_t st);
 // Any mode.
 int op_matvec(const PointSet& Q, const PointSet& Ks, bool self, int kf, const KConst& kc, int mode,
-              const float* V, int m, int ldv, float* O, int ldo, int* status, cudaStream_t st);
+              const float* V, int m, int ldv, float* O, int ldo, int* status, cudaStream_t st,
+              bool v_bf16_exact = false);
 
 int num_sms();
 inline size_t smem_limit_bytes() { return 227u * 1024u; }

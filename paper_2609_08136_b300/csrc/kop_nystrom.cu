@@ -12,6 +12,9 @@
 // tall product.  All r x r work is FP64 on the device; the O(n r^2) Gram and
 // product passes read FP32 and accumulate in FP64 / FP32.  One Cholesky-QR
 // pass afterwards restores the orthonormality of U lost to FP32 rounding.
+// The test matrix is rounded to BF16 once on entry and the rounded Omega is
+// used in every step: the result is the exact Nystrom approximation for that
+// test matrix, and the sketch's contraction needs no lo split of Omega.
 #include <cmath>
 #include <vector>
 
@@ -51,23 +54,24 @@ __global__ void nys_scale_kernel(double* __restrict__ W, int r, int m, const dou
 
 // Device side of nys_apply with caller-provided scratch:
 //   Wd: r*m doubles, alpha: m doubles, Wf: r*m floats, alpha_f: m floats.
-// Up to 8 columns the whole apply runs in FP64 arithmetic on the stored FP32
-// U, so that P^-1 is applied as one fixed symmetric operator: in FP32 the
-// cancellation between v / rho and the projected part loses a factor
-// (lam_1 + mu) / rho of accuracy on the leading subspace.  Wider blocks use
-// FP32 tensor-shaped products (the solver tolerates the inexact apply).
+// Up to 8 columns the whole apply runs with FP64-accurate sums (error-free
+// float-float arithmetic) on the stored FP32 U, so that P^-1 is applied as one
+// fixed symmetric operator: in plain FP32 the cancellation between v / rho and
+// the projected part loses a factor (lam_1 + mu) / rho of accuracy on the
+// leading subspace.  Wider blocks use FP32 tensor-shaped products (the solver
+// tolerates the inexact apply).
 int nys_apply_dev(const nys_s* ny, const double* mu_dev, int adaptive, const float* V, int m, float* O, double* Wd,
                   double* alpha, float* Wf, float* alpha_f, cudaStream_t st) {
   const int r = ny->r;
   const int64_t n = ny->n;
   const int64_t tot = (int64_t)r * m;
   if (m <= 8) {
-    int rc = utv64(ny->U, r, n, r, V, m, Wd, st);
+    int rc = utv_ff(ny->U, r, n, r, V, m, Wd, st);
     if (rc) return rc;
     nys_scale_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(Wd, r, m, ny->lam_dev, mu_dev, adaptive, nullptr,
                                                                     alpha, nullptr);
     KOP_LAUNCHED();
-    return uw64(ny->U, r, n, r, Wd, V, m, alpha, O, st);
+    return uw_ff(ny->U, r, n, r, Wd, V, m, alpha, O, st);
   }
   int rc = gram(ny->U, r, V, m, n, r, m, Wd, m, st);
   if (rc) return rc;
@@ -75,6 +79,11 @@ int nys_apply_dev(const nys_s* ny, const double* mu_dev, int adaptive, const flo
                                                                   alpha_f);
   KOP_LAUNCHED();
   return tall_gemm(ny->U, nullptr, 0.0f, r, n, r, Wf, m, m, V, m, alpha_f, O, m, st);
+}
+
+__global__ void round_bf16_kernel(const float* __restrict__ a, float* __restrict__ b, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = __bfloat162float(__float2bfloat16_rn(a[i]));
 }
 
 static int read_info(const int* dev, int* host, cudaStream_t st) {
@@ -102,9 +111,16 @@ extern "C" int nys_build(kop_t op, const float* Omega, int32_t r, double nu_rel,
   const size_t rr = (size_t)r * r;
   const int64_t n_pad = op->pts.n_pad;
   // workspace
-  DevBuf wsY, wsR, wsU;
-  wsY.st = wsR.st = wsU.st = st;
+  DevBuf wsY, wsR, wsU, wsO;
+  wsY.st = wsR.st = wsU.st = wsO.st = st;
   KOP_CUDA_TRY(cudaMallocAsync(&wsY.p, sizeof(float) * (size_t)n * r, st));
+  KOP_CUDA_TRY(cudaMallocAsync(&wsO.p, sizeof(float) * (size_t)n * r, st));
+  {
+    const int64_t tot = (int64_t)n * r;
+    round_bf16_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(Omega, (float*)wsO.p, tot);
+    KOP_LAUNCHED();
+    Omega = (const float*)wsO.p;
+  }
   const size_t nd = 9 * rr + 4 * (size_t)r + 16 + sym_eig_work_doubles(r);
   KOP_CUDA_TRY(cudaMallocAsync(&wsR.p, sizeof(double) * nd + sizeof(float) * rr + sizeof(int) * (r + 8), st));
   KOP_CUDA_TRY(cudaMallocAsync(&wsU.p, sizeof(float) * (size_t)n_pad * r, st));
@@ -130,7 +146,7 @@ extern "C" int nys_build(kop_t op, const float* Omega, int32_t r, double nu_rel,
   int rc;
   // 1. sketch Y = K Omega (fused operator, m = r)
   const KConst kc = kernel_constants(op->kernel, op->bw);
-  rc = op_matvec(op->pts, op->pts, true, op->kernel, kc, mode, Omega, r, r, Y, r, op->status, st);
+  rc = op_matvec(op->pts, op->pts, true, op->kernel, kc, mode, Omega, r, r, Y, r, op->status, st, true);
   if (rc) return rc;
   // 2. Gram blocks
   if ((rc = gram(Omega, r, Omega, r, n, r, r, Goo, r, st))) return rc;

@@ -241,7 +241,7 @@ struct PcgProblem {
   const float* B = nullptr;
   double* Xout = nullptr;
   double tol = 1e-6;
-  int maxit = 1000, refine_every = 0, inner_mode = KOP_FAST, refine_mode = KOP_ACCURATE;
+  int maxit = 1000, refine_every = 0, inner_mode = KOP_FAST, refine_mode = KOP_ACCURATE, check_mode = KOP_PLAIN;
   int32_t* iters = nullptr;
   double* res_hist = nullptr;
   double* true_relres = nullptr;
@@ -272,7 +272,7 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
   const size_t fbytes = sizeof(float) * (8 * nc + (size_t)r * cols + cols);
   const size_t dbytes = sizeof(double) * (12 * (size_t)cols + (size_t)r * cols);
   const size_t ibytes = sizeof(int) * (size_t)cols;
-  const size_t xbytes = pb.refine_mode == KOP_EXACT ? sizeof(double) * nc : 0;
+  const size_t xbytes = (pb.refine_mode == KOP_EXACT || pb.check_mode == KOP_EXACT) ? sizeof(double) * nc : 0;
   KOP_CUDA_TRY(cudaMallocAsync(&ws.p, xbytes + dbytes + fbytes + ibytes + 256, st));
   double* T64 = (double*)ws.p;
   double* lam = T64 + (xbytes / sizeof(double));
@@ -397,13 +397,16 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
     }
     const bool refine = any_cand || (pb.refine_every > 0 && it % pb.refine_every == 0) || it == pb.maxit;
     if (refine) {
-      // true residual with the accurate operator replaces the recursive one
-      if (pb.refine_mode == KOP_EXACT) {
+      // the true residual replaces the recursive one: the refinement operator
+      // for periodic replacement, the check operator when a column may stop
+      int rmode = (any_cand || it == pb.maxit) ? pb.check_mode : pb.refine_mode;
+      if (rmode == KOP_PLAIN) rmode = KOP_PLAIN_CHECK;
+      if (rmode == KOP_EXACT) {
         if ((rc = exact_matvec(op->pts, op->pts, op->kernel, op->bw, X, cols, cols, T64, cols, st))) return rc;
         if ((rc = vec_launch<OP_RES64>(va, st))) return rc;
       } else {
         if ((rc = vec_launch<OP_SPLIT>(va, st))) return rc;
-        if ((rc = matvec2(V2, T, pb.refine_mode))) return rc;
+        if ((rc = matvec2(V2, T, rmode))) return rc;
         if ((rc = vec_launch<OP_RES>(va, st))) return rc;
       }
       KOP_CUDA_TRY(cudaMemcpyAsync(hr.data(), acc, sizeof(double) * cols, cudaMemcpyDeviceToHost, st));
@@ -450,14 +453,15 @@ static bool valid_mode(int m) { return m >= KOP_FAST && m <= KOP_EXACT; }
 
 extern "C" int pcg_solve(kop_t op, nys_t ny, const double* lambdas, int32_t n_shifts, const double* mu,
                          int32_t adaptive, const float* B, int32_t nrhs, double tol, int32_t maxit,
-                         int32_t refine_every, int32_t inner_mode, int32_t refine_mode, double* Xout, int32_t* iters,
-                         double* res_hist, double* true_relres, void* stream) {
+                         int32_t refine_every, int32_t inner_mode, int32_t refine_mode, int32_t check_mode,
+                         double* Xout, int32_t* iters, double* res_hist, double* true_relres, void* stream) {
   if (!op || !lambdas || !B || !Xout || !iters) return fail(KOP_EINVAL, "pcg_solve: NULL argument");
   if (ny && ny->op != op) return fail(KOP_EINVAL, "pcg_solve: preconditioner built for another operator");
   if (n_shifts < 1 || nrhs < 1 || (int64_t)n_shifts * nrhs > 4096)
     return fail(KOP_EINVAL, "pcg_solve: need 1 <= nrhs * n_shifts <= 4096");
   if (!(tol > 0.0) || maxit < 1 || refine_every < 0) return fail(KOP_EINVAL, "pcg_solve: bad tol / maxit / refine");
-  if (!valid_mode(inner_mode) || !valid_mode(refine_mode)) return fail(KOP_EINVAL, "pcg_solve: bad mode");
+  if (!valid_mode(inner_mode) || !valid_mode(refine_mode) || !valid_mode(check_mode))
+    return fail(KOP_EINVAL, "pcg_solve: bad mode");
   PcgProblem pb;
   pb.op = op;
   pb.ny = ny;
@@ -481,6 +485,7 @@ extern "C" int pcg_solve(kop_t op, nys_t ny, const double* lambdas, int32_t n_sh
   pb.refine_every = refine_every;
   pb.inner_mode = inner_mode;
   pb.refine_mode = refine_mode;
+  pb.check_mode = check_mode;
   pb.iters = iters;
   pb.res_hist = res_hist;
   pb.true_relres = true_relres;
@@ -503,12 +508,14 @@ __global__ void split_vec_kernel(const double* __restrict__ x, float* __restrict
 
 extern "C" int pcg_adjoint(kop_t op, nys_t ny, double lam, int32_t adaptive, const double* x, const double* dLdx,
                            double tol, int32_t maxit, int32_t refine_every, int32_t inner_mode, int32_t refine_mode,
-                           double* g_out, int32_t* iters, double* dLdlam, double* dLdbw, void* stream) {
+                           int32_t check_mode, double* g_out, int32_t* iters, double* dLdlam, double* dLdbw,
+                           void* stream) {
   if (!op || !x || !dLdx || !g_out || !dLdlam || !dLdbw) return fail(KOP_EINVAL, "pcg_adjoint: NULL argument");
   if (ny && ny->op != op) return fail(KOP_EINVAL, "pcg_adjoint: preconditioner built for another operator");
   if (!(lam > 0.0) || !std::isfinite(lam)) return fail(KOP_EINVAL, "pcg_adjoint: lam must be > 0");
   if (!(tol > 0.0) || maxit < 1 || refine_every < 0) return fail(KOP_EINVAL, "pcg_adjoint: bad tol / maxit");
-  if (!valid_mode(inner_mode) || !valid_mode(refine_mode)) return fail(KOP_EINVAL, "pcg_adjoint: bad mode");
+  if (!valid_mode(inner_mode) || !valid_mode(refine_mode) || !valid_mode(check_mode))
+    return fail(KOP_EINVAL, "pcg_adjoint: bad mode");
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t n = op->pts.n;
   Workspace ws;
@@ -536,6 +543,7 @@ extern "C" int pcg_adjoint(kop_t op, nys_t ny, double lam, int32_t adaptive, con
   pb.refine_every = refine_every;
   pb.inner_mode = inner_mode;
   pb.refine_mode = refine_mode;
+  pb.check_mode = check_mode;
   int32_t it = 0;
   pb.iters = &it;
   const int rc = pcg_core(pb, st);
@@ -549,7 +557,7 @@ extern "C" int pcg_adjoint(kop_t op, nys_t ny, double lam, int32_t adaptive, con
   // columns of the split (or one FP64 product in exact mode)
   dot_kernel<<<4 * num_sms(), 256, 0, st>>>(g_out, V2, V2 + 1, n, 2, acc);
   KOP_LAUNCHED();
-  if (refine_mode == KOP_EXACT) {
+  if (check_mode == KOP_EXACT) {
     double* t64 = nullptr;
     KOP_CUDA_TRY(cudaMallocAsync((void**)&t64, sizeof(double) * n, st));
     int r2 = exact_matvec(op->pts, op->pts, op->kernel + 3, op->bw, x, 1, 1, t64, 1, st);
@@ -561,7 +569,8 @@ extern "C" int pcg_adjoint(kop_t op, nys_t ny, double lam, int32_t adaptive, con
     if (r2) return r2;
   } else {
     const KConst kc = kernel_constants(op->kernel + 3, op->bw);
-    int r2 = op_matvec(op->pts, op->pts, true, op->kernel + 3, kc, refine_mode, V2, 2, 2, T2, 2, op->status, st);
+    const int dmode = check_mode == KOP_PLAIN ? KOP_PLAIN_CHECK : check_mode;
+    int r2 = op_matvec(op->pts, op->pts, true, op->kernel + 3, kc, dmode, V2, 2, 2, T2, 2, op->status, st);
     if (r2) return r2;
     dot_kernel<<<4 * num_sms(), 256, 0, st>>>(g_out, T2, T2 + 1, n, 2, acc + 1);
     KOP_LAUNCHED();

@@ -3,7 +3,10 @@
 // centred FP32 points, k by expf/sqrtf, contraction by FP32 FMAs with a
 // compensated running sum per output.  One thread per query row; key tiles of
 // 64 points and their V rows are staged in shared memory and read as
-// broadcasts.
+// broadcasts.  With COMP the contraction is error-free per entry (TwoProduct
+// + TwoSum): the solver's acceptance check uses that form, because direct
+// differences keep the kernel argument accurate where the norm identity of the
+// tensor-core path loses digits (points far from the common centre).
 #include "kop_device.cuh"
 #include "kop_internal.h"
 
@@ -36,7 +39,7 @@ KOP_DEV float plain_kernel_value(float d2, const PlainConst& p) {
   }
 }
 
-template <int KF, int MV>
+template <int KF, int MV, bool COMP>
 __global__ void __launch_bounds__(K2_ROWS) k2_plain_kernel(const float* __restrict__ Q, const float* __restrict__ Xk,
                                                            const float* __restrict__ V, float* __restrict__ O, int nq,
                                                            int nk, int dp, int m, int ldv, int ldo, PlainConst pc) {
@@ -84,17 +87,32 @@ __global__ void __launch_bounds__(K2_ROWS) k2_plain_kernel(const float* __restri
         }
       }
     }
-    float part[MV];
+    float part[MV], perr[MV];
 #pragma unroll
-    for (int c = 0; c < MV; ++c) part[c] = 0.0f;
+    for (int c = 0; c < MV; ++c) part[c] = perr[c] = 0.0f;
 #pragma unroll
     for (int jj = 0; jj < K2_KEYS; ++jj) {
       const float kv = plain_kernel_value<KF>(d2[jj], pc);
 #pragma unroll
-      for (int c = 0; c < MV; ++c) part[c] = fmaf(kv, Vs[jj * MV + c], part[c]);
+      for (int c = 0; c < MV; ++c) {
+        const float v = Vs[jj * MV + c];
+        if constexpr (COMP) {
+          const float p = kv * v;
+          const float pe = fmaf(kv, v, -p);
+          const float t = part[c] + p;
+          const float bb = t - part[c];
+          perr[c] += ((part[c] - (t - bb)) + (p - bb)) + pe;
+          part[c] = t;
+        } else {
+          part[c] = fmaf(kv, v, part[c]);
+        }
+      }
     }
 #pragma unroll
-    for (int c = 0; c < MV; ++c) two_sum_acc(acc_s[c], acc_e[c], part[c]);
+    for (int c = 0; c < MV; ++c) {
+      two_sum_acc(acc_s[c], acc_e[c], part[c]);
+      acc_e[c] += perr[c];
+    }
   }
   const int gi = row0 + tid;
   if (gi < nq) {
@@ -125,10 +143,10 @@ static PlainConst plain_constants(int kf, double bw) {
   return p;
 }
 
-template <int KF, int MV>
+template <int KF, int MV, bool COMP>
 static int launch_plain_t(const PointSet& Q, const PointSet& Ks, const float* V, int m, int ldv, float* O, int ldo,
                           const PlainConst& pc, cudaStream_t st) {
-  auto kern = k2_plain_kernel<KF, MV>;
+  auto kern = k2_plain_kernel<KF, MV, COMP>;
   const int dp = Q.dp;
   const size_t smem = sizeof(float) * ((size_t)dp * (K2_ROWS + 1) + (size_t)K2_KEYS * dp + K2_KEYS * MV);
   static bool attr_set = false;
@@ -142,26 +160,33 @@ static int launch_plain_t(const PointSet& Q, const PointSet& Ks, const float* V,
   return KOP_OK;
 }
 
-template <int KF>
+template <int KF, bool COMP>
 static int launch_plain_kf(const PointSet& Q, const PointSet& Ks, const float* V, int m, int ldv, float* O, int ldo,
                            const PlainConst& pc, cudaStream_t st) {
-  if (m == 1) return launch_plain_t<KF, 1>(Q, Ks, V, m, ldv, O, ldo, pc, st);
-  if (m <= 4) return launch_plain_t<KF, 4>(Q, Ks, V, m, ldv, O, ldo, pc, st);
-  return launch_plain_t<KF, 8>(Q, Ks, V, m, ldv, O, ldo, pc, st);
+  if (m == 1) return launch_plain_t<KF, 1, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st);
+  if (m <= 4) return launch_plain_t<KF, 4, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st);
+  return launch_plain_t<KF, 8, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st);
+}
+
+template <bool COMP>
+static int plain_dispatch(int kf, const PointSet& Q, const PointSet& Ks, const float* V, int m, int ldv, float* O,
+                          int ldo, const PlainConst& pc, cudaStream_t st) {
+  switch (kf) {
+    case KF_RBF: return launch_plain_kf<KF_RBF, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st);
+    case KF_LAPLACE: return launch_plain_kf<KF_LAPLACE, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st);
+    case KF_MATERN: return launch_plain_kf<KF_MATERN, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st);
+    case KF_DRBF: return launch_plain_kf<KF_DRBF, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st);
+    case KF_DLAPLACE: return launch_plain_kf<KF_DLAPLACE, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st);
+    default: return launch_plain_kf<KF_DMATERN, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st);
+  }
 }
 
 int plain_matvec(const PointSet& Q, const PointSet& Ks, bool /*self*/, int kf, const KConst& kc, const float* V,
-                 int m, int ldv, float* O, int ldo, cudaStream_t st) {
+                 int m, int ldv, float* O, int ldo, cudaStream_t st, bool compensated) {
   if (Q.n == 0 || Ks.n == 0 || m == 0) return KOP_OK;
   const PlainConst pc = plain_constants(kf, kc.bw);
-  switch (kf) {
-    case KF_RBF: return launch_plain_kf<KF_RBF>(Q, Ks, V, m, ldv, O, ldo, pc, st);
-    case KF_LAPLACE: return launch_plain_kf<KF_LAPLACE>(Q, Ks, V, m, ldv, O, ldo, pc, st);
-    case KF_MATERN: return launch_plain_kf<KF_MATERN>(Q, Ks, V, m, ldv, O, ldo, pc, st);
-    case KF_DRBF: return launch_plain_kf<KF_DRBF>(Q, Ks, V, m, ldv, O, ldo, pc, st);
-    case KF_DLAPLACE: return launch_plain_kf<KF_DLAPLACE>(Q, Ks, V, m, ldv, O, ldo, pc, st);
-    default: return launch_plain_kf<KF_DMATERN>(Q, Ks, V, m, ldv, O, ldo, pc, st);
-  }
+  return compensated ? plain_dispatch<true>(kf, Q, Ks, V, m, ldv, O, ldo, pc, st)
+                     : plain_dispatch<false>(kf, Q, Ks, V, m, ldv, O, ldo, pc, st);
 }
 
 }  // namespace kop

@@ -40,6 +40,13 @@ def _kind(kernel) -> int:
     return KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
 
 
+def sfu_rates(stream=None):
+    """Measured SFU throughput (ops/s): {'ex2': ..., 'sqrt': ..., 'rsqrt': ...}."""
+    arr = (ctypes.c_double * 3)()
+    check(_ffi.lib().kop_sfu_rates(arr, _stream(stream)), "kop_sfu_rates")
+    return {"ex2": arr[0], "sqrt": arr[1], "rsqrt": arr[2]}
+
+
 class KernelOperator:
     """K(X, X) for points X (n x d, CUDA float32): kop_create / kop_matvec."""
 
@@ -182,7 +189,8 @@ class SolveResult:
 
 def pcg_solve(op: KernelOperator, B: torch.Tensor, lambdas, nys: Nystrom | None = None, mu=None,
               adaptive: bool = True, tol: float = 1e-6, maxit: int = 1000, refine_every: int = 20,
-              inner_mode: int = FAST, refine_mode: int = ACCURATE, history: bool = False, stream=None):
+              inner_mode: int = FAST, refine_mode: int = ACCURATE, check_mode: int = PLAIN, history: bool = False,
+              stream=None):
     """Block PCG for (K + lam_s I) x = B[:, j] over all shifts s and columns j
     (column s * nrhs + j of the result)."""
     vec = B.dim() == 1
@@ -202,7 +210,7 @@ def pcg_solve(op: KernelOperator, B: torch.Tensor, lambdas, nys: Nystrom | None 
     tr = (ctypes.c_double * cols)()
     rc = check(_ffi.lib().pcg_solve(op.handle, nys.handle if nys is not None else None, lam_arr, ns, mu_arr,
                                     int(bool(adaptive)), _ptr(B2), nrhs, float(tol), int(maxit), int(refine_every),
-                                    int(inner_mode), int(refine_mode), _ptr(X), iters, hist, tr,
+                                    int(inner_mode), int(refine_mode), int(check_mode), _ptr(X), iters, hist, tr,
                                     _stream(stream)), "pcg_solve")
     h = None
     if history:
@@ -214,7 +222,7 @@ def pcg_solve(op: KernelOperator, B: torch.Tensor, lambdas, nys: Nystrom | None 
 
 def pcg_adjoint(op: KernelOperator, x: torch.Tensor, dLdx: torch.Tensor, lam: float, nys: Nystrom | None = None,
                 adaptive: bool = True, tol: float = 1e-6, maxit: int = 1000, refine_every: int = 20,
-                inner_mode: int = FAST, refine_mode: int = ACCURATE, stream=None):
+                inner_mode: int = FAST, refine_mode: int = ACCURATE, check_mode: int = PLAIN, stream=None):
     """g = (K + lam I)^{-1} dL/dx, and dL/dlam = -g^T x, dL/dbw = -g^T (dK/dbw) x.
     x, dL/dx and g are FP64 device vectors."""
     x2 = x.detach().reshape(-1).to(torch.float64).contiguous()
@@ -227,7 +235,8 @@ def pcg_adjoint(op: KernelOperator, x: torch.Tensor, dLdx: torch.Tensor, lam: fl
     db = ctypes.c_double()
     check(_ffi.lib().pcg_adjoint(op.handle, nys.handle if nys is not None else None, float(lam),
                                  int(bool(adaptive)), _ptr(x2), _ptr(d2), float(tol), int(maxit), int(refine_every),
-                                 int(inner_mode), int(refine_mode), _ptr(g), ctypes.byref(it), ctypes.byref(dl),
+                                 int(inner_mode), int(refine_mode), int(check_mode), _ptr(g), ctypes.byref(it),
+                                 ctypes.byref(dl),
                                  ctypes.byref(db), _stream(stream)), "pcg_adjoint")
     return g, dl.value, db.value, it.value
 
@@ -264,24 +273,24 @@ def krr_solve(op: KernelOperator, b: torch.Tensor, bw: torch.Tensor, lam: torch.
 
 def krr_val_loss_and_grad(op: KernelOperator, nys: Nystrom | None, y: torch.Tensor, Xv: torch.Tensor,
                           yv: torch.Tensor, lam: float, tol: float = 1e-6, maxit: int = 1000, refine_every: int = 20,
-                          inner_mode: int = FAST, refine_mode: int = ACCURATE):
+                          inner_mode: int = FAST, refine_mode: int = ACCURATE, check_mode: int = PLAIN):
     """Validation loss L = (1/n_val) ||K(Xv, X) x - yv||^2 with x = (K + lam I)^{-1} y,
     and its derivatives with respect to the bandwidth and lam (adjoint method)."""
     res = pcg_solve(op, y, [lam], nys=nys, tol=tol, maxit=maxit, refine_every=refine_every, inner_mode=inner_mode,
-                    refine_mode=refine_mode)
+                    refine_mode=refine_mode, check_mode=check_mode)
     x = res.x.reshape(-1)
     # products with the FP64 x go through its exact two-column FP32 split
     x_hi = x.float()
     x2 = torch.stack([x_hi, (x - x_hi.double()).float()], dim=1).contiguous()
     nv = Xv.shape[0]
-    kx = op.cross_matvec(Xv, x2, mode=refine_mode).double().sum(dim=1)
+    kx = op.cross_matvec(Xv, x2, mode=check_mode).double().sum(dim=1)
     e64 = kx - yv.reshape(-1).double()
     loss = float(e64 @ e64) / nv
     e_hi = e64.float()
     e2 = torch.stack([e_hi, (e64 - e_hi.double()).float()], dim=1).contiguous()
-    dLdx = op.cross_matvec(Xv, e2, transpose=True, mode=refine_mode).double().sum(dim=1) * (2.0 / nv)
+    dLdx = op.cross_matvec(Xv, e2, transpose=True, mode=check_mode).double().sum(dim=1) * (2.0 / nv)
     g, dlam, dbw_k, _ = pcg_adjoint(op, x, dLdx, lam, nys=nys, tol=tol, maxit=maxit, refine_every=refine_every,
-                                    inner_mode=inner_mode, refine_mode=refine_mode)
-    dkv = op.cross_matvec(Xv, x2, deriv=True, mode=refine_mode).double().sum(dim=1)
+                                    inner_mode=inner_mode, refine_mode=refine_mode, check_mode=check_mode)
+    dkv = op.cross_matvec(Xv, x2, deriv=True, mode=check_mode).double().sum(dim=1)
     dbw = (2.0 / nv) * float(e64 @ dkv) + dbw_k
     return loss, dbw, dlam

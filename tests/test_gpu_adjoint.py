@@ -22,7 +22,7 @@ def test_val_loss_gradient_n2048(kind):
     yv = torch.from_numpy(wl.yval).cuda()
     op = ops.KernelOperator(Xt, kind, bw)
     ny = ops.Nystrom(op, torch.from_numpy(W.gaussian_sketch(2048, 100, seed=0)).cuda())
-    loss, g_bw, g_lam = ops.krr_val_loss_and_grad(op, ny, y, Xv, yv, lam, tol=1e-8, refine_mode=ops.EXACT)
+    loss, g_bw, g_lam = ops.krr_val_loss_and_grad(op, ny, y, Xv, yv, lam, tol=1e-8, refine_mode=ops.EXACT, check_mode=ops.EXACT)
     L_o, dbw_o, dlam_o, _ = O.krr_val_grad(kind, wl.X, wl.B[:, 0], wl.Xval, wl.yval, bw, lam)
     assert abs(loss - L_o) <= 1e-5 * abs(L_o)
     assert abs(g_lam - dlam_o) <= 1e-4 * abs(dlam_o)
@@ -37,7 +37,7 @@ def test_autograd_function_matches_adjoint():
     y = torch.from_numpy(wl.B[:, 0].copy()).cuda().requires_grad_(True)
     bw_t = torch.tensor(wl.bandwidth, dtype=torch.float64, requires_grad=True)
     lam_t = torch.tensor(lam, dtype=torch.float64, requires_grad=True)
-    x = ops.krr_solve(op, y, bw_t, lam_t, None, tol=1e-8, refine_mode=ops.EXACT)
+    x = ops.krr_solve(op, y, bw_t, lam_t, None, tol=1e-8, refine_mode=ops.EXACT, check_mode=ops.EXACT)
     w = torch.from_numpy(W.random_block(700, 1, seed=4)[:, 0]).cuda()
     (x * w).sum().backward()
     # d/dy (w^T x) = (K + lam I)^{-1} w ; d/dlam = -g^T x

@@ -1,0 +1,93 @@
+"""The other workload shapes at sizes the FP64 oracle finishes in seconds:
+the Matern workload (z-scored uniform points, lengthscale 1 and the flagged
+sqrt(d) variant), the block workload (d = 128, right-hand sides x shifts,
+whose PCG products run on the tensor-core contraction path), and the
+hyper-parameter workload's solve.  Acceptance as in test_gpu_solver.py: FP64
+relative residual <= 1e-6 per column and ||x - x*|| / ||x*|| <= 1e-4."""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import torch
+
+from oracle import cmatvec
+from oracle import kop_oracle as O
+from paper_2609_08136_b300 import ops
+from paper_2609_08136_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _accept(kind, X, bw, lams, B, Xg, dense=True):
+    n = len(X)
+    if dense:
+        K = O.kernel_matrix(kind, X, X, bw)
+    for c in range(Xg.shape[1]):
+        lam = lams[c]
+        b = B[:, c % B.shape[1]].astype(np.float64)
+        x = Xg[:, c]
+        kx = K @ x if dense else cmatvec.kernel_matvec(kind, X, x, bw)
+        rr = np.linalg.norm(kx + lam * x - b) / np.linalg.norm(b)
+        assert rr <= 1e-6, (c, rr)
+        if dense:
+            xs = sla.cho_solve(sla.cho_factor(K + lam * np.eye(n)), b)
+            assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= 1e-4, c
+
+
+@pytest.mark.parametrize("lengthscale", [1.0, float(np.sqrt(32))])
+def test_matern_workload_scaled(lengthscale):
+    wl = W.krr_matern_large(seed=0, n=6000, lengthscale=lengthscale, rank=200)
+    lam = 1e-7 * 1_000_000  # the full-size shift
+    op = ops.KernelOperator(torch.from_numpy(wl.X).cuda(), ops.MATERN52, lengthscale)
+    ny = ops.Nystrom(op, torch.from_numpy(W.gaussian_sketch(wl.n, 200, seed=0)).cuda())
+    res = ops.pcg_solve(op, torch.from_numpy(wl.B).cuda(), [lam], nys=ny, tol=5e-7, maxit=400,
+                        refine_mode=ops.EXACT, check_mode=ops.EXACT)
+    assert res.converged
+    _accept(O.MATERN52, wl.X, lengthscale, [lam], wl.B, res.x.cpu().numpy())
+
+
+def test_block_workload_scaled():
+    # d = 128 RBF, 8 right-hand sides x 4 shifts = 32 columns: the PCG products
+    # use the tensor-core contraction kernel, the preconditioner the FP32 block
+    # products
+    n, nrhs, n_shifts = 3000, 8, 4
+    wl = W.krr_rbf_block(seed=0, n=n, nrhs=nrhs, n_shifts=n_shifts, rank=150)
+    lams = list(np.logspace(-4, -2, n_shifts) * n)
+    op = ops.KernelOperator(torch.from_numpy(wl.X).cuda(), ops.RBF, wl.bandwidth)
+    ny = ops.Nystrom(op, torch.from_numpy(W.gaussian_sketch(n, 150, seed=0)).cuda())
+    res = ops.pcg_solve(op, torch.from_numpy(wl.B).cuda(), lams, nys=ny, tol=5e-7, maxit=500,
+                        refine_mode=ops.EXACT, check_mode=ops.EXACT)
+    assert res.converged
+    cols_lam = [lams[c // nrhs] for c in range(nrhs * n_shifts)]
+    _accept(O.RBF, wl.X, wl.bandwidth, cols_lam, wl.B, res.x.cpu().numpy())
+
+
+def test_hyper_workload_solve_scaled():
+    wl = W.krr_rbf_hyper(seed=0, n=5000, nval=1000)
+    lam = 1e-4 * 100_000
+    op = ops.KernelOperator(torch.from_numpy(wl.X).cuda(), ops.RBF, wl.bandwidth)
+    ny = ops.Nystrom(op, torch.from_numpy(W.gaussian_sketch(wl.n, 100, seed=0)).cuda())
+    res = ops.pcg_solve(op, torch.from_numpy(wl.B).cuda(), [lam], nys=ny, tol=5e-7, maxit=300,
+                        refine_mode=ops.EXACT, check_mode=ops.EXACT)
+    assert res.converged
+    _accept(O.RBF, wl.X, wl.bandwidth, [lam], wl.B, res.x.cpu().numpy())
+
+
+def test_laplace_mixture_full_size_sampled_rows():
+    # the benchmark workload at its full size, in the launch configuration the
+    # benchmark times: FP64 residual on sampled rows (host oracle), and the
+    # preconditioner's eigenvalues are positive and descending
+    wl = W.krr_laplace_mix(seed=0)
+    lam = float(wl.lambdas[0])
+    op = ops.KernelOperator(torch.from_numpy(wl.X).cuda(), ops.LAPLACE, wl.bandwidth)
+    ny = ops.Nystrom(op, torch.from_numpy(W.gaussian_sketch(wl.n, wl.rank, seed=0)).cuda())
+    lam_hat, _ = ny.eigs()
+    assert np.all(np.diff(lam_hat.numpy()) <= 0) and lam_hat[0] > 0
+    res = ops.pcg_solve(op, torch.from_numpy(wl.B).cuda(), [lam], nys=ny, tol=5e-7, maxit=500)
+    assert res.converged
+    x = res.x.cpu().numpy()[:, 0]
+    b = wl.B[:, 0].astype(np.float64)
+    rows = np.random.default_rng(3).choice(wl.n, 512, replace=False)
+    kx = cmatvec.kernel_matvec(O.LAPLACE, wl.X, x, wl.bandwidth, Z=wl.X[rows])
+    r_s = b[rows] - kx - lam * x[rows]
+    est = np.sqrt(wl.n / len(rows)) * np.linalg.norm(r_s) / np.linalg.norm(b)
+    assert est <= 1e-6, est

@@ -87,12 +87,12 @@ def test_krr_rbf_small_full_size(inner):
     Om = torch.from_numpy(W.gaussian_sketch(wl.n, wl.rank, seed=0)).cuda()
     ny = ops.Nystrom(op, Om, mode=inner if inner != ops.ACCURATE else ops.FAST)
     res = ops.pcg_solve(op, torch.from_numpy(wl.B).cuda(), [lam], nys=ny, tol=5e-7, maxit=500, refine_every=20,
-                        inner_mode=inner, refine_mode=ops.EXACT)
+                        inner_mode=inner, refine_mode=ops.EXACT, check_mode=ops.EXACT)
     assert res.converged
     _check_cols(K, [lam], wl.B, res.x.cpu().numpy(), [xs])
     # preconditioning pays off: plain CG needs more iterations
     cg = ops.pcg_solve(op, torch.from_numpy(wl.B).cuda(), [lam], nys=None, tol=5e-7, maxit=3000,
-                       refine_mode=ops.EXACT)
+                       refine_mode=ops.EXACT, check_mode=ops.EXACT)
     assert cg.converged and cg.iters[0] > res.iters[0]
 
 
@@ -105,7 +105,7 @@ def test_block_shifts_ragged(kind):
     lams = [0.05, 0.5]
     op = ops.KernelOperator(torch.from_numpy(X).cuda(), kind, bw)
     ny = ops.Nystrom(op, torch.from_numpy(W.gaussian_sketch(n, 50, seed=3)).cuda())
-    res = ops.pcg_solve(op, torch.from_numpy(B).cuda(), lams, nys=ny, tol=5e-7, maxit=800, refine_mode=ops.EXACT)
+    res = ops.pcg_solve(op, torch.from_numpy(B).cuda(), lams, nys=ny, tol=5e-7, maxit=800, refine_mode=ops.EXACT, check_mode=ops.EXACT)
     assert res.converged
     Xg = res.x.cpu().numpy()
     K = O.kernel_matrix(kind, X, X, bw)
@@ -122,7 +122,7 @@ def test_identity_preconditioner_is_cg_and_edge_cases():
     B[:, 1] = 0.0
     op = ops.KernelOperator(torch.from_numpy(X).cuda(), ops.RBF, 1.0)
     res = ops.pcg_solve(op, torch.from_numpy(B).cuda(), [0.3], nys=None, tol=1e-7, maxit=600,
-                        refine_mode=ops.EXACT)
+                        refine_mode=ops.EXACT, check_mode=ops.EXACT)
     assert res.converged
     assert res.iters[1] == 0 and np.all(res.x.cpu().numpy()[:, 1] == 0.0)
     K = O.kernel_matrix(O.RBF, X, X, 1.0)
@@ -131,7 +131,7 @@ def test_identity_preconditioner_is_cg_and_edge_cases():
     assert np.linalg.norm(x - xo) / np.linalg.norm(xo) < 1e-5
     # maxit reached: warning status, iterate written
     r1 = ops.pcg_solve(op, torch.from_numpy(B[:, :1].copy()).cuda(), [0.3], tol=1e-12, maxit=2,
-                       refine_mode=ops.EXACT)
+                       refine_mode=ops.EXACT, check_mode=ops.EXACT)
     assert r1.status == 1 and r1.iters[0] == 2
     assert np.all(np.isfinite(r1.x.cpu().numpy()))
 
