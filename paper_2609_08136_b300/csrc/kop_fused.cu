@@ -208,6 +208,11 @@ __global__ void __launch_bounds__(K1_THREADS, (MV <= 4 && NSPLIT == 2) ? 2 : 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row0 = blockIdx.x * 128;
   const int ntiles = (a.nk + BN - 1) / BN;
+  // Each row block starts its sweep at its own tile, so that the CTAs resident
+  // at one time read different tiles of X instead of all hitting the same L2
+  // lines; tile_of maps the sweep index t to the tile it processes.
+  const int toff = (int)(((int64_t)blockIdx.x * ntiles) / gridDim.x);
+  auto tile_of = [&](int t) { return t + toff < ntiles ? t + toff : t + toff - ntiles; };
   const int rb = a.row_bytes;
   const int nsub = (a.dp * 2) / rb;
 
@@ -252,7 +257,7 @@ __global__ void __launch_bounds__(K1_THREADS, (MV <= 4 && NSPLIT == 2) ? 2 : 1)
       const uint32_t ph = (t / nst) & 1;
       if (!warp_wait_bg(&empty[s], ph ^ 1, abort_word, a.status)) break;
       if (lane == 0) {
-        const int j0 = t * BN;
+        const int j0 = tile_of(t) * BN;
         const int rows_v = a.v_padded ? BN : (a.nk - j0 < BN ? a.nk - j0 : BN);
         const uint32_t vbytes = (uint32_t)rows_v * MV * 4;
         mbar_arrive_expect_tx(&full[s], NSPLIT * L.x_split + BN * 4 + vbytes);
@@ -328,7 +333,7 @@ __global__ void __launch_bounds__(K1_THREADS, (MV <= 4 && NSPLIT == 2) ? 2 : 1)
       if (!warp_wait(&tfull[b], bph, abort_word, a.status)) break;
       tc_fence_after();
       if (!warp_wait(&full[s], ph, abort_word, a.status)) break;
-      const int j0 = t * BN;
+      const int j0 = tile_of(t) * BN;
       const bool mask = (self && j0 < row0 + 128 && j0 + BN > row0) || (j0 + BN > a.nk);
       constexpr bool COMP = NSPLIT == 3;
       float part[MV], perr[MV];

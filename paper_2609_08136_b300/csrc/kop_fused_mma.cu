@@ -13,9 +13,11 @@
 // S has four TMEM buffers and the MMA warp issues PV(t) before S(t+3), so the
 // tensor pipe works on one tile's contraction while two pairs of epilogue
 // warpgroups (even and odd tiles) turn the next tiles' distances into kernel
-// values.  When V holds BF16-exact values
-// (the Nystrom test matrix is rounded once on entry) its lo split is skipped:
-// half the V traffic and two contraction MMAs instead of three.
+// values.  Two producer warps keep three rings filled: X tiles (released as
+// soon as their distance MMAs finish), the X tiles' norms (read by the
+// epilogue) and V tiles (released by the contraction).  When V holds BF16-exact
+// values (the Nystrom test matrix is rounded once on entry) its lo split is
+// skipped: half the V traffic and two contraction MMAs instead of three.
 #include "kop_device.cuh"
 #include "kop_epilogue.cuh"
 #include "kop_internal.h"
@@ -24,9 +26,16 @@ namespace kop {
 
 constexpr int K3_THREADS = 640;  // 4 control warps + 4 epilogue warpgroups
 constexpr int K3_MAXX = 4;       // X-tile ring (freed when the distance MMAs finish)
-constexpr int K3_MAXV = 4;       // V-tile ring (freed when the contraction finishes); even
+constexpr int K3_MAXV = 4;       // V-tile ring (freed when the contraction finishes)
 constexpr int K3_BN = 64;
 constexpr int K3_NSB = 4;  // S buffers in TMEM (even: a buffer always serves the same warpgroup pair)
+// Ring of the scaled norms of the X tiles, loaded with the X tiles and read by
+// the epilogue.  It has no "empty" barrier: the norms of tile t + K3_NKS are
+// loaded after the distance MMAs of tile t + K3_NKS - nx completed, which were
+// issued after the contraction of tile t + K3_NKS - nx - lookahead >= t, which
+// waited for the epilogue of tile t; so K3_NKS >= K3_MAXX + K3_NSB - 1.
+constexpr int K3_NKS = 8;
+static_assert(K3_NKS >= K3_MAXX + K3_NSB - 1, "norm ring too shallow");
 
 struct MmaArgs {
   const float* qnorm;
@@ -34,6 +43,7 @@ struct MmaArgs {
   float* O;
   int nq, nk, m, ldo;
   int dp, row_bytes, swz, self, mc, tcols, nx, nv, vsplits;
+  int m_pad;  // rows of one blocked V^T tile (all column chunks)
   float m2c, c2;
   int* status;
 };
@@ -48,8 +58,8 @@ struct K3Layout {
     xs = qs + 2 * q_split;
     vs = xs + nx * 2 * x_split;
     kn = vs + nv * vsplits * v_split;
-    bars = kn + nv * K3_BN * 4;
-    holder = bars + (2 * K3_MAXX + 2 * K3_MAXV + 3 * K3_NSB + 4) * 8;
+    bars = kn + K3_NKS * K3_BN * 4;
+    holder = bars + (2 * K3_MAXX + 2 * K3_MAXV + K3_NKS + 3 * K3_NSB + 4) * 8;
     abort_word = holder + 4;
     total = abort_word + 12;
   }
@@ -58,11 +68,6 @@ struct K3Layout {
 KOP_DEV bool warp_wait3(uint64_t* bar, uint32_t parity, volatile int* abort_word, int* status) {
   bool ok = true;
   if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort_word, status);
-  return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-}
-KOP_DEV bool warp_wait3_bg(uint64_t* bar, uint32_t parity, volatile int* abort_word, int* status) {
-  bool ok = true;
-  if ((threadIdx.x & 31) == 0) ok = mbar_wait_backoff(bar, parity, abort_word, status);
   return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
 }
 
@@ -93,7 +98,8 @@ __global__ void __launch_bounds__(K3_THREADS, 1)
   uint64_t* xempty = bars + K3_MAXX;         // nx
   uint64_t* vfull = bars + 2 * K3_MAXX;      // nv
   uint64_t* vempty = vfull + K3_MAXV;        // nv
-  uint64_t* sfull = vempty + K3_MAXV;        // K3_NSB
+  uint64_t* nfull = vempty + K3_MAXV;        // K3_NKS
+  uint64_t* sfull = nfull + K3_NKS;          // K3_NSB
   uint64_t* pfull = sfull + K3_NSB;          // K3_NSB
   uint64_t* sfree = pfull + K3_NSB;          // K3_NSB
   uint64_t* qbar = sfree + K3_NSB;
@@ -106,6 +112,11 @@ __global__ void __launch_bounds__(K3_THREADS, 1)
   const int row0 = blockIdx.x * 128;
   const int m0 = blockIdx.y * a.mc;
   const int ntiles = (a.nk + K3_BN - 1) / K3_BN;
+  // Each row block starts its sweep at its own tile, so that the CTAs resident
+  // at one time read different X and V tiles instead of all hitting the same
+  // L2 lines; tile_of maps the sweep index t to the tile it processes.
+  const int toff = (int)(((int64_t)blockIdx.x * ntiles) / gridDim.x);
+  auto tile_of = [&](int t) { return t + toff < ntiles ? t + toff : t + toff - ntiles; };
   const int rb = a.row_bytes;
   const int nsub = (a.dp * 2) / rb;
   const uint32_t OCOL = 256;  // O accumulator columns start after the S buffers
@@ -119,6 +130,7 @@ __global__ void __launch_bounds__(K3_THREADS, 1)
       mbar_init(&vfull[s], 1);
       mbar_init(&vempty[s], 1);
     }
+    for (int s = 0; s < K3_NKS; ++s) mbar_init(&nfull[s], 1);
     for (int b = 0; b < K3_NSB; ++b) {
       mbar_init(&sfull[b], 1);
       mbar_init(&pfull[b], 256);
@@ -140,11 +152,10 @@ __global__ void __launch_bounds__(K3_THREADS, 1)
   const uint32_t tmem = *holder;
 
   if (warp == 0) {
-    // ------------------------------------------------------------ producer
-    // X(t) into the X ring, V(t) and the scaled norms of tile t into the V ring
+    // ------------------------------------------------------------ X producer
+    // Q once, then X(t) into the X ring and the scaled norms of tile t into the norm ring
     const CUtensorMap* mq[2] = {&tq0, &tq1};
     const CUtensorMap* mk[2] = {&tk0, &tk1};
-    const CUtensorMap* mvv[2] = {&tv0, &tv1};
     if (lane == 0) {
       mbar_arrive_expect_tx(qbar, 2 * L.q_split);
       for (int sp = 0; sp < 2; ++sp)
@@ -153,115 +164,122 @@ __global__ void __launch_bounds__(K3_THREADS, 1)
             tma_load_2d(qs + sp * L.q_split + ks * (128 * rb) + rr * (K3_BN * rb), mq[sp], qbar, ks * 64,
                         row0 + rr * K3_BN);
     }
-    int tx = 0, tv = 0;
-    bool ok = true;
-    while (ok && (tx < ntiles || tv < ntiles)) {
-      // keep X loads up to nx tiles ahead, but never more than nx tiles ahead of V
-      if (tx < ntiles && tx < tv + nx) {
-        const int s = tx % nx;
-        const uint32_t ph = (tx / nx) & 1;
-        if (!warp_wait3_bg(&xempty[s], ph ^ 1, abort_word, a.status)) { ok = false; break; }
-        if (lane == 0) {
-          const int j0 = tx * K3_BN;
-          mbar_arrive_expect_tx(&xfull[s], 2 * L.x_split);
-          for (int sp = 0; sp < 2; ++sp)
-            for (int ks = 0; ks < nsub; ++ks)
-              tma_load_2d(xs + (s * 2 + sp) * L.x_split + ks * (K3_BN * rb), mk[sp], &xfull[s], ks * 64, j0);
-        }
-        __syncwarp();
-        ++tx;
-      } else {
-        const int s = tv % nv;
-        const uint32_t ph = (tv / nv) & 1;
-        if (!warp_wait3_bg(&vempty[s], ph ^ 1, abort_word, a.status)) { ok = false; break; }
-        if (lane == 0) {
-          const int j0 = tv * K3_BN;
-          mbar_arrive_expect_tx(&vfull[s], nvs * L.v_split + K3_BN * 4);
-          for (int sp = 0; sp < nvs; ++sp)
-            tma_load_2d(vs + (s * nvs + sp) * L.v_split, mvv[sp], &vfull[s], j0, m0);
-          bulk_load(kn + s * K3_BN, a.knorm + j0, K3_BN * 4, &vfull[s]);
-        }
-        __syncwarp();
-        ++tv;
+    int t = 0;
+    for (; t < ntiles; ++t) {
+      const int s = t % nx;
+      if (!warp_wait3(&xempty[s], ((t / nx) & 1) ^ 1, abort_word, a.status)) break;
+      if (lane == 0) {
+        const int j0 = tile_of(t) * K3_BN;
+        mbar_arrive_expect_tx(&xfull[s], 2 * L.x_split);
+        for (int sp = 0; sp < 2; ++sp)
+          for (int ks = 0; ks < nsub; ++ks)
+            tma_load_2d(xs + (s * 2 + sp) * L.x_split + ks * (K3_BN * rb), mk[sp], &xfull[s], ks * 64, j0);
+        const int ns = t % K3_NKS;
+        mbar_arrive_expect_tx(&nfull[ns], K3_BN * 4);
+        bulk_load(kn + ns * K3_BN, a.knorm + j0, K3_BN * 4, &nfull[ns]);
       }
+      __syncwarp();
     }
-    if (!ok && lane == 0) {
-      for (int u = (tx - nx > 0 ? tx - nx : 0); u < tx; ++u) drain_wait3(&xfull[u % nx], (u / nx) & 1);
-      for (int u = (tv - nv > 0 ? tv - nv : 0); u < tv; ++u) drain_wait3(&vfull[u % nv], (u / nv) & 1);
+    if (t < ntiles && lane == 0) {
+      for (int u = (t - nx > 0 ? t - nx : 0); u < t; ++u) drain_wait3(&xfull[u % nx], (u / nx) & 1);
+      for (int u = (t - K3_NKS > 0 ? t - K3_NKS : 0); u < t; ++u) drain_wait3(&nfull[u % K3_NKS], (u / K3_NKS) & 1);
     }
+  } else if (warp == 3) {
+    // ------------------------------------------------------------ V producer
+    const CUtensorMap* mvv[2] = {&tv0, &tv1};
+    int t = 0;
+    for (; t < ntiles; ++t) {
+      const int s = t % nv;
+      if (!warp_wait3(&vempty[s], ((t / nv) & 1) ^ 1, abort_word, a.status)) break;
+      if (lane == 0) {
+        mbar_arrive_expect_tx(&vfull[s], nvs * L.v_split);
+        for (int sp = 0; sp < nvs; ++sp)
+          tma_load_2d(vs + (s * nvs + sp) * L.v_split, mvv[sp], &vfull[s], 0, tile_of(t) * a.m_pad + m0);
+      }
+      __syncwarp();
+    }
+    if (t < ntiles && lane == 0)
+      for (int u = (t - nv > 0 ? t - nv : 0); u < t; ++u) drain_wait3(&vfull[u % nv], (u / nv) & 1);
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     // order: S(0) .. S(L-1), then for each u: PV(u), S(u + L), with the
-    // lookahead L = min(S buffers - 1, X stages)
+    // lookahead L = min(S buffers - 1, X stages).  One MMA must issue in far
+    // less time than the tensor pipe takes for it (about 32 cycles for a
+    // 128 x 64 x 16 distance step), so the loop only adds constant offsets to
+    // descriptors prepared here, and ring slots and phases are counters.
     const uint32_t idesc_s = idesc_bf16_f32(128, K3_BN);
     const uint32_t idesc_o = idesc_bf16_f32(128, a.mc);
     const uint32_t sbo = 8u * rb;
-    const int steps_per_sub = rb / 32;
-    bool ok = warp_wait3_bg(qbar, 0, abort_word, a.status);
+    const int kspb = rb / 32;  // K steps of 16 (32 bytes) per swizzled row
+    const uint64_t dq_hi = sdesc(smem_u32(qs), sbo, a.swz);
+    const uint64_t dq_mid = sdesc(smem_u32(qs + L.q_split), sbo, a.swz);
+    const uint64_t dx0 = sdesc(smem_u32(xs), sbo, a.swz);
+    const uint64_t dv0 = sdesc(smem_u32(vs), 1024u, 2u);
+    const uint32_t q_sub16 = (128u * rb) >> 4, x_sub16 = ((uint32_t)K3_BN * rb) >> 4;
+    const uint32_t x_split16 = L.x_split >> 4, v_split16 = L.v_split >> 4;
+    bool ok = warp_wait3(qbar, 0, abort_word, a.status);
     uint32_t oacc = 0;
-    auto issue_s = [&](int t) -> bool {
-      const int s = t % nx;
-      const uint32_t ph = (t / nx) & 1;
-      const int b = t % K3_NSB;
-      const uint32_t bph = (t / K3_NSB) & 1;
-      if (!warp_wait3_bg(&xfull[s], ph, abort_word, a.status)) return false;
-      if (!warp_wait3_bg(&sfree[b], bph ^ 1, abort_word, a.status)) return false;
-      tc_fence_after();
-      if (lane == 0) {
-        const uint32_t d = tmem + b * K3_BN;
-        uint32_t acc = 0;
-#pragma unroll
-        for (int term = 0; term < 3; ++term) {
-          const int ta = term == 1 ? 1 : 0, tb = term == 0 ? 1 : 0;  // hi*mid, mid*hi, hi*hi
-          const uint32_t abase = smem_u32(qs + ta * L.q_split);
-          const uint32_t bbase = smem_u32(xs + (s * 2 + tb) * L.x_split);
-          for (int kc = 0; kc < a.dp / 16; ++kc) {
-            const int ks = kc / steps_per_sub, w = kc - ks * steps_per_sub;
-            tc_mma_ss(d, sdesc(abase + ks * (128 * rb) + w * 32, sbo, a.swz),
-                      sdesc(bbase + ks * (K3_BN * rb) + w * 32, sbo, a.swz), idesc_s, acc);
-            acc = 1;
-          }
-        }
-        tc_commit(&sfull[b]);
-        tc_commit(&xempty[s]);
-      }
-      __syncwarp();
-      return true;
-    };
-    auto issue_pv = [&](int u) -> bool {
-      const int s = u % nv;
-      const uint32_t ph = (u / nv) & 1;
-      const int b = u % K3_NSB;
-      const uint32_t bph = (u / K3_NSB) & 1;
-      if (!warp_wait3_bg(&vfull[s], ph, abort_word, a.status)) return false;
-      if (!warp_wait3_bg(&pfull[b], bph, abort_word, a.status)) return false;
-      tc_fence_after();
-      if (lane == 0) {
-        const uint32_t pbase = tmem + b * K3_BN;
-        const int nterms = nvs == 2 ? 3 : 2;
-        for (int term = 0; term < nterms; ++term) {
-          // (P split, V split): lo*hi, hi*hi [, hi*lo]; P hi at +0, lo at +16 in each 32-column chunk
-          const uint32_t poff = term == 0 ? 16u : 0u;
-          const int vsp = term == 2 ? 1 : 0;
-          const uint32_t vbase = smem_u32(vs + (s * nvs + vsp) * L.v_split);
+    int sx = 0, sv = 0;            // ring slots of the next S / PV tile
+    uint32_t phx = 0, phv = 0;     // their phases
+    int ts = 0;                    // next S tile
+    const int look = (K3_NSB - 1) < nx ? (K3_NSB - 1) : nx;
+    for (int step = 0; ok; ++step) {
+      // step < look: S(step); afterwards PV(step - look), then S(step)
+      const int u = step - look;
+      if (u >= ntiles) break;
+      if (u >= 0) {
+        const int b = u & (K3_NSB - 1);
+        if (!warp_wait3(&vfull[sv], phv, abort_word, a.status)) { ok = false; break; }
+        if (!warp_wait3(&pfull[b], (u / K3_NSB) & 1, abort_word, a.status)) { ok = false; break; }
+        tc_fence_after();
+        if (lane == 0) {
+          // (P split, V split): lo*hi, hi*hi [, hi*lo]; P hi at +0, lo at +16 of each 32-column chunk
+          const uint32_t pb = tmem + b * K3_BN;
+          const uint64_t vd = dv0 + (uint64_t)(sv * nvs) * v_split16;
 #pragma unroll
           for (int kk = 0; kk < K3_BN / 16; ++kk) {
-            const uint32_t acol = pbase + 32u * (kk >> 1) + 8u * (kk & 1) + poff;
-            tc_mma_ts(tmem + OCOL, acol, sdesc(vbase + kk * 32, 1024u, 2u), idesc_o, oacc);
+            tc_mma_ts(tmem + OCOL, pb + 32u * (kk >> 1) + 8u * (kk & 1) + 16u, vd + 2 * kk, idesc_o, oacc);
             oacc = 1;
           }
+#pragma unroll
+          for (int kk = 0; kk < K3_BN / 16; ++kk)
+            tc_mma_ts(tmem + OCOL, pb + 32u * (kk >> 1) + 8u * (kk & 1), vd + 2 * kk, idesc_o, 1u);
+          if (nvs == 2) {
+#pragma unroll
+            for (int kk = 0; kk < K3_BN / 16; ++kk)
+              tc_mma_ts(tmem + OCOL, pb + 32u * (kk >> 1) + 8u * (kk & 1), vd + v_split16 + 2 * kk, idesc_o, 1u);
+          }
+          tc_commit(&sfree[b]);
+          tc_commit(&vempty[sv]);
         }
-        tc_commit(&sfree[b]);
-        tc_commit(&vempty[s]);
+        __syncwarp();
+        if (++sv == nv) { sv = 0; phv ^= 1u; }
       }
-      __syncwarp();
-      return true;
-    };
-    const int look = (K3_NSB - 1) < nx ? (K3_NSB - 1) : nx;
-    for (int t = 0; ok && t < look && t < ntiles; ++t) ok = issue_s(t);
-    for (int u = 0; ok && u < ntiles; ++u) {
-      ok = issue_pv(u);
-      if (ok && u + look < ntiles) ok = issue_s(u + look);
+      if (ts < ntiles) {
+        const int b = ts & (K3_NSB - 1);
+        if (!warp_wait3(&xfull[sx], phx, abort_word, a.status)) { ok = false; break; }
+        if (!warp_wait3(&sfree[b], ((ts / K3_NSB) & 1) ^ 1, abort_word, a.status)) { ok = false; break; }
+        tc_fence_after();
+        if (lane == 0) {
+          // hi(Q) mid(X) + mid(Q) hi(X) + hi(Q) hi(X)
+          const uint32_t d = tmem + b * K3_BN;
+          const uint64_t xh = dx0 + (uint64_t)(2 * sx) * x_split16, xm = xh + x_split16;
+          uint32_t acc = 0;
+          for (int ks = 0; ks < nsub; ++ks)
+            for (int w = 0; w < kspb; ++w) {
+              const uint32_t qo = ks * q_sub16 + 2 * w, xo = ks * x_sub16 + 2 * w;
+              tc_mma_ss(d, dq_hi + qo, xm + xo, idesc_s, acc);
+              tc_mma_ss(d, dq_mid + qo, xh + xo, idesc_s, 1u);
+              tc_mma_ss(d, dq_hi + qo, xh + xo, idesc_s, 1u);
+              acc = 1;
+            }
+          tc_commit(&sfull[b]);
+          tc_commit(&xempty[sx]);
+        }
+        __syncwarp();
+        if (++sx == nx) { sx = 0; phx ^= 1u; }
+        ++ts;
+      }
     }
     if (lane == 0) {
       tc_commit(ofull);
@@ -288,11 +306,12 @@ __global__ void __launch_bounds__(K3_THREADS, 1)
       const uint32_t col = b * K3_BN + wg * 32;
       tmem_ld32(lane_addr + col, r);
       tmem_ld_wait(r);
-      const int vsl = t % nv;
-      if (!warp_wait3(&vfull[vsl], (t / nv) & 1, abort_word, a.status)) { ok = false; break; }
-      const int jbase = t * K3_BN + wg * 32;
-      const float* knG = kn + vsl * K3_BN + wg * 32;
-      const bool mask = (a.self && t * K3_BN < row0 + 128 && t * K3_BN + K3_BN > row0) || (t * K3_BN + K3_BN > a.nk);
+      const int nsl = t % K3_NKS;
+      if (!warp_wait3(&nfull[nsl], (t / K3_NKS) & 1, abort_word, a.status)) { ok = false; break; }
+      const int jt0 = tile_of(t) * K3_BN;
+      const int jbase = jt0 + wg * 32;
+      const float* knG = kn + nsl * K3_BN + wg * 32;
+      const bool mask = (a.self && jt0 < row0 + 128 && jt0 + K3_BN > row0) || (jt0 + K3_BN > a.nk);
       float kv[32];
 #pragma unroll
       for (int j4 = 0; j4 < 32; j4 += 4) {
@@ -355,8 +374,11 @@ __global__ void __launch_bounds__(K3_THREADS, 1)
   }
 }
 
-// V (nk x m, ld ldv, FP32) -> V^T split into BF16 hi and lo, each m_pad x nk_pad
-// (row c holds column c of V), zero padded.
+// V (nk x m, ld ldv, FP32) -> V^T split into BF16 hi and lo, zero padded to
+// m_pad x nk_pad and blocked by tiles of 64 points: the 64-point tile jt of
+// column c is the 128-byte row jt * m_pad + c, so that the box one CTA loads
+// for a tile (mc columns) is one contiguous run of memory.  (Rows of a plain
+// V^T lie nk_pad * 2 bytes apart, and boxes of such strided rows load slowly.)
 __global__ void vsplit_kernel(const float* __restrict__ V, int nk, int m, int ldv, int nk_pad, int m_pad,
                               __nv_bfloat16* __restrict__ vh, __nv_bfloat16* __restrict__ vl) {
   __shared__ float tile[32][33];
@@ -371,8 +393,9 @@ __global__ void vsplit_kernel(const float* __restrict__ V, int nk, int m, int ld
     if (c < m_pad && j < nk_pad) {
       const float v = tile[threadIdx.x][r];
       const __nv_bfloat16 h = __float2bfloat16_rn(v);
-      vh[(int64_t)c * nk_pad + j] = h;
-      vl[(int64_t)c * nk_pad + j] = __float2bfloat16_rn(v - __bfloat162float(h));
+      const int64_t o = ((int64_t)(j / K3_BN) * m_pad + c) * K3_BN + (j % K3_BN);
+      vh[o] = h;
+      vl[o] = __float2bfloat16_rn(v - __bfloat162float(h));
     }
   }
 }
@@ -433,8 +456,9 @@ int fused_matvec_mma(const PointSet& Q, const PointSet& Ks, bool self, int kf, c
   cudaError_t e = cudaGetLastError();
   int rc = e == cudaSuccess ? KOP_OK : cuda_fail(e, "vsplit_kernel");
   CUtensorMap tv[2];
-  if (rc == KOP_OK) rc = encode_tmap_bf16(&tv[0], vh, m_pad, (int)nk_pad, 64, mc);
-  if (rc == KOP_OK) rc = encode_tmap_bf16(&tv[1], vl, m_pad, (int)nk_pad, 64, mc);
+  const int64_t vrows = (nk_pad / K3_BN) * m_pad;  // blocked V^T: 64 values per row
+  if (rc == KOP_OK) rc = encode_tmap_bf16(&tv[0], vh, vrows, K3_BN, K3_BN, mc);
+  if (rc == KOP_OK) rc = encode_tmap_bf16(&tv[1], vl, vrows, K3_BN, K3_BN, mc);
   if (rc == KOP_OK) {
     MmaArgs a;
     a.qnorm = Q.snorm;
@@ -451,11 +475,13 @@ int fused_matvec_mma(const PointSet& Q, const PointSet& Ks, bool self, int kf, c
     a.mc = mc;
     a.tcols = 512;
     a.vsplits = vsplits;
-    // deepest rings that fit: V ring 4 or 2 (even), X ring 4 .. 2
+    a.m_pad = m_pad;
+    // deepest rings that fit, the X ring first (it sets the MMA lookahead)
     const size_t lim = smem_limit_bytes();
-    a.nv = mma_smem_bytes(Q.dp, mc, 2, 4, vsplits) <= lim ? 4 : 2;
-    a.nx = 4;
-    while (a.nx > 2 && mma_smem_bytes(Q.dp, mc, a.nx, a.nv, vsplits) > lim) --a.nx;
+    a.nx = K3_MAXX;
+    while (a.nx > 2 && mma_smem_bytes(Q.dp, mc, a.nx, 2, vsplits) > lim) --a.nx;
+    a.nv = K3_MAXV;
+    while (a.nv > 2 && mma_smem_bytes(Q.dp, mc, a.nx, a.nv, vsplits) > lim) --a.nv;
     a.m2c = -2.0f * kc.scale;
     a.c2 = kc.c2;
     a.status = status;
