@@ -302,10 +302,11 @@ __global__ void __launch_bounds__(256) utv_ff_kernel(const float* __restrict__ U
   }
 }
 
-// O[i][c] = alpha[c] V[i][c] + sum_k U[i][k] W[k][c]; W (FP64) is used as the
-// exact pair hi + lo of FP32 values, one warp per row.
+// O[i][c] = alpha[c] V[i][c] + sum_k U[i][k] W[k][c]; W is given as pairs
+// hi + lo of FP32 values (FP64 arithmetic is slow on this GPU, so the split is
+// made once per W, not once per row), one warp per row.
 __global__ void __launch_bounds__(256) uw_ff_kernel(const float* __restrict__ U, int ldu, int64_t n, int p,
-                                                    const double* __restrict__ W, const float* __restrict__ V, int m,
+                                                    const float2* __restrict__ W, const float* __restrict__ V, int m,
                                                     const double* __restrict__ alpha, float* __restrict__ O) {
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -318,11 +319,9 @@ __global__ void __launch_bounds__(256) uw_ff_kernel(const float* __restrict__ U,
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       if (c < m) {
-        const double w = W[(int64_t)k * m + c];
-        const float wh = (float)w;
-        const float wl = (float)(w - (double)wh);
-        ff_add_prod(s[c], e[c], u, wh);
-        e[c] = fmaf(u, wl, e[c]);
+        const float2 w = W[(int64_t)k * m + c];
+        ff_add_prod(s[c], e[c], u, w.x);
+        e[c] = fmaf(u, w.y, e[c]);
       }
     }
   }
@@ -346,7 +345,7 @@ int utv_ff(const float* U, int ldu, int64_t n, int p, const float* V, int m, dou
   return KOP_OK;
 }
 
-int uw_ff(const float* U, int ldu, int64_t n, int p, const double* W, const float* V, int m, const double* alpha,
+int uw_ff(const float* U, int ldu, int64_t n, int p, const float2* W, const float* V, int m, const double* alpha,
           float* O, cudaStream_t st) {
   const int64_t threads = n * 32;
   uw_ff_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(U, ldu, n, p, W, V, m, alpha, O);

@@ -24,7 +24,7 @@ int uw64(const float* U, int ldu, int64_t n, int p, const double* W, const float
          float* O, cudaStream_t st);
 // Same two projections in float-float arithmetic (error-free FP32 pairs).
 int utv_ff(const float* U, int ldu, int64_t n, int p, const float* V, int m, double* W, cudaStream_t st);
-int uw_ff(const float* U, int ldu, int64_t n, int p, const double* W, const float* V, int m, const double* alpha,
+int uw_ff(const float* U, int ldu, int64_t n, int p, const float2* W, const float* V, int m, const double* alpha,
           float* O, cudaStream_t st);
 // mode 0: M = sym(Goy) + nu Goo;  mode 1: M = Gyy + nu (Goy + Goy^T) + nu^2 Goo.
 int combine(const double* Goo, const double* Goy, const double* Gyy, int r, double nu, int mode, double* M,

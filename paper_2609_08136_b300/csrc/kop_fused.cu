@@ -275,37 +275,44 @@ __global__ void __launch_bounds__(K1_THREADS, (MV <= 4 && NSPLIT == 2) ? 2 : 1)
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
+    // The loop adds constant offsets to descriptors prepared here (one MMA
+    // must issue faster than the tensor pipe runs it); ring slot and phase are
+    // counters.
     const uint32_t idesc = idesc_bf16_f32(128, BN);
     const uint32_t sbo = 8u * rb;
-    const int steps_per_sub = rb / 32;
-    bool ok = warp_wait_bg(qbar, 0, abort_word, a.status);
+    const int kspb = rb / 32;  // K steps of 16 (32 bytes) per swizzled row
+    const uint64_t dq0 = sdesc(smem_u32(qs), sbo, a.swz);
+    const uint64_t dx0 = sdesc(smem_u32(xs), sbo, a.swz);
+    const uint32_t q_split16 = L.q_split >> 4, x_split16 = L.x_split >> 4;
+    const uint32_t q_sub16 = (128u * rb) >> 4, x_sub16 = ((uint32_t)BN * rb) >> 4;
+    bool ok = warp_wait(qbar, 0, abort_word, a.status);
+    int s = 0;
+    uint32_t ph = 0;
     for (int t = 0; ok && t < ntiles; ++t) {
-      const int s = t % nst;
-      const uint32_t ph = (t / nst) & 1;
       const int b = t & 1;
       const uint32_t bph = (t >> 1) & 1;
-      if (!warp_wait_bg(&full[s], ph, abort_word, a.status)) break;
-      if (!warp_wait_bg(&tempty[b], bph ^ 1, abort_word, a.status)) break;
+      if (!warp_wait(&full[s], ph, abort_word, a.status)) break;
+      if (!warp_wait(&tempty[b], bph ^ 1, abort_word, a.status)) break;
       tc_fence_after();
       if (lane == 0) {
         const uint32_t d = tmem + b * BN;
+        const uint64_t xb = dx0 + (uint64_t)(s * NSPLIT) * x_split16;
         uint32_t acc = 0;
+        for (int ks = 0; ks < nsub; ++ks)
+          for (int w = 0; w < kspb; ++w) {
+            const uint32_t qo = ks * q_sub16 + 2 * w, xo = ks * x_sub16 + 2 * w;
 #pragma unroll
-        for (int term = 0; term < n_terms<NSPLIT>(); ++term) {
-          const uint32_t abase = smem_u32(qs + term_a<NSPLIT>(term) * L.q_split);
-          const uint32_t bbase = smem_u32(xs + (s * NSPLIT + term_b<NSPLIT>(term)) * L.x_split);
-          for (int kc = 0; kc < a.dp / 16; ++kc) {
-            const int ks = kc / steps_per_sub, w = kc - ks * steps_per_sub;
-            const uint64_t ad = sdesc(abase + ks * (128 * rb) + w * 32, sbo, a.swz);
-            const uint64_t bd = sdesc(bbase + ks * (BN * rb) + w * 32, sbo, a.swz);
-            tc_mma_ss(d, ad, bd, idesc, acc);
-            acc = 1;
+            for (int term = 0; term < n_terms<NSPLIT>(); ++term) {
+              tc_mma_ss(d, dq0 + term_a<NSPLIT>(term) * q_split16 + qo, xb + term_b<NSPLIT>(term) * x_split16 + xo,
+                        idesc, acc);
+              acc = 1;
+            }
           }
-        }
         tc_commit(&tfull[b]);
         tc_commit(&empty[s]);
       }
       __syncwarp();
+      if (++s == nst) { s = 0; ph ^= 1u; }
     }
     if (lane == 0) {
       tc_commit(drain);

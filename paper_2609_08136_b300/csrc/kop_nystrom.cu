@@ -38,13 +38,19 @@ struct DevBuf {
 // W (r x m) is scaled in place; an FP32 copy is written when Wf != NULL.
 __global__ void nys_scale_kernel(double* __restrict__ W, int r, int m, const double* __restrict__ lam,
                                  const double* __restrict__ mu, int adaptive, float* __restrict__ Wf,
-                                 double* __restrict__ alpha, float* __restrict__ alpha_f) {
+                                 double* __restrict__ alpha, float* __restrict__ alpha_f, int split_inplace) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)r * m) return;
   const int k = (int)(t / m), c = (int)(t - (int64_t)k * m);
   const double rho = adaptive ? lam[r - 1] + mu[c] : mu[c];
   const double w = W[t] * (1.0 / (lam[k] + mu[c]) - 1.0 / rho);
-  W[t] = w;
+  if (split_inplace) {
+    // w as the exact-to-2^-48 pair hi + lo of FP32 values, in W's own slot
+    const float hi = (float)w;
+    reinterpret_cast<float2*>(W)[t] = make_float2(hi, (float)(w - (double)hi));
+  } else {
+    W[t] = w;
+  }
   if (Wf) Wf[t] = (float)w;
   if (k == 0) {
     alpha[c] = 1.0 / rho;
@@ -69,14 +75,14 @@ int nys_apply_dev(const nys_s* ny, const double* mu_dev, int adaptive, const flo
     int rc = utv_ff(ny->U, r, n, r, V, m, Wd, st);
     if (rc) return rc;
     nys_scale_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(Wd, r, m, ny->lam_dev, mu_dev, adaptive, nullptr,
-                                                                    alpha, nullptr);
+                                                                    alpha, nullptr, 1);
     KOP_LAUNCHED();
-    return uw_ff(ny->U, r, n, r, Wd, V, m, alpha, O, st);
+    return uw_ff(ny->U, r, n, r, reinterpret_cast<const float2*>(Wd), V, m, alpha, O, st);
   }
   int rc = gram(ny->U, r, V, m, n, r, m, Wd, m, st);
   if (rc) return rc;
   nys_scale_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(Wd, r, m, ny->lam_dev, mu_dev, adaptive, Wf, alpha,
-                                                                  alpha_f);
+                                                                  alpha_f, 0);
   KOP_LAUNCHED();
   return tall_gemm(ny->U, nullptr, 0.0f, r, n, r, Wf, m, m, V, m, alpha_f, O, m, st);
 }
