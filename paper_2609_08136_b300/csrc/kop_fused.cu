@@ -12,18 +12,26 @@
 //   O += K V_J           FP32 FMAs, compensated running sum per output
 // K never reaches global memory.  Warp roles: warp 0 issues all loads
 // asynchronously (tensor-map TMA for the split operands, bulk copies for the
-// scaled norms and V), warp 1 issues the MMAs, warp 2 owns TMEM, warps 4..11
-// (two warpgroups, one half of the tile columns each) run the epilogue.  The
-// S accumulator is double-buffered in TMEM so that the MMAs of tile t+1
-// overlap the epilogue of tile t.
+// scaled norms and V), warp 1 issues the MMAs, warp 2 owns TMEM, and NWG
+// epilogue warpgroups (warps 4..) turn distances into kernel values and
+// contract them with V, each warpgroup 64 columns of a tile: a tile of BN
+// points is taken by a group of BN / 64 warpgroups, and the groups take
+// alternate tiles.  One CTA per SM holds all of TMEM as 512 / BN S buffers
+// (at most four), so the MMAs run ahead of the epilogue.  Two rings
+// feed the pipeline: X tiles (warp 0), released as soon as their distance
+// MMAs complete, and the tiles' scaled norms and V rows (warp 3), released by
+// the epilogue.
 #include "kop_device.cuh"
 #include "kop_epilogue.cuh"
 #include "kop_internal.h"
+#include "kop_sdist.cuh"
 
 namespace kop {
 
-constexpr int K1_THREADS = 384;
 constexpr int K1_MAXST = 4;
+// S buffers in TMEM for a tile width: as many as fit in 512 columns, at most four.
+__host__ __device__ constexpr int k1_nsb(int bn) { return 512 / bn < 4 ? 512 / bn : 4; }
+constexpr int K1_NKV = 4;  // slots of the norm / V ring
 
 struct FusedArgs {
   const float* qnorm;  // scaled row norms of Q, padded to the 128-row grid
@@ -32,7 +40,8 @@ struct FusedArgs {
   float* O;
   int nq, nk, m, ldo;
   int dp, row_bytes, swz, self, nst;
-  int v_padded;        // V has n_pad rows (else the last tile copies only nk - j0 rows)
+  int v_padded;        // V has nk_pad rows (else the last tile copies only nk - j0 rows)
+  int nk_pad;          // rows of the padded X norms (a multiple of 128)
   float m2c, c2;       // -2 s, derivative factor
   int* status;
 };
@@ -40,18 +49,18 @@ struct FusedArgs {
 // Shared-memory layout (offsets from a 1024-byte aligned base).
 struct K1Layout {
   uint32_t q_split, x_split, qs, xs, kn, vs, bars, holder, abort_word, red, total;
-  __host__ __device__ K1Layout(int nsplit, int dp, int bn, int mv, int nst) {
+  __host__ __device__ K1Layout(int nsplit, int dp, int bn, int mv, int nst, int nwg) {
     q_split = 128u * dp * 2;
     x_split = (uint32_t)bn * dp * 2;
     qs = 0;
     xs = qs + nsplit * q_split;
     kn = xs + nst * nsplit * x_split;
-    vs = kn + nst * bn * 4;
-    bars = vs + nst * bn * mv * 4;
-    holder = bars + (2 * K1_MAXST + 6) * 8;
+    vs = kn + K1_NKV * bn * 4;
+    bars = vs + K1_NKV * bn * mv * 4;
+    holder = bars + (2 * K1_MAXST + 2 * K1_NKV + 2 * 4 + 2) * 8;
     abort_word = holder + 4;
     red = abort_word + 12;
-    total = red + 128 * mv * 2 * 4;
+    total = red + (nwg - 1) * 128 * mv * 2 * 4;
   }
 };
 
@@ -75,22 +84,6 @@ KOP_DEV void drain_wait(uint64_t* bar, uint32_t parity) {
   while (!mbar_try_wait(bar, parity)) {
     if (globaltimer_ns() - t0 > KOP_WAIT_LIMIT_NS) break;
   }
-}
-
-// (A split, B split) of the i-th partial product.  Small terms come first so
-// that the large hi*hi product is added last, to an accumulator that still
-// holds only small values.
-//   2 splits (hi, mid):       hi*mid, mid*hi, hi*hi
-//   3 splits (hi, mid, lo):   mid*mid, hi*lo, lo*hi, hi*mid, mid*hi, hi*hi
-template <int NSPLIT>
-KOP_DEV constexpr int n_terms() { return NSPLIT == 2 ? 3 : 6; }
-template <int NSPLIT>
-KOP_DEV constexpr int term_a(int t) {
-  return NSPLIT == 2 ? (t == 1 ? 1 : 0) : (t == 0 ? 1 : t == 2 ? 2 : t == 4 ? 1 : 0);
-}
-template <int NSPLIT>
-KOP_DEV constexpr int term_b(int t) {
-  return NSPLIT == 2 ? (t == 0 ? 1 : 0) : (t == 0 ? 1 : t == 1 ? 2 : t == 3 ? 1 : 0);
 }
 
 // Epilogue over one 32-column chunk.  MASK: check the diagonal and the ragged
@@ -180,8 +173,8 @@ KOP_DEV void chunk_fma(const uint32_t (&r)[32], float qn, const float* __restric
   }
 }
 
-template <int KF, int NSPLIT, int MV, int BN>
-__global__ void __launch_bounds__(K1_THREADS, (MV <= 4 && NSPLIT == 2) ? 2 : 1)
+template <int KF, int NSPLIT, int MV, int BN, int NWG>
+__global__ void __launch_bounds__(128 + 128 * NWG, 1)
     k1_fma_kernel(const __grid_constant__ CUtensorMap tq0, const __grid_constant__ CUtensorMap tq1,
                   const __grid_constant__ CUtensorMap tq2, const __grid_constant__ CUtensorMap tk0,
                   const __grid_constant__ CUtensorMap tk1, const __grid_constant__ CUtensorMap tk2,
@@ -189,17 +182,23 @@ __global__ void __launch_bounds__(K1_THREADS, (MV <= 4 && NSPLIT == 2) ? 2 : 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int nst = a.nst;
-  const K1Layout L(NSPLIT, a.dp, BN, MV, nst);
+  constexpr int NSB = k1_nsb(BN);
+  constexpr int WPG = BN / 64;    // warpgroups per tile
+  constexpr int G = NWG / WPG;    // tile groups
+  static_assert(BN % 64 == 0 && NWG % WPG == 0 && G >= 1, "bad epilogue split");
+  const K1Layout L(NSPLIT, a.dp, BN, MV, nst, NWG);
   uint8_t* qs = smem + L.qs;
   uint8_t* xs = smem + L.xs;
   float* kn = (float*)(smem + L.kn);
   float* vs = (float*)(smem + L.vs);
   uint64_t* bars = (uint64_t*)(smem + L.bars);
-  uint64_t* full = bars;
+  uint64_t* full = bars;                     // X ring
   uint64_t* empty = bars + K1_MAXST;
-  uint64_t* tfull = bars + 2 * K1_MAXST;
-  uint64_t* tempty = tfull + 2;
-  uint64_t* qbar = tempty + 2;
+  uint64_t* kvfull = bars + 2 * K1_MAXST;    // norm / V ring
+  uint64_t* kvempty = kvfull + K1_NKV;
+  uint64_t* tfull = kvempty + K1_NKV;
+  uint64_t* tempty = tfull + NSB;
+  uint64_t* qbar = tempty + NSB;
   uint64_t* drain = qbar + 1;
   uint32_t* holder = (uint32_t*)(smem + L.holder);
   volatile int* abort_word = (volatile int*)(smem + L.abort_word);
@@ -219,11 +218,15 @@ __global__ void __launch_bounds__(K1_THREADS, (MV <= 4 && NSPLIT == 2) ? 2 : 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < nst; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1 + 256);
+      mbar_init(&empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int s = 0; s < K1_NKV; ++s) {
+      mbar_init(&kvfull[s], 1);
+      mbar_init(&kvempty[s], 128 * WPG);
+    }
+    for (int b = 0; b < NSB; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 256);
+      mbar_init(&tempty[b], 128 * WPG);
     }
     mbar_init(qbar, 1);
     mbar_init(drain, 1);
@@ -231,7 +234,7 @@ __global__ void __launch_bounds__(K1_THREADS, (MV <= 4 && NSPLIT == 2) ? 2 : 1)
     fence_mbar_init();
   }
   if (warp == 2) {
-    tmem_alloc(holder, 256);
+    tmem_alloc(holder, NSB * BN);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -240,39 +243,56 @@ __global__ void __launch_bounds__(K1_THREADS, (MV <= 4 && NSPLIT == 2) ? 2 : 1)
   const uint32_t tmem = *holder;
 
   if (warp == 0) {
-    // ------------------------------------------------------------ producer
+    // ------------------------------------------------------------ X producer
     const CUtensorMap* mq[3] = {&tq0, &tq1, &tq2};
     const CUtensorMap* mk[3] = {&tk0, &tk1, &tk2};
     if (lane == 0) {
       mbar_arrive_expect_tx(qbar, NSPLIT * L.q_split);
       for (int sp = 0; sp < NSPLIT; ++sp)
         for (int ks = 0; ks < nsub; ++ks)
-          for (int rr = 0; rr < 128 / BN; ++rr)
-            tma_load_2d(qs + sp * L.q_split + ks * (128 * rb) + rr * (BN * rb), mq[sp], qbar, ks * 64,
-                        row0 + rr * BN);
+          tma_load_2d(qs + sp * L.q_split + ks * (128 * rb), mq[sp], qbar, ks * 64, row0);
     }
-    int t = 0;
+    int t = 0, s = 0;
+    uint32_t ph = 0;
     for (; t < ntiles; ++t) {
-      const int s = t % nst;
-      const uint32_t ph = (t / nst) & 1;
       if (!warp_wait_bg(&empty[s], ph ^ 1, abort_word, a.status)) break;
       if (lane == 0) {
         const int j0 = tile_of(t) * BN;
-        const int rows_v = a.v_padded ? BN : (a.nk - j0 < BN ? a.nk - j0 : BN);
-        const uint32_t vbytes = (uint32_t)rows_v * MV * 4;
-        mbar_arrive_expect_tx(&full[s], NSPLIT * L.x_split + BN * 4 + vbytes);
+        mbar_arrive_expect_tx(&full[s], NSPLIT * L.x_split);
         for (int sp = 0; sp < NSPLIT; ++sp)
           for (int ks = 0; ks < nsub; ++ks)
             tma_load_2d(xs + (s * NSPLIT + sp) * L.x_split + ks * (BN * rb), mk[sp], &full[s], ks * 64, j0);
-        bulk_load(kn + s * BN, a.knorm + j0, BN * 4, &full[s]);
-        bulk_load(vs + s * BN * MV, a.V + (int64_t)j0 * MV, vbytes, &full[s]);
       }
       __syncwarp();
+      if (++s == nst) { s = 0; ph ^= 1u; }
     }
     if (t < ntiles && lane == 0) {
       // aborted: let the loads already issued land before the CTA exits
       for (int u = (t - nst > 0 ? t - nst : 0); u < t; ++u) drain_wait(&full[u % nst], (u / nst) & 1);
     }
+  } else if (warp == 3) {
+    // ------------------------------------------------------------ norm / V producer
+    int t = 0, s = 0;
+    uint32_t ph = 0;
+    for (; t < ntiles; ++t) {
+      if (!warp_wait_bg(&kvempty[s], ph ^ 1, abort_word, a.status)) break;
+      if (lane == 0) {
+        const int j0 = tile_of(t) * BN;
+        // a wide last tile may run past the padded rows: copy only what exists
+        // (the rest of the slot is masked by the epilogue)
+        const int rows_k = a.nk_pad - j0 < BN ? a.nk_pad - j0 : BN;
+        const int lim_v = a.v_padded ? a.nk_pad : a.nk;
+        const int rows_v = lim_v - j0 < BN ? lim_v - j0 : BN;
+        const uint32_t vbytes = (uint32_t)rows_v * MV * 4;
+        mbar_arrive_expect_tx(&kvfull[s], (uint32_t)rows_k * 4 + vbytes);
+        bulk_load(kn + s * BN, a.knorm + j0, (uint32_t)rows_k * 4, &kvfull[s]);
+        bulk_load(vs + s * BN * MV, a.V + (int64_t)j0 * MV, vbytes, &kvfull[s]);
+      }
+      __syncwarp();
+      if (++s == K1_NKV) { s = 0; ph ^= 1u; }
+    }
+    if (t < ntiles && lane == 0)
+      for (int u = (t - K1_NKV > 0 ? t - K1_NKV : 0); u < t; ++u) drain_wait(&kvfull[u % K1_NKV], (u / K1_NKV) & 1);
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     // The loop adds constant offsets to descriptors prepared here (one MMA
@@ -280,7 +300,7 @@ __global__ void __launch_bounds__(K1_THREADS, (MV <= 4 && NSPLIT == 2) ? 2 : 1)
     // counters.
     const uint32_t idesc = idesc_bf16_f32(128, BN);
     const uint32_t sbo = 8u * rb;
-    const int kspb = rb / 32;  // K steps of 16 (32 bytes) per swizzled row
+    const int nks = a.dp / 16;  // K steps of 16 over the padded feature width
     const uint64_t dq0 = sdesc(smem_u32(qs), sbo, a.swz);
     const uint64_t dx0 = sdesc(smem_u32(xs), sbo, a.swz);
     const uint32_t q_split16 = L.q_split >> 4, x_split16 = L.x_split >> 4;
@@ -289,57 +309,49 @@ __global__ void __launch_bounds__(K1_THREADS, (MV <= 4 && NSPLIT == 2) ? 2 : 1)
     int s = 0;
     uint32_t ph = 0;
     for (int t = 0; ok && t < ntiles; ++t) {
-      const int b = t & 1;
-      const uint32_t bph = (t >> 1) & 1;
+      const int b = t % NSB;
+      const uint32_t bph = (t / NSB) & 1;
       if (!warp_wait(&full[s], ph, abort_word, a.status)) break;
       if (!warp_wait(&tempty[b], bph ^ 1, abort_word, a.status)) break;
       tc_fence_after();
-      if (lane == 0) {
+      {
         const uint32_t d = tmem + b * BN;
         const uint64_t xb = dx0 + (uint64_t)(s * NSPLIT) * x_split16;
-        uint32_t acc = 0;
-        for (int ks = 0; ks < nsub; ++ks)
-          for (int w = 0; w < kspb; ++w) {
-            const uint32_t qo = ks * q_sub16 + 2 * w, xo = ks * x_sub16 + 2 * w;
-#pragma unroll
-            for (int term = 0; term < n_terms<NSPLIT>(); ++term) {
-              tc_mma_ss(d, dq0 + term_a<NSPLIT>(term) * q_split16 + qo, xb + term_b<NSPLIT>(term) * x_split16 + xo,
-                        idesc, acc);
-              acc = 1;
-            }
-          }
-        tc_commit(&tfull[b]);
-        tc_commit(&empty[s]);
+        switch (nks) {
+          case 1: issue_s_tile<NSPLIT, 1>(d, dq0, xb, q_split16, x_split16, q_sub16, x_sub16, idesc); break;
+          case 2: issue_s_tile<NSPLIT, 2>(d, dq0, xb, q_split16, x_split16, q_sub16, x_sub16, idesc); break;
+          case 4: issue_s_tile<NSPLIT, 4>(d, dq0, xb, q_split16, x_split16, q_sub16, x_sub16, idesc); break;
+          default: issue_s_tile<NSPLIT, 8>(d, dq0, xb, q_split16, x_split16, q_sub16, x_sub16, idesc); break;
+        }
+        tc_commit_elect(&tfull[b]);
+        tc_commit_elect(&empty[s]);
       }
       __syncwarp();
       if (++s == nst) { s = 0; ph ^= 1u; }
     }
-    if (lane == 0) {
-      tc_commit(drain);
-      drain_wait(drain, 0);
-    }
+    tc_commit_elect(drain);
+    if (lane == 0) drain_wait(drain, 0);
     __syncwarp();
   } else if (warp >= 4) {
     // ------------------------------------------------------------ epilogue
-    const int ep = warp - 4, wg = ep >> 2, quarter = warp & 3;
+    const int wgi = (warp - 4) >> 2, grp = wgi / WPG, wg = wgi - grp * WPG, quarter = warp & 3;
     const int row = quarter * 32 + lane;
     const int gi = row0 + row;
     const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
-    constexpr int HALF = BN / 2;
-    constexpr int NCH = HALF / 32;
+    constexpr int NCH = 2;  // 32-column chunks per warpgroup
     const float qn = a.qnorm[gi];
     const bool self = a.self != 0;
     float acc_s[MV], acc_e[MV];
 #pragma unroll
     for (int c = 0; c < MV; ++c) acc_s[c] = acc_e[c] = 0.0f;
-    for (int t = 0; t < ntiles; ++t) {
-      const int s = t % nst;
-      const uint32_t ph = (t / nst) & 1;
-      const int b = t & 1;
-      const uint32_t bph = (t >> 1) & 1;
+    for (int t = grp; t < ntiles; t += G) {
+      const int b = t % NSB;
+      const uint32_t bph = (t / NSB) & 1;
+      const int s = t % K1_NKV;
+      const uint32_t ph = (t / K1_NKV) & 1;
       if (!warp_wait(&tfull[b], bph, abort_word, a.status)) break;
       tc_fence_after();
-      if (!warp_wait(&full[s], ph, abort_word, a.status)) break;
+      if (!warp_wait(&kvfull[s], ph, abort_word, a.status)) break;
       const int j0 = tile_of(t) * BN;
       const bool mask = (self && j0 < row0 + 128 && j0 + BN > row0) || (j0 + BN > a.nk);
       constexpr bool COMP = NSPLIT == 3;
@@ -348,7 +360,7 @@ __global__ void __launch_bounds__(K1_THREADS, (MV <= 4 && NSPLIT == 2) ? 2 : 1)
       for (int c = 0; c < MV; ++c) part[c] = perr[c] = 0.0f;
 #pragma unroll
       for (int ch = 0; ch < NCH; ++ch) {
-        const int col = wg * HALF + ch * 32;
+        const int col = wg * 64 + ch * 32;
         uint32_t r[32];
         tmem_ld32(lane_addr + b * BN + col, r);
         tmem_ld_wait(r);
@@ -361,27 +373,35 @@ __global__ void __launch_bounds__(K1_THREADS, (MV <= 4 && NSPLIT == 2) ? 2 : 1)
       }
       tc_fence_before();
       mbar_arrive(&tempty[b]);
-      mbar_arrive(&empty[s]);
+      mbar_arrive(&kvempty[s]);
 #pragma unroll
       for (int c = 0; c < MV; ++c) {
         two_sum_acc(acc_s[c], acc_e[c], part[c]);
         acc_e[c] += perr[c];
       }
     }
-    if (wg == 1) {
+    // combine the NWG partial sums of each row: all warpgroups but the first
+    // leave theirs in shared memory
+    const int contrib = wgi;
+    if (contrib > 0) {
+      float* rd = red + (size_t)(contrib - 1) * 128 * MV * 2;
 #pragma unroll
       for (int c = 0; c < MV; ++c) {
-        red[(row * MV + c) * 2] = acc_s[c];
-        red[(row * MV + c) * 2 + 1] = acc_e[c];
+        rd[(row * MV + c) * 2] = acc_s[c];
+        rd[(row * MV + c) * 2 + 1] = acc_e[c];
       }
     }
-    named_bar_sync(1, 256);
-    if (wg == 0 && gi < a.nq && !*abort_word) {
+    named_bar_sync(1, 128 * NWG);
+    if (contrib == 0 && gi < a.nq && !*abort_word) {
 #pragma unroll
       for (int c = 0; c < MV; ++c) {
         if (c < a.m) {
-          const float hi = acc_s[c] + red[(row * MV + c) * 2];
-          const float lo = acc_e[c] + red[(row * MV + c) * 2 + 1];
+          float hi = acc_s[c], lo = acc_e[c];
+          for (int k = 0; k < NWG - 1; ++k) {
+            const float* rd = red + (size_t)k * 128 * MV * 2;
+            two_sum_acc(hi, lo, rd[(row * MV + c) * 2]);
+            lo += rd[(row * MV + c) * 2 + 1];
+          }
           a.O[(int64_t)gi * a.ldo + c] = hi + lo;
         }
       }
@@ -391,7 +411,7 @@ __global__ void __launch_bounds__(K1_THREADS, (MV <= 4 && NSPLIT == 2) ? 2 : 1)
   __syncthreads();
   if (warp == 2) {
     tc_fence_after();
-    tmem_dealloc(tmem, 256);
+    tmem_dealloc(tmem, NSB * BN);
   }
 }
 
@@ -408,28 +428,39 @@ __global__ void vpad_kernel(const float* __restrict__ V, int64_t n, int m, int l
 // ---------------------------------------------------------------- host side
 static int swizzle_code(int row_bytes) { return row_bytes == 128 ? 2 : (row_bytes == 64 ? 4 : 6); }
 
+// Epilogue warpgroups: four where the epilogue's registers allow 640 threads,
+// else two.
+constexpr int fma_wgs(int nsplit, int mv) { return (nsplit == 2 && mv <= 4) ? 4 : 2; }
+
 size_t fma_smem_bytes(int nsplit, int dp, int bn, int mv, int nst) {
-  return K1Layout(nsplit, dp, bn, mv, nst).total + 1024;
+  return K1Layout(nsplit, dp, bn, mv, nst, fma_wgs(nsplit, mv)).total + 1024;
 }
 
 template <int KF, int NSPLIT, int MV, int BN>
 static int launch_fma_t(const PointSet& Q, const PointSet& Ks, const FusedArgs& a, cudaStream_t st) {
-  auto kern = k1_fma_kernel<KF, NSPLIT, MV, BN>;
-  size_t smem = fma_smem_bytes(NSPLIT, a.dp, BN, MV, a.nst);
-  // at most two CTAs per SM (TMEM: 256 columns each)
-  if (smem < 80 * 1024) smem = 80 * 1024;
-  static bool attr_set = false;
-  if (!attr_set) {
-    KOP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_limit_bytes()));
-    KOP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-    attr_set = true;
+  constexpr int NWG = fma_wgs(NSPLIT, MV);
+  if constexpr (BN / 64 > NWG) {
+    return fail(KOP_EINVAL, "fused_matvec: tile too wide for the epilogue");
+  } else {
+    auto kern = k1_fma_kernel<KF, NSPLIT, MV, BN, NWG>;
+    size_t smem = fma_smem_bytes(NSPLIT, a.dp, BN, MV, a.nst);
+    // one CTA per SM: it allocates all of TMEM
+    const size_t one_per_sm = smem_limit_bytes() / 2 + 4096;
+    if (smem < one_per_sm) smem = one_per_sm;
+    static bool attr_set = false;
+    if (!attr_set) {
+      KOP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_limit_bytes()));
+      KOP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+      attr_set = true;
+    }
+    // Q in boxes of 128 rows, X in boxes of BN rows
+    const int bi = BN == 128 ? 0 : 1;
+    dim3 grid((unsigned)((a.nq + 127) / 128));
+    kern<<<grid, 128 + 128 * NWG, smem, st>>>(Q.tm[0][0], Q.tm[1][0], Q.tm[2][0], Ks.tm[0][bi], Ks.tm[1][bi],
+                                              Ks.tm[2][bi], a);
+    KOP_LAUNCHED();
+    return KOP_OK;
   }
-  const int bi = BN == 128 ? 0 : 1;
-  dim3 grid((unsigned)((a.nq + 127) / 128));
-  kern<<<grid, K1_THREADS, smem, st>>>(Q.tm[0][bi], Q.tm[1][bi], Q.tm[2][bi], Ks.tm[0][bi], Ks.tm[1][bi],
-                                       Ks.tm[2][bi], a);
-  KOP_LAUNCHED();
-  return KOP_OK;
 }
 
 template <int KF, int NSPLIT, int BN>
@@ -439,12 +470,18 @@ static int launch_fma_mv(int mv, const PointSet& Q, const PointSet& Ks, const Fu
   return launch_fma_t<KF, NSPLIT, 8, BN>(Q, Ks, a, st);
 }
 
+template <int KF, int NSPLIT>
+static int launch_fma_bn(int bn, int mv, const PointSet& Q, const PointSet& Ks, const FusedArgs& a,
+                         cudaStream_t st) {
+  if (bn == 128) return launch_fma_mv<KF, NSPLIT, 128>(mv, Q, Ks, a, st);
+  return launch_fma_mv<KF, NSPLIT, 64>(mv, Q, Ks, a, st);
+}
+
 template <int KF>
 static int launch_fma_kf(int nsplit, int bn, int mv, const PointSet& Q, const PointSet& Ks, const FusedArgs& a,
                          cudaStream_t st) {
-  if (nsplit == 2)
-    return bn == 128 ? launch_fma_mv<KF, 2, 128>(mv, Q, Ks, a, st) : launch_fma_mv<KF, 2, 64>(mv, Q, Ks, a, st);
-  return bn == 128 ? launch_fma_mv<KF, 3, 128>(mv, Q, Ks, a, st) : launch_fma_mv<KF, 3, 64>(mv, Q, Ks, a, st);
+  if (nsplit == 2) return launch_fma_bn<KF, 2>(bn, mv, Q, Ks, a, st);
+  return launch_fma_bn<KF, 3>(bn, mv, Q, Ks, a, st);
 }
 
 int fused_matvec(const PointSet& Q, const PointSet& Ks, bool self, int kf, const KConst& kc, int nsplit,
@@ -455,21 +492,16 @@ int fused_matvec(const PointSet& Q, const PointSet& Ks, bool self, int kf, const
     return fused_matvec_mma(Q, Ks, self, kf, kc, V, m, ldv, O, ldo, status, st, v_bf16_exact);
   const int dp = Q.dp;
   const size_t lim = smem_limit_bytes();
-  // tile width: 128 unless even a 2-stage pipeline of 8 columns does not fit
-  int bn = 128;
-  if (fma_smem_bytes(nsplit, dp, 128, 8, 2) > lim) bn = 64;
-  if (fma_smem_bytes(nsplit, dp, bn, 8, 2) > lim)
+  // tile width: 128 points where a 2-stage X ring fits, else 64.  (256-point
+  // tiles leave two S buffers, and measured slower: with the epilogue busy on
+  // the special-function units the distance MMAs of the next tile arrive late.)
+  auto width_for = [&](int mv) { return fma_smem_bytes(nsplit, dp, 128, mv, 2) <= lim ? 128 : 64; };
+  if (fma_smem_bytes(nsplit, dp, 64, 8, 2) > lim)
     return fail(KOP_EINVAL, "fused_matvec: feature width too large for the fused kernel");
-  // pipeline depth for a block of mv columns: two CTAs per SM when a 2-stage
-  // pipeline fits in half the shared memory (deeper if it still fits), else
-  // one CTA with three stages
-  auto stages_for = [&](int mv) {
+  // X ring depth: the deepest that fits (one CTA per SM)
+  auto stages_for = [&](int bn, int mv) {
     int nst = 2;
-    if (fma_smem_bytes(nsplit, dp, bn, mv, 2) <= lim / 2) {
-      while (nst < K1_MAXST && fma_smem_bytes(nsplit, dp, bn, mv, nst + 1) <= lim / 2) ++nst;
-    } else if (fma_smem_bytes(nsplit, dp, bn, mv, 3) <= lim) {
-      nst = 3;
-    }
+    while (nst < K1_MAXST && fma_smem_bytes(nsplit, dp, bn, mv, nst + 1) <= lim) ++nst;
     return nst;
   };
   int rc = ensure_scaled_norms(const_cast<PointSet&>(Q), kc.scale, st);
@@ -480,6 +512,7 @@ int fused_matvec(const PointSet& Q, const PointSet& Ks, bool self, int kf, const
   a.knorm = Ks.snorm;
   a.nq = (int)Q.n;
   a.nk = (int)Ks.n;
+  a.nk_pad = (int)Ks.n_pad;
   a.ldo = ldo;
   a.dp = dp;
   a.row_bytes = dp >= 64 ? 128 : dp * 2;
@@ -492,7 +525,8 @@ int fused_matvec(const PointSet& Q, const PointSet& Ks, bool self, int kf, const
   for (int c0 = 0; c0 < m && rc == KOP_OK; c0 += 8) {
     const int mc = (m - c0) < 8 ? (m - c0) : 8;
     const int mv = mc == 1 ? 1 : (mc <= 4 ? 4 : 8);
-    a.nst = stages_for(mv);
+    const int bn = width_for(mv);
+    a.nst = stages_for(bn, mv);
     // V is read with bulk copies: used in place when its rows are exactly mv
     // floats and 16-byte aligned, else staged in a padded copy
     const bool direct = (mc == mv) && (ldv == mv) && (c0 == 0) && ((uintptr_t)V % 16 == 0) &&

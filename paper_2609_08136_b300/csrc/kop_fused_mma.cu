@@ -21,6 +21,7 @@
 #include "kop_device.cuh"
 #include "kop_epilogue.cuh"
 #include "kop_internal.h"
+#include "kop_sdist.cuh"
 
 namespace kop {
 
@@ -210,13 +211,12 @@ __global__ void __launch_bounds__(K3_THREADS, 1)
     const uint32_t idesc_s = idesc_bf16_f32(128, K3_BN);
     const uint32_t idesc_o = idesc_bf16_f32(128, a.mc);
     const uint32_t sbo = 8u * rb;
-    const int kspb = rb / 32;  // K steps of 16 (32 bytes) per swizzled row
+    const int nks = a.dp / 16;  // K steps of 16 over the padded feature width
     const uint64_t dq_hi = sdesc(smem_u32(qs), sbo, a.swz);
-    const uint64_t dq_mid = sdesc(smem_u32(qs + L.q_split), sbo, a.swz);
     const uint64_t dx0 = sdesc(smem_u32(xs), sbo, a.swz);
     const uint64_t dv0 = sdesc(smem_u32(vs), 1024u, 2u);
     const uint32_t q_sub16 = (128u * rb) >> 4, x_sub16 = ((uint32_t)K3_BN * rb) >> 4;
-    const uint32_t x_split16 = L.x_split >> 4, v_split16 = L.v_split >> 4;
+    const uint32_t q_split16 = L.q_split >> 4, x_split16 = L.x_split >> 4, v_split16 = L.v_split >> 4;
     bool ok = warp_wait3(qbar, 0, abort_word, a.status);
     uint32_t oacc = 0;
     int sx = 0, sv = 0;            // ring slots of the next S / PV tile
@@ -232,25 +232,25 @@ __global__ void __launch_bounds__(K3_THREADS, 1)
         if (!warp_wait3(&vfull[sv], phv, abort_word, a.status)) { ok = false; break; }
         if (!warp_wait3(&pfull[b], (u / K3_NSB) & 1, abort_word, a.status)) { ok = false; break; }
         tc_fence_after();
-        if (lane == 0) {
+        {
           // (P split, V split): lo*hi, hi*hi [, hi*lo]; P hi at +0, lo at +16 of each 32-column chunk
           const uint32_t pb = tmem + b * K3_BN;
           const uint64_t vd = dv0 + (uint64_t)(sv * nvs) * v_split16;
 #pragma unroll
           for (int kk = 0; kk < K3_BN / 16; ++kk) {
-            tc_mma_ts(tmem + OCOL, pb + 32u * (kk >> 1) + 8u * (kk & 1) + 16u, vd + 2 * kk, idesc_o, oacc);
+            tc_mma_ts_elect(tmem + OCOL, pb + 32u * (kk >> 1) + 8u * (kk & 1) + 16u, vd + 2 * kk, idesc_o, oacc);
             oacc = 1;
           }
 #pragma unroll
           for (int kk = 0; kk < K3_BN / 16; ++kk)
-            tc_mma_ts(tmem + OCOL, pb + 32u * (kk >> 1) + 8u * (kk & 1), vd + 2 * kk, idesc_o, 1u);
+            tc_mma_ts_elect(tmem + OCOL, pb + 32u * (kk >> 1) + 8u * (kk & 1), vd + 2 * kk, idesc_o, 1u);
           if (nvs == 2) {
 #pragma unroll
             for (int kk = 0; kk < K3_BN / 16; ++kk)
-              tc_mma_ts(tmem + OCOL, pb + 32u * (kk >> 1) + 8u * (kk & 1), vd + v_split16 + 2 * kk, idesc_o, 1u);
+              tc_mma_ts_elect(tmem + OCOL, pb + 32u * (kk >> 1) + 8u * (kk & 1), vd + v_split16 + 2 * kk, idesc_o, 1u);
           }
-          tc_commit(&sfree[b]);
-          tc_commit(&vempty[sv]);
+          tc_commit_elect(&sfree[b]);
+          tc_commit_elect(&vempty[sv]);
         }
         __syncwarp();
         if (++sv == nv) { sv = 0; phv ^= 1u; }
@@ -260,32 +260,27 @@ __global__ void __launch_bounds__(K3_THREADS, 1)
         if (!warp_wait3(&xfull[sx], phx, abort_word, a.status)) { ok = false; break; }
         if (!warp_wait3(&sfree[b], ((ts / K3_NSB) & 1) ^ 1, abort_word, a.status)) { ok = false; break; }
         tc_fence_after();
-        if (lane == 0) {
+        {
           // hi(Q) mid(X) + mid(Q) hi(X) + hi(Q) hi(X)
           const uint32_t d = tmem + b * K3_BN;
-          const uint64_t xh = dx0 + (uint64_t)(2 * sx) * x_split16, xm = xh + x_split16;
-          uint32_t acc = 0;
-          for (int ks = 0; ks < nsub; ++ks)
-            for (int w = 0; w < kspb; ++w) {
-              const uint32_t qo = ks * q_sub16 + 2 * w, xo = ks * x_sub16 + 2 * w;
-              tc_mma_ss(d, dq_hi + qo, xm + xo, idesc_s, acc);
-              tc_mma_ss(d, dq_mid + qo, xh + xo, idesc_s, 1u);
-              tc_mma_ss(d, dq_hi + qo, xh + xo, idesc_s, 1u);
-              acc = 1;
-            }
-          tc_commit(&sfull[b]);
-          tc_commit(&xempty[sx]);
+          const uint64_t xb = dx0 + (uint64_t)(2 * sx) * x_split16;
+          switch (nks) {
+            case 1: issue_s_tile<2, 1>(d, dq_hi, xb, q_split16, x_split16, q_sub16, x_sub16, idesc_s); break;
+            case 2: issue_s_tile<2, 2>(d, dq_hi, xb, q_split16, x_split16, q_sub16, x_sub16, idesc_s); break;
+            case 4: issue_s_tile<2, 4>(d, dq_hi, xb, q_split16, x_split16, q_sub16, x_sub16, idesc_s); break;
+            default: issue_s_tile<2, 8>(d, dq_hi, xb, q_split16, x_split16, q_sub16, x_sub16, idesc_s); break;
+          }
+          tc_commit_elect(&sfull[b]);
+          tc_commit_elect(&xempty[sx]);
         }
         __syncwarp();
         if (++sx == nx) { sx = 0; phx ^= 1u; }
         ++ts;
       }
     }
-    if (lane == 0) {
-      tc_commit(ofull);
-      tc_commit(drain);
-      drain_wait3(drain, 0);
-    }
+    tc_commit_elect(ofull);
+    tc_commit_elect(drain);
+    if (lane == 0) drain_wait3(drain, 0);
     __syncwarp();
   } else if (warp >= 4) {
     // ------------------------------------------------------------ epilogue

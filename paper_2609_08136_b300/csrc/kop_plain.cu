@@ -2,8 +2,10 @@
 // (same contract, no tensor cores).  Distances by direct differences of the
 // centred FP32 points, k by expf/sqrtf, contraction by FP32 FMAs with a
 // compensated running sum per output.  One thread per query row; key tiles of
-// 64 points and their V rows are staged in shared memory and read as
-// broadcasts.  With COMP the contraction is error-free per entry (TwoProduct
+// 32 points and their V rows are staged in shared memory and read as
+// broadcasts.  The differences and squares run on packed pairs of features
+// (two-lane FP32 instructions, each lane rounded as a scalar FP32 operation):
+// even and odd features accumulate separately and are added at the end.  With COMP the contraction is error-free per entry (TwoProduct
 // + TwoSum): the solver's acceptance check uses that form, because direct
 // differences keep the kernel argument accurate where the norm identity of the
 // tensor-core path loses digits (points far from the common centre).
@@ -13,7 +15,29 @@
 namespace kop {
 
 constexpr int K2_ROWS = 128;
-constexpr int K2_KEYS = 64;
+constexpr int K2_KEYS = 32;
+
+// Two-lane FP32 arithmetic on a packed pair (lo, hi).
+KOP_DEV uint64_t pk2(float lo, float hi) {
+  uint64_t d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+  return d;
+}
+KOP_DEV float2 unpk2(uint64_t v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+KOP_DEV uint64_t sub_f32x2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+KOP_DEV uint64_t fma_f32x2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
 
 struct PlainConst {
   float e0, e1, c2;
@@ -66,26 +90,32 @@ __global__ void __launch_bounds__(K2_ROWS) k2_plain_kernel(const float* __restri
       Vs[idx] = (j < nk && c < mc) ? V[(int64_t)j * ldv + col0 + c] : 0.0f;
     }
     __syncthreads();
-    float d2[K2_KEYS];
+    uint64_t d2p[K2_KEYS];  // (sum over even features, sum over odd features)
 #pragma unroll
-    for (int jj = 0; jj < K2_KEYS; ++jj) d2[jj] = 0.0f;
+    for (int jj = 0; jj < K2_KEYS; ++jj) d2p[jj] = 0ull;
     for (int k0 = 0; k0 < dp; k0 += 16) {
-      float q[16];
+      uint64_t q2[8];
 #pragma unroll
-      for (int kk = 0; kk < 16; ++kk) q[kk] = Qs[(k0 + kk) * (K2_ROWS + 1) + tid];
+      for (int i = 0; i < 8; ++i)
+        q2[i] = pk2(Qs[(k0 + 2 * i) * (K2_ROWS + 1) + tid], Qs[(k0 + 2 * i + 1) * (K2_ROWS + 1) + tid]);
 #pragma unroll
       for (int jj = 0; jj < K2_KEYS; ++jj) {
         const float4* xr = reinterpret_cast<const float4*>(Xs + jj * dp + k0);
 #pragma unroll
         for (int k4 = 0; k4 < 4; ++k4) {
           const float4 x4 = xr[k4];
-          float t;
-          t = q[4 * k4 + 0] - x4.x; d2[jj] = fmaf(t, t, d2[jj]);
-          t = q[4 * k4 + 1] - x4.y; d2[jj] = fmaf(t, t, d2[jj]);
-          t = q[4 * k4 + 2] - x4.z; d2[jj] = fmaf(t, t, d2[jj]);
-          t = q[4 * k4 + 3] - x4.w; d2[jj] = fmaf(t, t, d2[jj]);
+          uint64_t t = sub_f32x2(q2[2 * k4], pk2(x4.x, x4.y));
+          d2p[jj] = fma_f32x2(t, t, d2p[jj]);
+          t = sub_f32x2(q2[2 * k4 + 1], pk2(x4.z, x4.w));
+          d2p[jj] = fma_f32x2(t, t, d2p[jj]);
         }
       }
+    }
+    float d2[K2_KEYS];
+#pragma unroll
+    for (int jj = 0; jj < K2_KEYS; ++jj) {
+      const float2 h = unpk2(d2p[jj]);
+      d2[jj] = h.x + h.y;
     }
     float part[MV], perr[MV];
 #pragma unroll
