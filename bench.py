@@ -26,6 +26,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "PCG time-to-relres 1e-6 & fused kernel-matvec TFLOP/s vs plain FP32 path"
 TOL = 5e-7
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the FAST
+# single-column product, keyed by (n, d); mean of two launches at full size
+TRAFFIC_BYTES = {(200_000, 64): 74.46e6}
 
 
 def _args():
@@ -265,6 +268,11 @@ def run_native(a):
     rates = ops.sfu_rates()
     peak_entries = 1.0 / (1.0 / rates["ex2"] + 1.0 / rates["sqrt"])
     achieved_entries = n * n / t_fast
+    # DRAM bytes per launch of that kernel, from one ncu capture of this
+    # workload (profiles/k1_fma_fast_m1_laplace.md); algorithmic bytes: X as
+    # two BF16 splits, scaled norms, v and the output, each once
+    traffic = TRAFFIC_BYTES.get((n, d))
+    alg_bytes = n * d * 2 * 2 + 3 * n * 4
     out = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -280,8 +288,9 @@ def run_native(a):
                           "plain_fp32": None if t_plain is None else flops / t_plain / 1e12},
         "kernel_evals_per_s": achieved_entries,
         "roofline": {"bound": "alu", "achieved": achieved_entries / 1e12, "peak": peak_entries / 1e12,
-                     "unit": "Tentries/s", "frac": achieved_entries / peak_entries, "traffic": None,
-                     "kernel": "k1_fma_kernel<LAPLACE,2,1,128> (K v, m = 1)",
+                     "unit": "Tentries/s", "frac": achieved_entries / peak_entries, "traffic": traffic,
+                     "traffic_unit": "bytes per launch (DRAM read + write, ncu)", "algorithmic_bytes": alg_bytes,
+                     "kernel": "k1_fma_kernel<LAPLACE,2,1,128,4> (K v, m = 1)",
                      "peak_source": ("SFU rates measured live by kop_sfu_rates (ex2 %.2f, sqrt %.2f Tops/s); "
                                      "one Laplace entry = 1 sqrt + 1 ex2" % (rates["ex2"] / 1e12, rates["sqrt"] / 1e12))},
         "clocks": clocks,

@@ -318,19 +318,23 @@ __global__ void __launch_bounds__(128 + 128 * NWG, 1)
         const uint32_t d = tmem + b * BN;
         const uint64_t xb = dx0 + (uint64_t)(s * NSPLIT) * x_split16;
         switch (nks) {
-          case 1: issue_s_tile<NSPLIT, 1>(d, dq0, xb, q_split16, x_split16, q_sub16, x_sub16, idesc); break;
-          case 2: issue_s_tile<NSPLIT, 2>(d, dq0, xb, q_split16, x_split16, q_sub16, x_sub16, idesc); break;
-          case 4: issue_s_tile<NSPLIT, 4>(d, dq0, xb, q_split16, x_split16, q_sub16, x_sub16, idesc); break;
-          default: issue_s_tile<NSPLIT, 8>(d, dq0, xb, q_split16, x_split16, q_sub16, x_sub16, idesc); break;
+          case 1: issue_s_tile<NSPLIT, 1, true>(d, dq0, xb, q_split16, x_split16, q_sub16, x_sub16, idesc); break;
+          case 2: issue_s_tile<NSPLIT, 2, true>(d, dq0, xb, q_split16, x_split16, q_sub16, x_sub16, idesc); break;
+          case 4: issue_s_tile<NSPLIT, 4, true>(d, dq0, xb, q_split16, x_split16, q_sub16, x_sub16, idesc); break;
+          default: issue_s_tile<NSPLIT, 8, true>(d, dq0, xb, q_split16, x_split16, q_sub16, x_sub16, idesc); break;
         }
-        tc_commit_elect(&tfull[b]);
-        tc_commit_elect(&empty[s]);
+        if (lane == 0) {
+          tc_commit(&tfull[b]);
+          tc_commit(&empty[s]);
+        }
       }
       __syncwarp();
       if (++s == nst) { s = 0; ph ^= 1u; }
     }
-    tc_commit_elect(drain);
-    if (lane == 0) drain_wait(drain, 0);
+    if (lane == 0) {
+      tc_commit(drain);
+      drain_wait(drain, 0);
+    }
     __syncwarp();
   } else if (warp >= 4) {
     // ------------------------------------------------------------ epilogue

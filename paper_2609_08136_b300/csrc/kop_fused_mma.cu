@@ -265,10 +265,10 @@ __global__ void __launch_bounds__(K3_THREADS, 1)
           const uint32_t d = tmem + b * K3_BN;
           const uint64_t xb = dx0 + (uint64_t)(2 * sx) * x_split16;
           switch (nks) {
-            case 1: issue_s_tile<2, 1>(d, dq_hi, xb, q_split16, x_split16, q_sub16, x_sub16, idesc_s); break;
-            case 2: issue_s_tile<2, 2>(d, dq_hi, xb, q_split16, x_split16, q_sub16, x_sub16, idesc_s); break;
-            case 4: issue_s_tile<2, 4>(d, dq_hi, xb, q_split16, x_split16, q_sub16, x_sub16, idesc_s); break;
-            default: issue_s_tile<2, 8>(d, dq_hi, xb, q_split16, x_split16, q_sub16, x_sub16, idesc_s); break;
+            case 1: issue_s_tile<2, 1, false>(d, dq_hi, xb, q_split16, x_split16, q_sub16, x_sub16, idesc_s); break;
+            case 2: issue_s_tile<2, 2, false>(d, dq_hi, xb, q_split16, x_split16, q_sub16, x_sub16, idesc_s); break;
+            case 4: issue_s_tile<2, 4, false>(d, dq_hi, xb, q_split16, x_split16, q_sub16, x_sub16, idesc_s); break;
+            default: issue_s_tile<2, 8, false>(d, dq_hi, xb, q_split16, x_split16, q_sub16, x_sub16, idesc_s); break;
           }
           tc_commit_elect(&sfull[b]);
           tc_commit_elect(&xempty[sx]);
