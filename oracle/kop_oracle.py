@@ -16,7 +16,8 @@ What it computes, and where the paper defines it:
   cites for GP inference (Sec. 2.1);
 * the randomized Nystrom approximation of Frangella, Tropp & Udell (cited in
   Sec. 1, Sec. 2.3 and Sec. 4.3) with damping per the NystromConfig table
-  (App. A.5, "damping_mode");
+  (App. A.5, "damping_mode"), and its rank adaptation (same table:
+  rank_init, rank_max, num_power_iters, error_tolerance);
 * preconditioned CG (Hestenes & Stiefel, cited in Sec. 5.1) with the stopping
   rule ||r_k|| <= tol ||b|| checked per right-hand side (App. A.1,
   PCGStoppingCriteria);
@@ -136,6 +137,51 @@ def nystrom(Y, Omega, nu_rel=None):
     U, s, _ = np.linalg.svd(Bm, full_matrices=False)
     lam_hat = np.maximum(0.0, s * s - nu)
     return U, lam_hat, nu
+
+
+def nystrom_error_estimate(apply_A, U, lam_hat, g0, power_iters):
+    """Power-iteration estimate of ||A - U diag(lam_hat) U^T||_2, the error of a
+    Nystrom approximation (NystromConfig num_power_iters, App. A.5).
+
+    E = A - A_nys is symmetric positive semidefinite for a Nystrom
+    approximation, so the power method from v_0 = g0 / ||g0|| converges to its
+    largest eigenvalue:  w = E v_{i-1},  est_i = ||w||,  v_i = w / est_i, for
+    i = 1 .. power_iters; returns est_q (0 if E v vanishes).  g0 is the start
+    vector the caller draws."""
+    v = np.asarray(g0, dtype=np.float64).copy()
+    v /= np.linalg.norm(v)
+    est = 0.0
+    for _ in range(power_iters):
+        w = np.asarray(apply_A(v), dtype=np.float64) - U @ (lam_hat * (U.T @ v))
+        est = float(np.linalg.norm(w))
+        if est == 0.0:
+            break
+        v = w / est
+    return est
+
+
+def nystrom_adaptive(apply_A, Omega, rank_init, rank_max, power_iters, err_tol, g0, nu_rel=None):
+    """Nystrom approximation with rank adaptation (NystromConfig rank_init,
+    rank_max, num_power_iters, error_tolerance; App. A.5).
+
+    The paper lists the parameters only.  Reading (Frangella-Tropp-Udell's
+    adaptive scheme): r = rank_init; the approximation of rank r uses the first
+    r columns of Omega; its error is estimated by nystrom_error_estimate; stop
+    when est <= err_tol * lam_hat_1 (the largest approximate eigenvalue) or
+    r == rank_max, else r = min(2 r, rank_max).  Returns
+    (U, lam_hat, nu, r, est, [(rank, est), ...])."""
+    Om_all = np.asarray(Omega, dtype=np.float64)
+    r = int(rank_init)
+    hist = []
+    while True:
+        Om = Om_all[:, :r]
+        Y = np.asarray(apply_A(Om), dtype=np.float64)
+        U, lam_hat, nu = nystrom(Y, Om, nu_rel)
+        est = nystrom_error_estimate(apply_A, U, lam_hat, g0, power_iters)
+        hist.append((r, est))
+        if est <= err_tol * lam_hat[0] or r >= rank_max:
+            return U, lam_hat, nu, r, est, hist
+        r = min(2 * r, int(rank_max))
 
 
 def nystrom_rho(lam_hat, mu, adaptive=True):

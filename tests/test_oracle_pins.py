@@ -269,3 +269,68 @@ def test_true_relres_definition():
     b2[0] += 1e-3 * np.linalg.norm(b)
     assert abs(O.true_relres(O.RBF, X, 1.0, 0.25, x, b2, K=A)
                - 1e-3 * np.linalg.norm(b) / np.linalg.norm(b2)) < 1e-12
+
+
+# ---------------------------------------------------------------- rank adaptation
+def _planted_psd(n, lam, seed):
+    """A = Q diag(lam) Q^T with a random orthonormal Q (n x len(lam))."""
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, len(lam))))
+    return Q, (Q * lam) @ Q.T
+
+
+def test_error_estimate_closed_form_exact_eigenvectors():
+    # Omega spanning the top r eigenvectors makes the Nystrom approximation the
+    # truncated eigendecomposition, so ||A - A_nys||_2 = lam_{r+1} exactly; the
+    # power method from a generic start converges to it (gap lam_{r+1} / lam_{r+2} = 4)
+    n, r = 200, 6
+    lam = np.array([50.0, 30.0, 20.0, 10.0, 8.0, 6.0, 4.0, 1.0, 0.5, 0.25])
+    Q, A = _planted_psd(n, lam, 11)
+    U, lam_hat, _ = O.nystrom(A @ Q[:, :r], Q[:, :r], nu_rel=1e-14)
+    assert np.allclose(lam_hat, lam[:r], rtol=1e-10)
+    g0 = np.random.default_rng(12).standard_normal(n)
+    est = O.nystrom_error_estimate(lambda v: A @ v, U, lam_hat, g0, 60)
+    assert abs(est - lam[r]) <= 1e-9 * lam[r]
+
+
+def test_error_estimate_bounded_by_largest_eigenvalue_of_error():
+    # for unit v, ||E v|| <= lambda_max(E): every iterate is a lower bound, and it
+    # reaches lambda_max(E) (computed by a dense symmetric eigensolver) as q grows
+    n, r = 300, 12
+    X = W.random_points(n, 4, seed=13)
+    A = O.kernel_matrix(O.RBF, X, X, 2.0)
+    Om = W.gaussian_sketch(n, r, seed=2)
+    U, lam_hat, _ = O.nystrom(A @ Om, Om, nu_rel=1e-14)
+    lmax = np.linalg.eigvalsh(A - (U * lam_hat) @ U.T)[-1]
+    g0 = np.random.default_rng(14).standard_normal(n)
+    prev = 0.0
+    for q in (1, 3, 10, 400):
+        est = O.nystrom_error_estimate(lambda v: A @ v, U, lam_hat, g0, q)
+        assert est <= lmax * (1 + 1e-12)
+        prev = est
+    assert prev >= lmax * (1 - 1e-6)
+
+
+def test_rank_adaptation_stops_at_planted_rank():
+    # exact rank 12: ranks 4 and 8 leave an error of at least lam_{r+1} (Eckart-
+    # Young: no rank-r matrix does better), rank 16 recovers A exactly
+    n = 256
+    lam = np.geomspace(100.0, 1.0, 12)
+    _, A = _planted_psd(n, lam, 15)
+    Om = np.random.default_rng(16).standard_normal((n, 64)) / np.sqrt(n)
+    g0 = np.random.default_rng(17).standard_normal(n)
+    U, lam_hat, _, r, est, hist = O.nystrom_adaptive(lambda V: A @ V, Om, 4, 64, 200, 1e-8, g0, nu_rel=1e-14)
+    assert [h[0] for h in hist] == [4, 8, 16] and r == 16
+    assert est <= 1e-8 * lam_hat[0]
+    for rk, e in hist[:-1]:
+        assert e >= lam[rk] * (1 - 1e-6)
+    assert np.allclose(lam_hat[:12], lam, rtol=1e-9)
+
+
+def test_rank_adaptation_doubles_and_caps():
+    n = 128
+    _, A = _planted_psd(n, np.geomspace(10.0, 0.1, 40), 18)
+    Om = np.random.default_rng(19).standard_normal((n, 12)) / np.sqrt(n)
+    g0 = np.ones(n)
+    *_, r, est, hist = O.nystrom_adaptive(lambda V: A @ V, Om, 5, 12, 5, 0.0, g0, nu_rel=1e-14)
+    assert [h[0] for h in hist] == [5, 10, 12] and r == 12
