@@ -18,9 +18,14 @@ namespace kop {
 // and B (n x q, ldb).  CTA tile 64 x 64 of C, 256 threads with 4 x 4 outputs
 // each; rows are consumed in chunks of 32 staged in shared memory, summed in
 // FP32 within a chunk and in FP64 across chunks; CTAs along z split the rows
-// and add their partial tiles atomically.
+// and add their partial tiles atomically.  With FF every product is taken
+// exactly (p + e = a b, e by FMA) and summed error-free within the chunk
+// (TwoSum into a float-float pair), so C is accurate to about FP64 rounding;
+// the Nystrom core needs that for Y^T Y, whose small eigen-directions (down
+// to ~1e-5 of the largest, squared condition) FP32 sums would swamp.
 constexpr int GT = 64, GK = 32;
 
+template <bool FF>
 __global__ void __launch_bounds__(256) gram_kernel(const float* __restrict__ A, int lda, const float* __restrict__ B,
                                                    int ldb, int64_t n, int p, int q, double* __restrict__ C, int ldc,
                                                    int64_t rows_per_split) {
@@ -43,11 +48,11 @@ __global__ void __launch_bounds__(256) gram_kernel(const float* __restrict__ A, 
       Bs[kk][c] = (row < r1 && q0 + c < q) ? B[row * ldb + q0 + c] : 0.0f;
     }
     __syncthreads();
-    float part[4][4];
+    float part[4][4], perr[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) part[i][j] = 0.0f;
+      for (int j = 0; j < 4; ++j) part[i][j] = perr[i][j] = 0.0f;
 #pragma unroll 8
     for (int kk = 0; kk < GK; ++kk) {
       float a[4], b[4];
@@ -58,12 +63,23 @@ __global__ void __launch_bounds__(256) gram_kernel(const float* __restrict__ A, 
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) part[i][j] = fmaf(a[i], b[j], part[i][j]);
+        for (int j = 0; j < 4; ++j) {
+          if constexpr (FF) {
+            const float pr = a[i] * b[j];
+            const float pe = fmaf(a[i], b[j], -pr);
+            const float t = part[i][j] + pr;
+            const float bb = t - part[i][j];
+            perr[i][j] += ((part[i][j] - (t - bb)) + (pr - bb)) + pe;
+            part[i][j] = t;
+          } else {
+            part[i][j] = fmaf(a[i], b[j], part[i][j]);
+          }
+        }
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] += (double)part[i][j];
+      for (int j = 0; j < 4; ++j) acc[i][j] += (double)part[i][j] + (double)perr[i][j];
     __syncthreads();
   }
 #pragma unroll
@@ -79,7 +95,7 @@ __global__ void __launch_bounds__(256) gram_kernel(const float* __restrict__ A, 
 }
 
 int gram(const float* A, int lda, const float* B, int ldb, int64_t n, int p, int q, double* C, int ldc,
-         cudaStream_t st) {
+         cudaStream_t st, bool error_free) {
   KOP_CUDA_TRY(cudaMemsetAsync(C, 0, sizeof(double) * (size_t)p * ldc, st));
   const int tiles = ((p + GT - 1) / GT) * ((q + GT - 1) / GT);
   int64_t splits = (2 * num_sms() + tiles - 1) / tiles;
@@ -90,7 +106,10 @@ int gram(const float* A, int lda, const float* B, int ldb, int64_t n, int p, int
   rps = ((rps + GK - 1) / GK) * GK;
   splits = (n + rps - 1) / rps;
   dim3 grid((p + GT - 1) / GT, (q + GT - 1) / GT, (unsigned)splits);
-  gram_kernel<<<grid, 256, 0, st>>>(A, lda, B, ldb, n, p, q, C, ldc, rps);
+  if (error_free)
+    gram_kernel<true><<<grid, 256, 0, st>>>(A, lda, B, ldb, n, p, q, C, ldc, rps);
+  else
+    gram_kernel<false><<<grid, 256, 0, st>>>(A, lda, B, ldb, n, p, q, C, ldc, rps);
   KOP_LAUNCHED();
   return KOP_OK;
 }

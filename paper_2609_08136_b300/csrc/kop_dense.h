@@ -6,9 +6,11 @@
 
 namespace kop {
 
-// C (p x q, FP64) = A^T B (A: n x p, B: n x q, FP32 row-major).
+// C (p x q, FP64) = A^T B (A: n x p, B: n x q, FP32 row-major); error_free:
+// exact products and error-free sums within each chunk of rows (about FP64
+// accuracy, several times the FP32 work).
 int gram(const float* A, int lda, const float* B, int ldb, int64_t n, int p, int q, double* C, int ldc,
-         cudaStream_t st);
+         cudaStream_t st, bool error_free = false);
 // O = alpha_col (.) V + (A + beta A2) W   (n x q); V / A2 / alpha_col may be NULL.
 int tall_gemm(const float* A, const float* A2, float beta, int lda, int64_t n, int p, const float* W, int ldw, int q,
               const float* V, int ldv, const float* alpha_col, float* O, int ldo, cudaStream_t st);

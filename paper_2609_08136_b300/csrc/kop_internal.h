@@ -112,6 +112,15 @@ struct kop_s {
   int* status = nullptr;   // device status word
 };
 
+// Stream-ordered device scratch, freed on the same stream when it goes out of scope.
+struct DevBuf {
+  void* p = nullptr;
+  cudaStream_t st = 0;
+  ~DevBuf() {
+    if (p) cudaFreeAsync(p, st);
+  }
+};
+
 struct nys_s {
   kop_s* op = nullptr;
   int r = 0;

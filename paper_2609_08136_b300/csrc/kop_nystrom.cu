@@ -24,14 +24,6 @@
 
 namespace kop {
 
-struct DevBuf {
-  void* p = nullptr;
-  cudaStream_t st = 0;
-  ~DevBuf() {
-    if (p) cudaFreeAsync(p, st);
-  }
-};
-
 // Per-column damping of the preconditioner apply.
 //   d_k(c) = 1 / (lam_k + mu_c) - 1 / rho_c,   alpha_c = 1 / rho_c,
 //   rho_c = lam_r + mu_c (adaptive) or mu_c.
@@ -157,7 +149,10 @@ extern "C" int nys_build(kop_t op, const float* Omega, int32_t r, double nu_rel,
   // 2. Gram blocks
   if ((rc = gram(Omega, r, Omega, r, n, r, r, Goo, r, st))) return rc;
   if ((rc = gram(Omega, r, Y, r, n, r, r, Goy, r, st))) return rc;
-  if ((rc = gram(Y, r, Y, r, n, r, r, Gyy, r, st))) return rc;
+  // Y^T Y error-free: the core C^-T (Y_nu^T Y_nu) C^-1 squares the condition
+  // of the sketch, and FP32 sums make its smallest eigenvalues negative once
+  // the spectrum spans ~1e5
+  if ((rc = gram(Y, r, Y, r, n, r, r, Gyy, r, st, true))) return rc;
   // 3. ||Y||_2 by power iteration on Y^T Y
   if ((rc = power_max_eig(Gyy, r, 60, scal, st))) return rc;
   double ymax2 = 0.0;
