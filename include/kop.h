@@ -149,6 +149,31 @@ int nys_build(kop_t op, const float* Omega, int32_t r, double nu_rel, int32_t mo
               nys_t* out);
 int nys_destroy(nys_t ny);
 
+/* Nystrom approximation with rank adaptation (NystromConfig rank_init,
+ * rank_max, num_power_iters, error_tolerance; App. A.5).  The paper lists the
+ * controls only; the scheme here is Frangella, Tropp & Udell's adaptive one:
+ * r = rank_init; build the rank-r approximation (nys_build) from the first r
+ * columns of Omega; estimate its error ||K - U diag(lam_hat) U^T||_2 by
+ * power_iters power iterations from the start vector g0; accept r when
+ * estimate <= err_tol * lam_hat_1 or r == rank_max, else r = min(2r, rank_max).
+ *   Omega      device, n x ld_omega FP32 row-major (ld_omega >= rank_max), the
+ *              caller's test matrix as for nys_build
+ *   g0         device, n FP32, nonzero (the caller draws it)
+ *   nu_rel, mode   as for nys_build (mode also selects the operator of the
+ *              error estimate's products K v)
+ *   out        the accepted approximation (free with nys_destroy)
+ *   rank_out, err_out   host, optional: accepted rank and its error estimate
+ *   hist_rank, hist_err, hist_len   host, optional: rank and estimate of each
+ *              build, in order (at most hist_len entries are written; at most
+ *              1 + ceil(log2(rank_max / rank_init)) builds happen)
+ * 1 <= rank_init <= rank_max <= min(n, 2048), 1 <= power_iters <= 1000,
+ * err_tol >= 0; otherwise KOP_EINVAL.  Errors of a build are returned as by
+ * nys_build.  Synchronizes `stream`.                                         */
+int nys_build_adaptive(kop_t op, const float* Omega, int32_t ld_omega, int32_t rank_init, int32_t rank_max,
+                       int32_t power_iters, double err_tol, const float* g0, double nu_rel, int32_t mode,
+                       void* stream, nys_t* out, int32_t* rank_out, double* err_out, int32_t* hist_rank,
+                       double* hist_err, int32_t hist_len);
+
 /* O = P^-1 V column by column, with damping mu[c] (host, m values):
  *   P^-1 v = v / rho + U [ (diag(lam_hat) + mu I)^-1 - I / rho ] U^T v,
  *   rho = lam_hat_r + mu (adaptive != 0) or mu (adaptive == 0).

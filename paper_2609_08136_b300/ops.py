@@ -139,6 +139,47 @@ class Nystrom:
                                    ctypes.byref(h)), "nys_build")
         self._h = h
 
+    @classmethod
+    def adaptive(cls, op: KernelOperator, Omega: torch.Tensor, rank_init: int, rank_max: int | None = None,
+                 g0: torch.Tensor | None = None, power_iters: int = 10, err_tol: float = 1e-2,
+                 nu_rel: float = 0.0, mode: int = FAST, stream=None):
+        """Nystrom approximation with rank adaptation (nys_build_adaptive):
+        ranks rank_init, 2 rank_init, ... up to rank_max, using the first r
+        columns of Omega (n x >= rank_max), until the power-iteration error
+        estimate from g0 (n-vector) is <= err_tol * lam_hat_1.  The result has
+        .r, .err_est and .hist = [(rank, estimate), ...]."""
+        rank_max = rank_init if rank_max is None else int(rank_max)
+        Om = _dev_f32(Omega, "Omega")
+        if Om.shape[0] != op.n or Om.shape[1] < rank_max:
+            raise ValueError("Omega must be n x (>= rank_max)")
+        if g0 is None:
+            raise ValueError("g0 (the power iteration's start vector) is required")
+        g = _dev_f32(g0.reshape(-1, 1), "g0")
+        if g.shape[0] != op.n:
+            raise ValueError("g0 must have n entries")
+        h = ctypes.c_void_p()
+        r = ctypes.c_int32()
+        err = ctypes.c_double()
+        hl = 16
+        hr = (ctypes.c_int32 * hl)()
+        he = (ctypes.c_double * hl)()
+        check(_ffi.lib().nys_build_adaptive(op.handle, _ptr(Om), Om.shape[1], int(rank_init), rank_max,
+                                            int(power_iters), float(err_tol), _ptr(g), float(nu_rel), int(mode),
+                                            _stream(stream), ctypes.byref(h), ctypes.byref(r), ctypes.byref(err),
+                                            hr, he, hl), "nys_build_adaptive")
+        self = cls.__new__(cls)
+        self.op = op
+        self.r = r.value
+        self._h = h
+        self.err_est = err.value
+        hist = []
+        for i in range(hl):
+            if hr[i] == 0:
+                break
+            hist.append((int(hr[i]), float(he[i])))
+        self.hist = hist
+        return self
+
     @property
     def handle(self):
         return self._h

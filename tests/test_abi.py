@@ -41,3 +41,17 @@ def test_invalid_arguments_rejected_without_gpu():
     assert lib.kop_create(ctypes.c_void_p(16), 10, 4, 0, -1.0, None, ctypes.byref(h)) == -1
     assert lib.kop_create(ctypes.c_void_p(16), 10, 4, 7, 1.0, None, ctypes.byref(h)) == -1
     assert b"kernel" in lib.kop_last_error()
+
+
+def test_adaptive_build_rejects_bad_arguments_without_gpu():
+    import ctypes
+    lib = _ffi.lib()
+    out = ctypes.c_void_p()
+    r = ctypes.c_int32()
+    e = ctypes.c_double()
+    # NULL out, NULL operator: rejected before any CUDA call
+    assert lib.nys_build_adaptive(None, None, 8, 4, 8, 10, 1e-2, None, 0.0, 0, None, None, None, None,
+                                  None, None, 0) == -1
+    assert lib.nys_build_adaptive(None, ctypes.c_void_p(16), 8, 4, 8, 10, 1e-2, ctypes.c_void_p(16), 0.0, 0,
+                                  None, ctypes.byref(out), ctypes.byref(r), ctypes.byref(e), None, None, 0) == -1
+    assert b"NULL" in lib.kop_last_error()
