@@ -87,6 +87,45 @@ def dkernel_dbw_from_sqdist(kind, D2, bw):
     raise ValueError(kind)
 
 
+def radial_derivative_from_sqdist(kind, D2, bw):
+    """h(r) = -k'(r) / r, the factor of d k(x_i, x_j) / d x_i = -h (x_i - x_j)
+    (0 for Laplace at r = 0, where that kernel has no derivative)."""
+    D2 = np.asarray(D2, dtype=np.float64)
+    if kind == RBF:
+        # k = exp(-r^2 / 2 bw^2):  k' = -(r / bw^2) k
+        return np.exp(-D2 / (2.0 * bw * bw)) / (bw * bw)
+    r = np.sqrt(D2)
+    if kind == LAPLACE:
+        # k = exp(-r / bw):  k' = -k / bw
+        with np.errstate(divide="ignore", invalid="ignore"):
+            h = np.exp(-r / bw) / (bw * r)
+        return np.where(r > 0.0, h, 0.0)
+    if kind == MATERN52:
+        # k = (1 + a + a^2/3) e^-a, a = sqrt(5) r / bw:  dk/da = -(a/3)(1 + a) e^-a
+        a = SQRT5 * r / bw
+        return (5.0 / (3.0 * bw * bw)) * (1.0 + a) * np.exp(-a)
+    raise ValueError(kind)
+
+
+def kernel_grad_points(kind, X, a, b, bw, rows_per_block=256):
+    """d(a^T K(X) b) / dX (n x d): row i is
+    sum_j (a_i b_j + a_j b_i) d k(x_i, x_j) / d x_i = -sum_j c_ij h_ij (x_i - x_j),
+    the backward product of the operator for its inputs (differentiation
+    through the solve, Sec. 3.2), written out from that definition."""
+    X = np.asarray(X, dtype=np.float64)
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    n = X.shape[0]
+    G = np.zeros_like(X)
+    for i0 in range(0, n, rows_per_block):
+        i1 = min(n, i0 + rows_per_block)
+        Dif = X[i0:i1, None, :] - X[None, :, :]
+        h = radial_derivative_from_sqdist(kind, np.einsum("ijk,ijk->ij", Dif, Dif), bw)
+        c = a[i0:i1, None] * b[None, :] + b[i0:i1, None] * a[None, :]
+        G[i0:i1] = -np.einsum("ij,ijk->ik", c * h, Dif)
+    return G
+
+
 def kernel_matrix(kind, A, B, bw):
     return kernel_from_sqdist(kind, sqdist(A, B), bw)
 

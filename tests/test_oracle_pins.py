@@ -334,3 +334,40 @@ def test_rank_adaptation_doubles_and_caps():
     g0 = np.ones(n)
     *_, r, est, hist = O.nystrom_adaptive(lambda V: A @ V, Om, 5, 12, 5, 0.0, g0, nu_rel=1e-14)
     assert [h[0] for h in hist] == [5, 10, 12] and r == 12
+
+
+# ---------------------------------------------------------------- point gradient
+@pytest.mark.parametrize("kind", [O.RBF, O.LAPLACE, O.MATERN52])
+def test_point_gradient_matches_finite_differences(kind):
+    rng = np.random.default_rng(31)
+    n, d, bw = 30, 3, 1.3
+    X = rng.standard_normal((n, d))
+    a, b = rng.standard_normal(n), rng.standard_normal(n)
+    f = lambda Y: a @ O.kernel_matrix(kind, Y, Y, bw) @ b
+    G = O.kernel_grad_points(kind, X, a, b, bw, rows_per_block=7)
+    eps = 1e-6
+    for i, k in [(0, 0), (3, 2), (17, 1), (29, 0), (11, 2)]:
+        Xp, Xm = X.copy(), X.copy()
+        Xp[i, k] += eps
+        Xm[i, k] -= eps
+        fd = (f(Xp) - f(Xm)) / (2 * eps)
+        assert abs(G[i, k] - fd) <= 1e-6 * max(1.0, abs(fd)), (i, k, G[i, k], fd)
+
+
+def test_point_gradient_translation_invariance_and_two_points():
+    # a^T K b does not change when all points move together: the gradients sum to 0
+    rng = np.random.default_rng(32)
+    X = rng.standard_normal((50, 4))
+    a, b = rng.standard_normal(50), rng.standard_normal(50)
+    for kind in (O.RBF, O.LAPLACE, O.MATERN52):
+        G = O.kernel_grad_points(kind, X, a, b, 2.0)
+        assert np.abs(G.sum(axis=0)).max() <= 1e-12 * np.abs(G).max()
+    # two RBF points at distance 1 along x, bw = 2: the diagonal terms a_i b_i k(0)
+    # do not depend on X, so only (a1 b2 + a2 b1) k(x1, x2) moves, and
+    # d k / d x1 = -k (x1 - x2) / bw^2 = -e^{-1/8} (1, 0) / 4
+    X2 = np.array([[1.0, 0.0], [0.0, 0.0]])
+    a2, b2 = np.array([0.5, -2.0]), np.array([3.0, 1.5])
+    G2 = O.kernel_grad_points(O.RBF, X2, a2, b2, 2.0)
+    c = a2[0] * b2[1] + a2[1] * b2[0]
+    assert np.allclose(G2[0], [-c * math.exp(-1.0 / 8.0) / 4.0, 0.0], rtol=1e-14, atol=1e-15)
+    assert np.allclose(G2[1], -G2[0], rtol=1e-14, atol=1e-15)
