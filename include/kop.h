@@ -127,6 +127,18 @@ int kop_matvec_f64(kop_t op, const double* V, int32_t m, double* O, int32_t deri
 /* O (n x m) = (dK(X, X)/d bandwidth) V. */
 int kop_dbw_matvec(kop_t op, const float* V, int32_t m, float* O, int32_t mode, void* stream);
 
+/* Gradient of a^T K(X) b with respect to the points X (the backward product
+ * of the operator for its inputs; the paper differentiates through the solve,
+ * Sec. 3.2): with c_ij = a_i b_j + a_j b_i and h(r) = -k'(r) / r,
+ *   G[i] = d(a^T K b)/dx_i = -sum_j c_ij h(|x_i - x_j|) (x_i - x_j),
+ *   RBF h = k / bw^2;  Laplace h = k / (bw r) (0 at r = 0, where k has no
+ *   derivative);  Matern-5/2 h = (5 / (3 bw^2)) (1 + a) e^-a, a = sqrt(5) r / bw.
+ * a, b: device n FP32;  G: device n x d FP32 row-major (overwritten).
+ * mode: KOP_FAST or KOP_ACCURATE (fused tensor-core products on the centred
+ * points) or KOP_EXACT (FP64 direct differences); KOP_PLAIN is KOP_EINVAL.
+ * Synchronizes `stream`.                                                    */
+int kop_grad_points(kop_t op, const float* a, const float* b, int32_t mode, float* G, void* stream);
+
 /* Synchronize `stream` and return the operator's device status (KOP_OK or
  * KOP_ETIMEOUT), clearing it. */
 int kop_sync(kop_t op, void* stream);

@@ -107,22 +107,22 @@ def radial_derivative_from_sqdist(kind, D2, bw):
     raise ValueError(kind)
 
 
-def kernel_grad_points(kind, X, a, b, bw, rows_per_block=256):
-    """d(a^T K(X) b) / dX (n x d): row i is
-    sum_j (a_i b_j + a_j b_i) d k(x_i, x_j) / d x_i = -sum_j c_ij h_ij (x_i - x_j),
+def kernel_grad_points(kind, X, a, b, bw, rows_per_block=256, rows=None):
+    """d(a^T K(X) b) / dX (n x d; only the given rows when `rows` is set): row i
+    is sum_j (a_i b_j + a_j b_i) d k(x_i, x_j) / d x_i = -sum_j c_ij h_ij (x_i - x_j),
     the backward product of the operator for its inputs (differentiation
     through the solve, Sec. 3.2), written out from that definition."""
     X = np.asarray(X, dtype=np.float64)
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
-    n = X.shape[0]
-    G = np.zeros_like(X)
-    for i0 in range(0, n, rows_per_block):
-        i1 = min(n, i0 + rows_per_block)
-        Dif = X[i0:i1, None, :] - X[None, :, :]
+    idx = np.arange(X.shape[0]) if rows is None else np.asarray(rows)
+    G = np.zeros((len(idx), X.shape[1]))
+    for s0 in range(0, len(idx), rows_per_block):
+        I = idx[s0:s0 + rows_per_block]
+        Dif = X[I, None, :] - X[None, :, :]
         h = radial_derivative_from_sqdist(kind, np.einsum("ijk,ijk->ij", Dif, Dif), bw)
-        c = a[i0:i1, None] * b[None, :] + b[i0:i1, None] * a[None, :]
-        G[i0:i1] = -np.einsum("ij,ijk->ik", c * h, Dif)
+        c = a[I, None] * b[None, :] + b[I, None] * a[None, :]
+        G[s0:s0 + len(I)] = -np.einsum("ij,ijk->ik", c * h, Dif)
     return G
 
 

@@ -10,6 +10,8 @@ namespace kop {
 
 int op_matvec(const PointSet& Q, const PointSet& Ks, bool self, int kf, const KConst& kc, int mode,
               const float* V, int m, int ldv, float* O, int ldo, int* status, cudaStream_t st, bool v_bf16_exact) {
+  if (kf >= KF_GRBF && (mode == KOP_PLAIN || mode == KOP_PLAIN_CHECK))
+    return fail(KOP_EINVAL, "point-gradient products run in the FAST, ACCURATE or EXACT mode");
   if (mode == KOP_PLAIN) return plain_matvec(Q, Ks, self, kf, kc, V, m, ldv, O, ldo, st);
   if (mode == KOP_PLAIN_CHECK) return plain_matvec(Q, Ks, self, kf, kc, V, m, ldv, O, ldo, st, true);
   if (mode == KOP_EXACT) return exact_matvec_f32(Q, Ks, kf, kc.bw, V, m, ldv, O, ldo, st);

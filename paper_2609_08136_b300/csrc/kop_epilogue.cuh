@@ -10,6 +10,11 @@
 //   RBF       k D2 / bw^3        = 2^u * u * c2,  c2 = 1 / (s bw^3)
 //   Laplace   k r / bw^2         = 2^-sqrt(u) * sqrt(u) * c2,  c2 = 1 / (sqrt(s) bw^2)
 //   Matern52  e^-a (a^2/3)(1+a)/bw = 2^(-log2(e) a) (u/3)(1 + a) c2,  c2 = 1 / bw
+// and the radial derivatives h(r) = -k'(r) / r of the point gradient:
+//   RBF       k / bw^2                = 2^u * c2,                  c2 = 1 / bw^2
+//   Laplace   k / (bw r)              = 2^-sqrt(u) / sqrt(u) * c2,  c2 = log2(e) / bw^2
+//             (0 at r = 0, where the Laplace kernel has no derivative)
+//   Matern52  (5 / 3 bw^2)(1 + a) e^-a = (1 + a) 2^(-log2(e) a) c2,  c2 = 5 / (3 bw^2)
 // u can be slightly negative from rounding when D2 ~ 0: sqrt takes |u|.
 #pragma once
 #include "kop_device.cuh"
@@ -32,6 +37,14 @@ KOP_DEV float kval_u(float u, float c2) {
   } else if constexpr (KF == 4) {
     const float r = sqrt_approx(fabsf(u));
     return ex2_approx(-r) * r * c2;
+  } else if constexpr (KF == 6) {
+    return ex2_approx(u) * c2;
+  } else if constexpr (KF == 7) {
+    const float a = sqrt_approx(fabsf(u));
+    return a > 0.0f ? ex2_approx(-a) / a * c2 : 0.0f;
+  } else if constexpr (KF == 8) {
+    const float a = sqrt_approx(fabsf(u));
+    return (1.0f + a) * ex2_approx(kNegLog2e * a) * c2;
   } else {
     const float a = sqrt_approx(fabsf(u));
     return ex2_approx(kNegLog2e * a) * (u * (1.0f / 3.0f)) * (1.0f + a) * c2;

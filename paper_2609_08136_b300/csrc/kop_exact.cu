@@ -33,6 +33,14 @@ KOP_DEV double exact_kernel_value(double d2, double bw) {
   } else if constexpr (KF == KF_DLAPLACE) {
     const double r = sqrt(d2);
     return exp(-r / bw) * r / (bw * bw);
+  } else if constexpr (KF == KF_GRBF) {
+    return exp(-d2 / (2.0 * bw * bw)) / (bw * bw);
+  } else if constexpr (KF == KF_GLAPLACE) {
+    const double r = sqrt(d2);
+    return r > 0.0 ? exp(-r / bw) / (bw * r) : 0.0;
+  } else if constexpr (KF == KF_GMATERN) {
+    const double a = 2.23606797749978969640 * sqrt(d2) / bw;
+    return (5.0 / (3.0 * bw * bw)) * (1.0 + a) * exp(-a);
   } else {
     const double a = 2.23606797749978969640 * sqrt(d2) / bw;
     return exp(-a) * (a * a / 3.0) * (1.0 + a) / bw;
@@ -131,6 +139,9 @@ int exact_matvec(const PointSet& Q, const PointSet& Ks, int kf, double bw, const
     case KF_MATERN: return launch_exact_kf<KF_MATERN>(Q, Ks, V, m, ldv, O, ldo, bw, st);
     case KF_DRBF: return launch_exact_kf<KF_DRBF>(Q, Ks, V, m, ldv, O, ldo, bw, st);
     case KF_DLAPLACE: return launch_exact_kf<KF_DLAPLACE>(Q, Ks, V, m, ldv, O, ldo, bw, st);
+    case KF_GRBF: return launch_exact_kf<KF_GRBF>(Q, Ks, V, m, ldv, O, ldo, bw, st);
+    case KF_GLAPLACE: return launch_exact_kf<KF_GLAPLACE>(Q, Ks, V, m, ldv, O, ldo, bw, st);
+    case KF_GMATERN: return launch_exact_kf<KF_GMATERN>(Q, Ks, V, m, ldv, O, ldo, bw, st);
     default: return launch_exact_kf<KF_DMATERN>(Q, Ks, V, m, ldv, O, ldo, bw, st);
   }
 }

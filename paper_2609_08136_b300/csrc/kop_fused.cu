@@ -557,6 +557,9 @@ int fused_matvec(const PointSet& Q, const PointSet& Ks, bool self, int kf, const
       case KF_MATERN: rc = launch_fma_kf<KF_MATERN>(nsplit, bn, mv, Q, Ks, a, st); break;
       case KF_DRBF: rc = launch_fma_kf<KF_DRBF>(nsplit, bn, mv, Q, Ks, a, st); break;
       case KF_DLAPLACE: rc = launch_fma_kf<KF_DLAPLACE>(nsplit, bn, mv, Q, Ks, a, st); break;
+      case KF_GRBF: rc = launch_fma_kf<KF_GRBF>(nsplit, bn, mv, Q, Ks, a, st); break;
+      case KF_GLAPLACE: rc = launch_fma_kf<KF_GLAPLACE>(nsplit, bn, mv, Q, Ks, a, st); break;
+      case KF_GMATERN: rc = launch_fma_kf<KF_GMATERN>(nsplit, bn, mv, Q, Ks, a, st); break;
       default: rc = launch_fma_kf<KF_DMATERN>(nsplit, bn, mv, Q, Ks, a, st); break;
     }
   }

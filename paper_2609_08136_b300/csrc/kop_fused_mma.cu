@@ -486,6 +486,9 @@ int fused_matvec_mma(const PointSet& Q, const PointSet& Ks, bool self, int kf, c
       case KF_MATERN: rc = launch_mma_t<KF_MATERN>(Q, Ks, tv, a, st); break;
       case KF_DRBF: rc = launch_mma_t<KF_DRBF>(Q, Ks, tv, a, st); break;
       case KF_DLAPLACE: rc = launch_mma_t<KF_DLAPLACE>(Q, Ks, tv, a, st); break;
+      case KF_GRBF: rc = launch_mma_t<KF_GRBF>(Q, Ks, tv, a, st); break;
+      case KF_GLAPLACE: rc = launch_mma_t<KF_GLAPLACE>(Q, Ks, tv, a, st); break;
+      case KF_GMATERN: rc = launch_mma_t<KF_GMATERN>(Q, Ks, tv, a, st); break;
       default: rc = launch_mma_t<KF_DMATERN>(Q, Ks, tv, a, st); break;
     }
   }

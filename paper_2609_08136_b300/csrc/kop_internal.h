@@ -14,7 +14,13 @@ namespace kop {
 
 // Kernel-function ids used by the device epilogues.  0..2 are k itself
 // (enum kop_kernel), 3..5 its derivative with respect to the bandwidth.
-enum { KF_RBF = 0, KF_LAPLACE = 1, KF_MATERN = 2, KF_DRBF = 3, KF_DLAPLACE = 4, KF_DMATERN = 5 };
+// Kernel kinds of the products: k, dk/d(bandwidth) (3..5) and the radial
+// derivative h(r) = -k'(r) / r of the point gradient (6..8).
+enum {
+  KF_RBF = 0, KF_LAPLACE = 1, KF_MATERN = 2,
+  KF_DRBF = 3, KF_DLAPLACE = 4, KF_DMATERN = 5,
+  KF_GRBF = 6, KF_GLAPLACE = 7, KF_GMATERN = 8
+};
 
 // Constants of the fused epilogue (kop_epilogue.cuh): the kernel sees
 // u = scale * D2 and, for derivatives, multiplies by c2.

@@ -57,6 +57,18 @@ KConst kernel_constants(int kind, double bw) {
       scale = (log2e / bw) * (log2e / bw);
       k.c2 = (float)(1.0 / ((log2e / bw) * bw * bw));
       break;
+    case KF_GRBF:
+      scale = -log2e / (2.0 * bw * bw);
+      k.c2 = (float)(1.0 / (bw * bw));
+      break;
+    case KF_GLAPLACE:
+      scale = (log2e / bw) * (log2e / bw);
+      k.c2 = (float)(log2e / (bw * bw));
+      break;
+    case KF_GMATERN:
+      scale = 5.0 / (bw * bw);
+      k.c2 = (float)(5.0 / (3.0 * bw * bw));
+      break;
     default:
       scale = 5.0 / (bw * bw);
       k.c2 = (float)(1.0 / bw);

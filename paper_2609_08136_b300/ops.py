@@ -107,6 +107,17 @@ class KernelOperator:
               "kop_dbw_matvec")
         return O[:, 0] if vec else O
 
+    def grad_points(self, a: torch.Tensor, b: torch.Tensor, mode: int = ACCURATE, stream=None):
+        """d(a^T K(X) b) / dX as an n x d tensor (kop_grad_points)."""
+        a2 = _dev_f32(a.reshape(-1), "a")
+        b2 = _dev_f32(b.reshape(-1), "b")
+        if a2.shape[0] != self.n or b2.shape[0] != self.n:
+            raise ValueError("a and b must have n entries")
+        G = torch.empty((self.n, self.d), dtype=torch.float32, device=self.device)
+        check(_ffi.lib().kop_grad_points(self._h, _ptr(a2), _ptr(b2), int(mode), _ptr(G), _stream(stream)),
+              "kop_grad_points")
+        return G
+
     def cross_matvec(self, Z: torch.Tensor, V: torch.Tensor, transpose: bool = False, deriv: bool = False,
                      mode: int = FAST, stream=None):
         """K(Z, X) V (transpose=False) or K(X, Z) V (transpose=True)."""
