@@ -323,6 +323,13 @@ def krr_solve(op: KernelOperator, b: torch.Tensor, bw: torch.Tensor, lam: torch.
     return _KRRSolve.apply(b, bw, lam, op, nys, kw)
 
 
+def solve_grad_points(op: KernelOperator, x: torch.Tensor, g: torch.Tensor, mode: int = ACCURATE):
+    """Gradient of a loss L(x) with respect to the training points X through the
+    operator, for x = (K(X) + lam I)^{-1} b and the adjoint g = (K + lam I)^{-1} dL/dx
+    (pcg_adjoint): dL/dX = -d(g^T K(X) x)/dX (kop_grad_points), n x d."""
+    return -op.grad_points(g.reshape(-1).float(), x.reshape(-1).float(), mode=mode)
+
+
 def krr_val_loss_and_grad(op: KernelOperator, nys: Nystrom | None, y: torch.Tensor, Xv: torch.Tensor,
                           yv: torch.Tensor, lam: float, tol: float = 1e-6, maxit: int = 1000, refine_every: int = 20,
                           inner_mode: int = FAST, refine_mode: int = ACCURATE, check_mode: int = PLAIN):

@@ -46,3 +46,32 @@ def test_grad_points_full_size_sampled_rows():
     err = np.linalg.norm(G[rows] - Go) / np.linalg.norm(Go)
     # measured 7.4e-4: 200000-term sums of BF16-split products
     assert err <= 3e-3, err
+
+
+def test_solve_gradient_matches_finite_differences():
+    # L(X) = w^T x with x = (K(X) + lam I)^-1 y: the adjoint solve plus the point
+    # gradient against central differences of the FP64 dense solve
+    n, d, bw, lam = 300, 3, 1.0, 1.0
+    X = W.random_points(n, d, seed=47)
+    y = W.random_block(n, 1, seed=48)
+    w = W.random_block(n, 1, seed=49)[:, 0].astype(np.float64)
+    op = ops.KernelOperator(torch.from_numpy(X).cuda(), ops.RBF, bw)
+    res = ops.pcg_solve(op, torch.from_numpy(y).cuda(), [lam], tol=1e-8, maxit=2000,
+                        refine_mode=ops.EXACT, check_mode=ops.EXACT)
+    assert res.converged
+    g, _, _, _ = ops.pcg_adjoint(op, res.x[:, 0], torch.from_numpy(w).cuda(), lam, tol=1e-8, maxit=2000,
+                                 refine_mode=ops.EXACT, check_mode=ops.EXACT)
+    G = ops.solve_grad_points(op, res.x[:, 0], g, mode=ops.EXACT).cpu().numpy()
+
+    X64 = X.astype(np.float64)
+
+    def loss(Y):
+        return w @ np.linalg.solve(O.kernel_matrix(O.RBF, Y, Y, bw) + lam * np.eye(n), y[:, 0].astype(np.float64))
+
+    eps = 1e-5
+    for i, k in [(0, 0), (57, 2), (150, 1), (299, 0)]:
+        Xp, Xm = X64.copy(), X64.copy()
+        Xp[i, k] += eps
+        Xm[i, k] -= eps
+        fd = (loss(Xp) - loss(Xm)) / (2 * eps)
+        assert abs(G[i, k] - fd) <= 1e-4 * np.abs(G).max(), (i, k, G[i, k], fd)
