@@ -109,9 +109,10 @@ def _dist():
     return world, rank, local
 
 
-def replica_seed(seed: int, rank: int) -> int:
-    """Each rank solves its own independent problem (weak scaling replicas)."""
-    return seed + rank
+def replica_seed(seed: int, rank: int, instance: int = 0, n_instances: int = 1) -> int:
+    """Each rank solves its own independent problems (weak scaling replicas):
+    rank r's instance j has seed seed + j + n_instances * r."""
+    return seed + instance + n_instances * rank
 
 
 def max_over_ranks(value: float, dist=None, device=None) -> float:
@@ -194,32 +195,39 @@ def run_native(a):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
-    # each rank solves its own independent problem (weak scaling, no data-path collective)
-    seed = replica_seed(a.seed, rank)
-    wl = W.krr_laplace_mix(seed=seed, n=a.n, rank=a.rank)
+    # each rank solves its own independent problems (weak scaling, no data-path
+    # collective); timed step j solves the instance of seed a.seed + (j mod 3)
+    n_inst = 3
+    insts = []
+    for j in range(n_inst):
+        seed = replica_seed(a.seed, rank, j, n_inst)
+        wl_j = W.krr_laplace_mix(seed=seed, n=a.n, rank=a.rank)
+        Omh_j = torch.from_numpy(W.gaussian_sketch(wl_j.n, a.rank, seed=seed)).pin_memory()
+        Xh_j = torch.from_numpy(wl_j.X).pin_memory()
+        Bh_j = torch.from_numpy(wl_j.B).pin_memory()
+        insts.append({"seed": seed, "wl": wl_j, "Xh": Xh_j, "Bh": Bh_j, "Omh": Omh_j, "X": Xh_j.to(dev),
+                      "B": Bh_j.to(dev), "Om": Omh_j.to(dev)})
+    wl, Xh, Bh, Omh = insts[0]["wl"], insts[0]["Xh"], insts[0]["Bh"], insts[0]["Omh"]
     lam = float(wl.lambdas[0])
-    Xh = torch.from_numpy(wl.X).pin_memory()
-    Bh = torch.from_numpy(wl.B).pin_memory()
-    Omh = torch.from_numpy(W.gaussian_sketch(wl.n, a.rank, seed=seed)).pin_memory()
-    X = Xh.to(dev)
-    B = Bh.to(dev)
-    Om = Omh.to(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
     stream = torch.cuda.current_stream()
 
-    def step():
-        op = ops.KernelOperator(X, wl.kernel, wl.bandwidth)
-        ny = ops.Nystrom(op, Om, mode=ops.FAST)
-        res = ops.pcg_solve(op, B, [lam], nys=ny, tol=TOL, maxit=500, refine_every=20)
+    def step(j, inner=ops.FAST, refine=ops.ACCURATE, check=ops.PLAIN, build=ops.FAST):
+        ins = insts[j % n_inst]
+        w = ins["wl"]
+        op = ops.KernelOperator(ins["X"], w.kernel, w.bandwidth)
+        ny = ops.Nystrom(op, ins["Om"], mode=build)
+        res = ops.pcg_solve(op, ins["B"], [float(w.lambdas[0])], nys=ny, tol=TOL, maxit=500, refine_every=20,
+                            inner_mode=inner, refine_mode=refine, check_mode=check)
         return op, ny, res
 
     for _ in range(a.warmup):
-        op, ny, res = step()
+        op, ny, res = step(0)
         del ny, op
-    times, iters_seen, launches = [], [], []
+    times, iters_seen, launches, by_seed = [], [], [], {}
     clk = ClockSampler(local)
     clk.start()
-    for _ in range(a.steps):
+    for j in range(a.steps):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         if dist:
@@ -228,18 +236,36 @@ def run_native(a):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        op, ny, res = step()
+        op, ny, res = step(j)
         e1.record(stream)
         torch.cuda.synchronize()
         launches.append(_ffi.lib().kop_launch_count() - l0)
         times.append(e0.elapsed_time(e1) / 1e3)
         iters_seen.append(res.iters[0])
-        last = (op, ny, res)
+        by_seed.setdefault(insts[j % n_inst]["seed"], []).append(times[-1])
+        last = (op, ny, res, insts[j % n_inst]["wl"])
         del ny, op
     clocks = clk.stop()
     t_step = max_over_ranks(statistics.mean(times), dist, dev)
-    op, ny, res = last
+    op, ny, res, wl_last = last
     value = world / t_step
+    seed_t = [statistics.mean(v) for v in by_seed.values()]
+    # the same PCG on the plain FP32 CUDA-core path: direct-difference kernel
+    # values and FP32 FMAs for every product (sketch, iterations, refinement)
+    plain_path = None
+    if not a.no_plain:
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        opp, nyp, resp = step(0, inner=ops.PLAIN, refine=ops.PLAIN, check=ops.PLAIN, build=ops.PLAIN)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tp = e0.elapsed_time(e1) / 1e3
+        plain_path = {"time_to_relres_s": tp, "pcg_iters": resp.iters[0], "converged": bool(resp.converged),
+                      "fused_speedup": tp / statistics.mean(by_seed[insts[0]["seed"]])
+                      if insts[0]["seed"] in by_seed else None}
+        del nyp, opp
 
     # fused operator product alone (m = 1), timed on the launching stream
     V = torch.randn(wl.n, 1, device=dev)
@@ -281,6 +307,9 @@ def run_native(a):
                    "n": n, "d": d, "rank": a.rank, "tol": TOL, "l2": "flushed (256 MB write) before each step",
                    "parallelism": f"replicas x{world}"},
         "time_to_relres_s": t_step,
+        "time_to_relres_by_seed_s": {"seeds": sorted(by_seed), "median": statistics.median(seed_t),
+                                     "min": min(seed_t), "max": max(seed_t)},
+        "plain_path": plain_path,
         "pcg_iters": iters_seen,
         "true_relres_accurate_op": res.true_relres[0],
         "matvec_ms": {"fused_fast": t_fast * 1e3, "plain_fp32": None if t_plain is None else t_plain * 1e3},
@@ -322,11 +351,12 @@ def run_native(a):
     try:
         from oracle import cmatvec
         xs = res.x.reshape(-1).cpu().numpy()
-        rows = np.random.default_rng(7).choice(wl.n, size=min(256, wl.n), replace=False)
-        kx = cmatvec.kernel_matvec(wl.kernel, wl.X, xs, wl.bandwidth, Z=wl.X[rows])
-        bvec = wl.B[:, 0].astype(np.float64)
-        r_s = bvec[rows] - kx - lam * xs[rows]
-        out["fp64_relres_sampled"] = float(np.sqrt(wl.n / len(rows)) * np.linalg.norm(r_s) / np.linalg.norm(bvec))
+        wv = wl_last
+        rows = np.random.default_rng(7).choice(wv.n, size=min(256, wv.n), replace=False)
+        kx = cmatvec.kernel_matvec(wv.kernel, wv.X, xs, wv.bandwidth, Z=wv.X[rows])
+        bvec = wv.B[:, 0].astype(np.float64)
+        r_s = bvec[rows] - kx - float(wv.lambdas[0]) * xs[rows]
+        out["fp64_relres_sampled"] = float(np.sqrt(wv.n / len(rows)) * np.linalg.norm(r_s) / np.linalg.norm(bvec))
     except Exception as e:  # the check is informational
         out["fp64_relres_sampled"] = f"unavailable: {e}"
     if rank == 0 and not a.no_cpu_baseline:
