@@ -212,12 +212,15 @@ def run_native(a):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
     stream = torch.cuda.current_stream()
 
-    def step(j, inner=ops.FAST, refine=ops.ACCURATE, check=ops.PLAIN, build=ops.FAST):
+    # refinement and acceptance both with the direct-difference operator: the
+    # tensor-core accurate operator's own residual floor on this data (~1.2e-6)
+    # is as large as the residuals it would replace
+    def step(j, inner=ops.FAST, refine=ops.PLAIN, check=ops.PLAIN, build=ops.FAST):
         ins = insts[j % n_inst]
         w = ins["wl"]
         op = ops.KernelOperator(ins["X"], w.kernel, w.bandwidth)
         ny = ops.Nystrom(op, ins["Om"], mode=build)
-        res = ops.pcg_solve(op, ins["B"], [float(w.lambdas[0])], nys=ny, tol=TOL, maxit=500, refine_every=20,
+        res = ops.pcg_solve(op, ins["B"], [float(w.lambdas[0])], nys=ny, tol=TOL, maxit=500, refine_every=30,
                             inner_mode=inner, refine_mode=refine, check_mode=check)
         return op, ny, res
 
@@ -339,7 +342,8 @@ def run_native(a):
             Omd = Omh.to(dev, non_blocking=True)
             op2 = ops.KernelOperator(Xd, wl.kernel, wl.bandwidth)
             ny2 = ops.Nystrom(op2, Omd, mode=ops.FAST)
-            r2 = ops.pcg_solve(op2, Bd, [lam], nys=ny2, tol=TOL, maxit=500, refine_every=20)
+            r2 = ops.pcg_solve(op2, Bd, [lam], nys=ny2, tol=TOL, maxit=500, refine_every=30,
+                               refine_mode=ops.PLAIN, check_mode=ops.PLAIN)
             xh.copy_(r2.x.reshape(-1), non_blocking=True)
             torch.cuda.synchronize()
             ets.append(time.perf_counter() - t0)

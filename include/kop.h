@@ -225,8 +225,12 @@ int nys_factor(nys_t ny, float* U_out, void* stream);
  * (0 = only at candidate stops and at maxit) the recursive residual is
  * replaced by the true one computed with `refine_mode` (iterative refinement:
  * operator products with `inner_mode`).  Recommended: inner KOP_FAST, refine
- * KOP_ACCURATE, check KOP_PLAIN (direct differences with error-free sums) or
- * KOP_EXACT for small badly conditioned systems.  ny = NULL gives plain CG
+ * and check KOP_PLAIN (direct differences with error-free sums), or KOP_EXACT
+ * for small badly conditioned systems, refine_every ~30.  The refinement
+ * operator must be accurate well below the residuals it replaces: the
+ * tensor-core KOP_ACCURATE operator's floor on clustered data far from the
+ * common centre is ~1e-6, and refining with it there slowed or stopped
+ * convergence.  ny = NULL gives plain CG
  * (IdentityConfig, App. A.1).
  * The preconditioner of column c uses damping mu[s] (host; NULL: mu = lambdas).
  *   lambdas      host, n_shifts values > 0

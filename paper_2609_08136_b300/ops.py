@@ -240,8 +240,8 @@ class SolveResult:
 
 
 def pcg_solve(op: KernelOperator, B: torch.Tensor, lambdas, nys: Nystrom | None = None, mu=None,
-              adaptive: bool = True, tol: float = 1e-6, maxit: int = 1000, refine_every: int = 20,
-              inner_mode: int = FAST, refine_mode: int = ACCURATE, check_mode: int = PLAIN, history: bool = False,
+              adaptive: bool = True, tol: float = 1e-6, maxit: int = 1000, refine_every: int = 30,
+              inner_mode: int = FAST, refine_mode: int = PLAIN, check_mode: int = PLAIN, history: bool = False,
               stream=None):
     """Block PCG for (K + lam_s I) x = B[:, j] over all shifts s and columns j
     (column s * nrhs + j of the result)."""
@@ -273,8 +273,8 @@ def pcg_solve(op: KernelOperator, B: torch.Tensor, lambdas, nys: Nystrom | None 
 
 
 def pcg_adjoint(op: KernelOperator, x: torch.Tensor, dLdx: torch.Tensor, lam: float, nys: Nystrom | None = None,
-                adaptive: bool = True, tol: float = 1e-6, maxit: int = 1000, refine_every: int = 20,
-                inner_mode: int = FAST, refine_mode: int = ACCURATE, check_mode: int = PLAIN, stream=None):
+                adaptive: bool = True, tol: float = 1e-6, maxit: int = 1000, refine_every: int = 30,
+                inner_mode: int = FAST, refine_mode: int = PLAIN, check_mode: int = PLAIN, stream=None):
     """g = (K + lam I)^{-1} dL/dx, and dL/dlam = -g^T x, dL/dbw = -g^T (dK/dbw) x.
     x, dL/dx and g are FP64 device vectors."""
     x2 = x.detach().reshape(-1).to(torch.float64).contiguous()
@@ -331,8 +331,8 @@ def solve_grad_points(op: KernelOperator, x: torch.Tensor, g: torch.Tensor, mode
 
 
 def krr_val_loss_and_grad(op: KernelOperator, nys: Nystrom | None, y: torch.Tensor, Xv: torch.Tensor,
-                          yv: torch.Tensor, lam: float, tol: float = 1e-6, maxit: int = 1000, refine_every: int = 20,
-                          inner_mode: int = FAST, refine_mode: int = ACCURATE, check_mode: int = PLAIN):
+                          yv: torch.Tensor, lam: float, tol: float = 1e-6, maxit: int = 1000, refine_every: int = 30,
+                          inner_mode: int = FAST, refine_mode: int = PLAIN, check_mode: int = PLAIN):
     """Validation loss L = (1/n_val) ||K(Xv, X) x - yv||^2 with x = (K + lam I)^{-1} y,
     and its derivatives with respect to the bandwidth and lam (adjoint method)."""
     res = pcg_solve(op, y, [lam], nys=nys, tol=tol, maxit=maxit, refine_every=refine_every, inner_mode=inner_mode,
