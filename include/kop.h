@@ -226,7 +226,10 @@ int nys_factor(nys_t ny, float* U_out, void* stream);
  * replaced by the true one computed with `refine_mode` (iterative refinement:
  * operator products with `inner_mode`).  Recommended: inner KOP_FAST, refine
  * and check KOP_PLAIN (direct differences with error-free sums), or KOP_EXACT
- * for small badly conditioned systems, refine_every ~30.  The refinement
+ * for small badly conditioned systems, refine_every ~30.  A periodic
+ * refinement is skipped when every active column's recursive residual is
+ * within 8x the tolerance (the candidate stop that follows recomputes the
+ * true residual itself).  The refinement
  * operator must be accurate well below the residuals it replaces: the
  * tensor-core KOP_ACCURATE operator's floor on clustered data far from the
  * common centre is ~1e-6, and refining with it there slowed or stopped

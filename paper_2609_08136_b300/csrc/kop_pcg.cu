@@ -27,6 +27,8 @@
 
 namespace kop {
 
+constexpr double kNearTol = 8.0;
+
 enum { OP_INIT = 0, OP_PQ = 1, OP_XR = 2, OP_DOT = 3, OP_P = 4, OP_RES = 5, OP_DOT2 = 6, OP_SPLIT = 7, OP_RES64 = 8 };
 
 // The iterate x is accumulated in FP64 (FP32 storage of x alone would limit
@@ -384,7 +386,7 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
       break;
     }
     if (hs == KOP_DEV_TIMEOUT) return fail(KOP_ETIMEOUT, "pcg: a bounded device wait timed out");
-    bool any_cand = false;
+    bool any_cand = false, all_near = true;
     for (int c = 0; c < cols; ++c) {
       cand[c] = 0;
       if (!act[c]) continue;
@@ -394,8 +396,13 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
         cand[c] = 1;
         any_cand = true;
       }
+      all_near = all_near && rel[c] <= kNearTol * pb.tol;
     }
-    const bool refine = any_cand || (pb.refine_every > 0 && it % pb.refine_every == 0) || it == pb.maxit;
+    // a periodic refinement is skipped when every active column is within
+    // kNearTol of the tolerance: its candidate stop, a few iterations later,
+    // recomputes the true residual anyway
+    const bool periodic = pb.refine_every > 0 && it % pb.refine_every == 0 && !all_near;
+    const bool refine = any_cand || periodic || it == pb.maxit;
     if (refine) {
       // the true residual replaces the recursive one: the refinement operator
       // for periodic replacement, the check operator when a column may stop
