@@ -223,6 +223,27 @@ def nystrom_adaptive(apply_A, Omega, rank_init, rank_max, power_iters, err_tol, 
         r = min(2 * r, int(rank_max))
 
 
+def ridge_normal_matvec(X, V):
+    """(X^T X) V without forming X^T X (the ridge normal operator, Sec. 5.1,
+    Eq. "experiment-ridge")."""
+    X = np.asarray(X, dtype=np.float64)
+    return X.T @ (X @ np.asarray(V, dtype=np.float64))
+
+
+def ridge_rhs(X, y):
+    """b = X^T y of (X^T X + lam I) w = X^T y."""
+    return np.asarray(X, dtype=np.float64).T @ np.asarray(y, dtype=np.float64)
+
+
+def ridge_exact_solution(V, g, alpha, lam):
+    """w* for the constructed data X = U diag(s) V^T, y = U g / ||g||,
+    s_i = i^(-alpha/2) (Eq. "experiment-ridge-data"):
+    w* = (X^T X + lam I)^-1 X^T y = V diag(s / (s^2 + lam)) g / ||g||."""
+    p = V.shape[1]
+    s = np.arange(1, p + 1, dtype=np.float64) ** (-alpha / 2.0)
+    return V @ ((s / (s * s + lam)) * (g / np.linalg.norm(g)))
+
+
 def nystrom_rho(lam_hat, mu, adaptive=True):
     """Damping of the complement subspace (App. A.5 NystromConfig):
     adaptive adds the smallest retained eigenvalue lam_hat_r to mu."""

@@ -24,6 +24,8 @@ data for this path, so every workload is synthetic:
 * ``krr_rbf_hyper``    train n=1e5, val n=2e4, d=32, X ~ N(0, I), RBF
                        sigma0 = sqrt(d), lam0 = 1e-4 n_train, r = 500,
                        y = sin(X w) + 0.1 eps for both splits.
+* ``ridge_spectral``   ridge regression (Sec. 5.1): X = U Sigma_alpha V^T,
+                       Sigma_alpha = diag(i^(-alpha/2)), y = U g / ||g||.
 
 The sketch matrix Omega is n x r with entries N(0,1)/sqrt(n), drawn with seed
 1000 + seed, so that Omega^T Omega is close to the identity.
@@ -129,6 +131,36 @@ def krr_rbf_hyper(seed: int = 0, n: int = 100_000, nval: int = 20_000, d: int = 
     yv = np.sin(Xv @ w) + 0.1 * rng.standard_normal(nval)
     return Workload("krr_rbf_hyper", _f32(X), _f32(y[:, None]), RBF, float(np.sqrt(d)),
                     np.array([1e-4 * n]), rank, Xval=_f32(Xv), yval=_f32(yv), seed=seed)
+
+
+@dataclasses.dataclass
+class RidgeWorkload:
+    """Ridge regression data of the paper's ridge experiments (Sec. 5.1):
+    X = U diag(i^(-alpha/2)) V^T (n x p, n >= p), y = U g / ||g||; the system is
+    (X^T X + lam I) w = X^T y.  U (n x p) and V (p x p) have orthonormal
+    columns (QR of Gaussian matrices; the paper uses structured orthogonal
+    matrices, which only matters for speed at large n)."""
+    X: np.ndarray        # n x p float32
+    y: np.ndarray        # n float32
+    U: np.ndarray        # n x p float64
+    V: np.ndarray        # p x p float64
+    g: np.ndarray        # p float64 (before normalization)
+    alpha: float
+    lam: float
+
+
+def ridge_spectral(seed: int = 0, n: int = 4096, p: int = 1024, alpha: float = 1.0,
+                   lam: float = 1e-4) -> RidgeWorkload:
+    if n < p:
+        raise ValueError("the ridge workloads have n >= p")
+    rng = np.random.default_rng(seed)
+    U, _ = np.linalg.qr(rng.standard_normal((n, p)))
+    V, _ = np.linalg.qr(rng.standard_normal((p, p)))
+    sig = np.arange(1, p + 1, dtype=np.float64) ** (-alpha / 2.0)
+    g = rng.standard_normal(p)
+    X = (U * sig) @ V.T
+    y = U @ (g / np.linalg.norm(g))
+    return RidgeWorkload(_f32(X), _f32(y), U, V, g, float(alpha), float(lam))
 
 
 def random_points(n: int, d: int, seed: int, scale: float = 1.0, shift: float = 0.0) -> np.ndarray:

@@ -371,3 +371,34 @@ def test_point_gradient_translation_invariance_and_two_points():
     c = a2[0] * b2[1] + a2[1] * b2[0]
     assert np.allclose(G2[0], [-c * math.exp(-1.0 / 8.0) / 4.0, 0.0], rtol=1e-14, atol=1e-15)
     assert np.allclose(G2[1], -G2[0], rtol=1e-14, atol=1e-15)
+
+
+# ---------------------------------------------------------------- ridge workload
+def test_ridge_spectrum_is_the_constructed_one():
+    # X^T X + lam I has eigenvalues i^-alpha + lam (the paper's statement of its
+    # construction), so condition number (1 + lam) / (p^-alpha + lam)
+    wl = W.ridge_spectral(seed=3, n=400, p=96, alpha=2.0, lam=1e-4)
+    X = wl.X.astype(np.float64)
+    ev = np.sort(np.linalg.eigvalsh(X.T @ X + wl.lam * np.eye(96)))[::-1]
+    want = np.arange(1, 97, dtype=np.float64) ** -2.0 + 1e-4
+    assert np.allclose(ev, want, rtol=1e-5, atol=1e-7)
+
+
+def test_ridge_nystrom_pcg_reaches_the_closed_form_solution():
+    wl = W.ridge_spectral(seed=4, n=600, p=200, alpha=1.0, lam=1e-4)
+    X = wl.X.astype(np.float64)
+    b = O.ridge_rhs(X, wl.y)
+    A = lambda v: O.ridge_normal_matvec(X, v) + wl.lam * v
+    Om = np.random.default_rng(5).standard_normal((200, 40)) / np.sqrt(200)
+    U, lam_hat, _ = O.nystrom(O.ridge_normal_matvec(X, Om), Om)
+    rho = O.nystrom_rho(lam_hat, wl.lam)
+    Pinv = lambda v: O.precond_apply(U, lam_hat, wl.lam, rho, v)
+    w, it, _ = O.pcg(A, b, Pinv, tol=1e-10, maxit=400)
+    # the closed form uses the float64 U, V of the construction while X is its
+    # float32 rounding: agreement to the rounding of X amplified by the condition
+    ws = O.ridge_exact_solution(wl.V, wl.g, wl.alpha, wl.lam)
+    assert np.linalg.norm(w - ws) / np.linalg.norm(ws) <= 2e-3
+    # and exactly the solution of the float32 X
+    wd = np.linalg.solve(X.T @ X + wl.lam * np.eye(200), b)
+    assert np.linalg.norm(w - wd) / np.linalg.norm(wd) <= 1e-8
+    assert it < 60
