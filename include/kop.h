@@ -104,6 +104,17 @@ int kop_sfu_rates(double* rates, void* stream);
  * about n * d' * 10 bytes.                                                  */
 int kop_create(const float* X, int64_t n, int32_t d, int32_t kernel, double bandwidth,
                void* stream, kop_t* out);
+/* The normal operator A = X^T X of a data matrix X (device, n x p FP32
+ * row-major; copied), the operator of ridge regression (X^T X + lam I) w =
+ * X^T y in the paper's ridge experiments (Sec. 5.1).  A is applied as
+ * X^T (X V) by two passes over X, never formed.  The handle works with
+ * kop_matvec (mode KOP_FAST: FP32; KOP_ACCURATE / KOP_PLAIN: error-free
+ * float-float sums of exact FP32 products), kop_matvec_f64 (deriv = 0),
+ * nys_build, nys_build_adaptive, pcg_solve and pcg_adjoint (dL/dbw = 0); its
+ * vectors have p entries.  Entry points of kernel operators only (bandwidth,
+ * cross products, point gradients) return KOP_EINVAL.
+ * 1 <= n < 2^31, 1 <= p <= 65536.                                          */
+int kop_create_ridge(const float* X, int64_t n, int32_t p, void* stream, kop_t* out);
 int kop_destroy(kop_t op);
 /* Change the bandwidth in place (the points are kept). */
 int kop_set_bandwidth(kop_t op, double bandwidth);

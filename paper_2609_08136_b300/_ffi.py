@@ -29,6 +29,7 @@ SIGNATURES = {
     "kop_sync": (c_int, [c_vp, c_vp]),
     "nys_build": (c_int, [c_vp, c_vp, c_i32, c_dbl, c_i32, c_vp, P(c_vp)]),
     "nys_destroy": (c_int, [c_vp]),
+    "kop_create_ridge": (c_int, [c_vp, c_i64, c_i32, c_vp, P(c_vp)]),
     "kop_grad_points": (c_int, [c_vp, c_vp, c_vp, c_i32, c_vp, c_vp]),
     "nys_build_adaptive": (c_int, [c_vp, c_vp, c_i32, c_i32, c_i32, c_i32, c_dbl, c_vp, c_dbl, c_i32, c_vp,
                                    P(c_vp), P(c_i32), P(c_dbl), P(c_i32), P(c_dbl), c_i32]),

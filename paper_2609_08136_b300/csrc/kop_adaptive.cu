@@ -86,7 +86,6 @@ static int error_estimate(nys_s* ny, int mode, const float* g0, int iters, float
   kop_s* op = ny->op;
   const int64_t n = ny->n;
   const int r = ny->r;
-  const KConst kc = kernel_constants(op->kernel, op->bw);
   const unsigned nb = (unsigned)((n + 255) / 256);
   double* acc = dev;
   double* alpha = dev + 1;  // -1: uw_ff returns -K v + U W = -E v
@@ -100,7 +99,7 @@ static int error_estimate(nys_s* ny, int mode, const float* g0, int iters, float
   KOP_LAUNCHED();
   double est = 0.0;
   for (int it = 0; it < iters; ++it) {
-    if ((rc = op_matvec(op->pts, op->pts, true, op->kernel, kc, mode, v, 1, 1, kv, 1, op->status, st))) return rc;
+    if ((rc = op_apply(op, mode, v, 1, 1, kv, 1, st))) return rc;
     if ((rc = utv_ff(ny->U, r, n, r, v, 1, wd, st))) return rc;
     lam_scale_split_kernel<<<(unsigned)((r + 127) / 128), 128, 0, st>>>(wd, ny->lam_dev, r);
     KOP_LAUNCHED();
@@ -126,7 +125,7 @@ extern "C" int nys_build_adaptive(kop_t op, const float* Omega, int32_t ld_omega
   if (!out) return fail(KOP_EINVAL, "nys_build_adaptive: out is NULL");
   *out = nullptr;
   if (!op || !Omega || !g0) return fail(KOP_EINVAL, "nys_build_adaptive: NULL argument");
-  const int64_t n = op->pts.n;
+  const int64_t n = op_dim(op);
   if (rank_init < 1 || rank_max < rank_init || rank_max > 2048 || rank_max > n)
     return fail(KOP_EINVAL, "nys_build_adaptive: need 1 <= rank_init <= rank_max <= min(n, 2048)");
   if (ld_omega < rank_max) return fail(KOP_EINVAL, "nys_build_adaptive: ld_omega < rank_max");

@@ -19,7 +19,24 @@ int op_matvec(const PointSet& Q, const PointSet& Ks, bool self, int kf, const KC
                       v_bf16_exact);
 }
 
+int op_apply(kop_s* op, int mode, const float* V, int m, int ldv, float* O, int ldo, cudaStream_t st,
+             bool v_bf16_exact) {
+  if (op->ridge) return ridge_apply(op, mode, V, m, ldv, O, ldo, st);
+  const KConst kc = kernel_constants(op->kernel, op->bw);
+  return op_matvec(op->pts, op->pts, true, op->kernel, kc, mode, V, m, ldv, O, ldo, op->status, st, v_bf16_exact);
+}
+
+int op_apply_f64(kop_s* op, const double* V, int m, int ldv, double* O, int ldo, cudaStream_t st) {
+  if (op->ridge) return ridge_apply_f64(op, V, m, ldv, O, ldo, st);
+  return exact_matvec(op->pts, op->pts, op->kernel, op->bw, V, m, ldv, O, ldo, st);
+}
+
 static bool bad_mode(int mode) { return mode < KOP_FAST || mode > KOP_EXACT; }
+
+// Entry points that exist only for kernel operators.
+static int need_kernel(const kop_s* op, const char* where) {
+  return op->ridge ? fail(KOP_EINVAL, std::string(where) + ": not defined for a ridge (X^T X) operator") : KOP_OK;
+}
 
 }  // namespace kop
 
@@ -68,6 +85,12 @@ extern "C" int kop_create(const float* X, int64_t n, int32_t d, int32_t kernel, 
 extern "C" int kop_destroy(kop_t op) {
   if (!op) return KOP_OK;
   cudaDeviceSynchronize();
+  if (op->ridge) {
+    cudaFree(op->rX);
+    cudaFree(op->status);
+    delete op;
+    return KOP_OK;
+  }
   pointset_free(op->pts, 0);
   cudaFree(op->mean);
   cudaDeviceSynchronize();
@@ -77,6 +100,7 @@ extern "C" int kop_destroy(kop_t op) {
 
 extern "C" int kop_set_bandwidth(kop_t op, double bandwidth) {
   if (!op) return fail(KOP_EINVAL, "kop_set_bandwidth: NULL handle");
+  if (int rc = need_kernel(op, "kop_set_bandwidth")) return rc;
   if (!(bandwidth > 0.0) || !std::isfinite(bandwidth)) return fail(KOP_EINVAL, "kop_set_bandwidth: bandwidth must be > 0");
   op->bw = bandwidth;
   return KOP_OK;
@@ -86,13 +110,14 @@ extern "C" int kop_matvec(kop_t op, const float* V, int32_t m, float* O, int32_t
   if (!op || !V || !O) return fail(KOP_EINVAL, "kop_matvec: NULL argument");
   if (m < 1) return fail(KOP_EINVAL, "kop_matvec: m must be >= 1");
   if (bad_mode(mode)) return fail(KOP_EINVAL, "kop_matvec: unknown mode");
-  const KConst kc = kernel_constants(op->kernel, op->bw);
-  return op_matvec(op->pts, op->pts, true, op->kernel, kc, mode, V, m, m, O, m, op->status, (cudaStream_t)stream);
+  return op_apply(op, mode, V, m, m, O, m, (cudaStream_t)stream);
 }
 
 extern "C" int kop_matvec_f64(kop_t op, const double* V, int32_t m, double* O, int32_t deriv, void* stream) {
   if (!op || !V || !O) return fail(KOP_EINVAL, "kop_matvec_f64: NULL argument");
   if (m < 1) return fail(KOP_EINVAL, "kop_matvec_f64: m must be >= 1");
+  if (!deriv) return op_apply_f64(op, V, m, m, O, m, (cudaStream_t)stream);
+  if (int rc = need_kernel(op, "kop_matvec_f64")) return rc;
   return exact_matvec(op->pts, op->pts, op->kernel + (deriv ? 3 : 0), op->bw, V, m, m, O, m, (cudaStream_t)stream);
 }
 
@@ -100,6 +125,7 @@ extern "C" int kop_dbw_matvec(kop_t op, const float* V, int32_t m, float* O, int
   if (!op || !V || !O) return fail(KOP_EINVAL, "kop_dbw_matvec: NULL argument");
   if (m < 1) return fail(KOP_EINVAL, "kop_dbw_matvec: m must be >= 1");
   if (bad_mode(mode)) return fail(KOP_EINVAL, "kop_dbw_matvec: unknown mode");
+  if (int rc = need_kernel(op, "kop_dbw_matvec")) return rc;
   const KConst kc = kernel_constants(op->kernel + 3, op->bw);
   return op_matvec(op->pts, op->pts, true, op->kernel + 3, kc, mode, V, m, m, O, m, op->status,
                    (cudaStream_t)stream);
@@ -111,6 +137,7 @@ extern "C" int kop_cross_matvec(kop_t op, const float* Z, int64_t nz, const floa
   if (nz < 1 || nz >= (int64_t(1) << 31)) return fail(KOP_EINVAL, "kop_cross_matvec: nz must be in [1, 2^31)");
   if (m < 1) return fail(KOP_EINVAL, "kop_cross_matvec: m must be >= 1");
   if (bad_mode(mode)) return fail(KOP_EINVAL, "kop_cross_matvec: unknown mode");
+  if (int rc = need_kernel(op, "kop_cross_matvec")) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   PointSet zs;
   int rc = pointset_alloc(zs, nz, op->pts.d, st);

@@ -60,6 +60,7 @@ using namespace kop;
 
 extern "C" int kop_grad_points(kop_t op, const float* a, const float* b, int32_t mode, float* G, void* stream) {
   if (!op || !a || !b || !G) return fail(KOP_EINVAL, "kop_grad_points: NULL argument");
+  if (op->ridge) return fail(KOP_EINVAL, "kop_grad_points: not defined for a ridge (X^T X) operator");
   if (mode != KOP_FAST && mode != KOP_ACCURATE && mode != KOP_EXACT)
     return fail(KOP_EINVAL, "kop_grad_points: mode must be KOP_FAST, KOP_ACCURATE or KOP_EXACT");
   cudaStream_t st = (cudaStream_t)stream;

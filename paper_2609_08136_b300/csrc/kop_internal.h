@@ -116,7 +116,26 @@ struct kop_s {
   double bw = 1.0;
   double* mean = nullptr;  // device, d
   int* status = nullptr;   // device status word
+  // the normal operator X^T X of a data matrix (ridge regression) instead of a
+  // kernel matrix, when ridge != 0
+  int ridge = 0;
+  float* rX = nullptr;  // device n x p copy of X
+  int64_t rn = 0;       // rows of X
+  int rp = 0;           // columns of X: the operator's dimension
 };
+
+namespace kop {
+// Dimension of the operator's vectors, and that padded to 128 rows.
+inline int64_t op_dim(const kop_s* op) { return op->ridge ? op->rp : op->pts.n; }
+inline int64_t op_dim_pad(const kop_s* op) { return op->ridge ? ((int64_t)op->rp + 127) / 128 * 128 : op->pts.n_pad; }
+// O = A V with the operator's product in `mode` (kernel K(X, X) or X^T X).
+int op_apply(kop_s* op, int mode, const float* V, int m, int ldv, float* O, int ldo, cudaStream_t st,
+             bool v_bf16_exact = false);
+// FP64 product with the operator (KOP_EXACT arithmetic).
+int op_apply_f64(kop_s* op, const double* V, int m, int ldv, double* O, int ldo, cudaStream_t st);
+int ridge_apply(const kop_s* op, int mode, const float* V, int m, int ldv, float* O, int ldo, cudaStream_t st);
+int ridge_apply_f64(const kop_s* op, const double* V, int m, int ldv, double* O, int ldo, cudaStream_t st);
+}  // namespace kop
 
 // Stream-ordered device scratch, freed on the same stream when it goes out of scope.
 struct DevBuf {

@@ -99,7 +99,7 @@ extern "C" int nys_build(kop_t op, const float* Omega, int32_t r, double nu_rel,
   if (!out) return fail(KOP_EINVAL, "nys_build: out is NULL");
   *out = nullptr;
   if (!op || !Omega) return fail(KOP_EINVAL, "nys_build: NULL argument");
-  const int64_t n = op->pts.n;
+  const int64_t n = op_dim(op);
   if (r < 1 || r > 2048 || r > n) return fail(KOP_EINVAL, "nys_build: r must be in [1, min(n, 2048)]");
   if (mode < KOP_FAST || mode > KOP_EXACT) return fail(KOP_EINVAL, "nys_build: bad mode");
   if (!std::isfinite(nu_rel)) return fail(KOP_EINVAL, "nys_build: nu_rel must be finite");
@@ -107,7 +107,7 @@ extern "C" int nys_build(kop_t op, const float* Omega, int32_t r, double nu_rel,
   if (!(nu_rel > 0.0)) nu_rel = mode == KOP_FAST ? std::ldexp(1.0, -16) : std::ldexp(1.0, -21);
 
   const size_t rr = (size_t)r * r;
-  const int64_t n_pad = op->pts.n_pad;
+  const int64_t n_pad = op_dim_pad(op);
   // workspace
   DevBuf wsY, wsR, wsU, wsO;
   wsY.st = wsR.st = wsU.st = wsO.st = st;
@@ -143,8 +143,7 @@ extern "C" int nys_build(kop_t op, const float* Omega, int32_t r, double nu_rel,
 
   int rc;
   // 1. sketch Y = K Omega (fused operator, m = r)
-  const KConst kc = kernel_constants(op->kernel, op->bw);
-  rc = op_matvec(op->pts, op->pts, true, op->kernel, kc, mode, Omega, r, r, Y, r, op->status, st, true);
+  rc = op_apply(op, mode, Omega, r, r, Y, r, st, true);
   if (rc) return rc;
   // 2. Gram blocks
   if ((rc = gram(Omega, r, Omega, r, n, r, r, Goo, r, st))) return rc;

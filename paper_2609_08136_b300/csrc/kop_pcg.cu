@@ -265,7 +265,7 @@ static int device_status(kop_s* op, cudaStream_t st, int* h) {
 
 int pcg_core(PcgProblem& pb, cudaStream_t st) {
   kop_s* op = pb.op;
-  const int64_t n = op->pts.n;
+  const int64_t n = op_dim(op);
   const int cols = pb.cols;
   const size_t nc = (size_t)n * cols;
   const int r = pb.ny ? pb.ny->r : 0;
@@ -333,13 +333,11 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
     }
     return nys_apply_dev(pb.ny, mu, pb.adaptive, R, cols, Z, Wd, palpha, Wf, acol, st);
   };
-  const KConst kc = kernel_constants(op->kernel, op->bw);
   auto matvec = [&](const float* V, float* O, int mode) -> int {
-    return op_matvec(op->pts, op->pts, true, op->kernel, kc, mode, V, cols, cols, O, cols, op->status, st);
+    return op_apply(op, mode, V, cols, cols, O, cols, st);
   };
   auto matvec2 = [&](const float* V, float* O, int mode) -> int {
-    return op_matvec(op->pts, op->pts, true, op->kernel, kc, mode, V, 2 * cols, 2 * cols, O, 2 * cols, op->status,
-                     st);
+    return op_apply(op, mode, V, 2 * cols, 2 * cols, O, 2 * cols, st);
   };
 
   // x0 = 0, r0 = b, ||b|| per column
@@ -409,7 +407,7 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
       int rmode = (any_cand || it == pb.maxit) ? pb.check_mode : pb.refine_mode;
       if (rmode == KOP_PLAIN) rmode = KOP_PLAIN_CHECK;
       if (rmode == KOP_EXACT) {
-        if ((rc = exact_matvec(op->pts, op->pts, op->kernel, op->bw, X, cols, cols, T64, cols, st))) return rc;
+        if ((rc = op_apply_f64(op, X, cols, cols, T64, cols, st))) return rc;
         if ((rc = vec_launch<OP_RES64>(va, st))) return rc;
       } else {
         if ((rc = vec_launch<OP_SPLIT>(va, st))) return rc;
@@ -524,7 +522,7 @@ extern "C" int pcg_adjoint(kop_t op, nys_t ny, double lam, int32_t adaptive, con
   if (!valid_mode(inner_mode) || !valid_mode(refine_mode) || !valid_mode(check_mode))
     return fail(KOP_EINVAL, "pcg_adjoint: bad mode");
   cudaStream_t st = (cudaStream_t)stream;
-  const int64_t n = op->pts.n;
+  const int64_t n = op_dim(op);
   Workspace ws;
   ws.st = st;
   // Bf (n) | V2 (2n) | T2 (2n) floats, acc (2) doubles
@@ -564,7 +562,9 @@ extern "C" int pcg_adjoint(kop_t op, nys_t ny, double lam, int32_t adaptive, con
   // columns of the split (or one FP64 product in exact mode)
   dot_kernel<<<4 * num_sms(), 256, 0, st>>>(g_out, V2, V2 + 1, n, 2, acc);
   KOP_LAUNCHED();
-  if (check_mode == KOP_EXACT) {
+  if (op->ridge) {
+    // X^T X has no bandwidth: dL/dbw = 0
+  } else if (check_mode == KOP_EXACT) {
     double* t64 = nullptr;
     KOP_CUDA_TRY(cudaMallocAsync((void**)&t64, sizeof(double) * n, st));
     int r2 = exact_matvec(op->pts, op->pts, op->kernel + 3, op->bw, x, 1, 1, t64, 1, st);

@@ -194,6 +194,7 @@ template <int KF, bool COMP>
 static int launch_plain_kf(const PointSet& Q, const PointSet& Ks, const float* V, int m, int ldv, float* O, int ldo,
                            const PlainConst& pc, cudaStream_t st) {
   if (m == 1) return launch_plain_t<KF, 1, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st);
+  if (m == 2) return launch_plain_t<KF, 2, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st);
   if (m <= 4) return launch_plain_t<KF, 4, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st);
   return launch_plain_t<KF, 8, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st);
 }

@@ -135,6 +135,23 @@ class KernelOperator:
         check(_ffi.lib().kop_sync(self._h, _stream(stream)), "kop_sync")
 
 
+class RidgeOperator(KernelOperator):
+    """A = X^T X for a data matrix X (n x p, CUDA float32): kop_create_ridge.
+    Vectors have p entries; matvec, Nystrom, pcg_solve and pcg_adjoint accept it."""
+
+    def __init__(self, X: torch.Tensor, stream=None):
+        X = _dev_f32(X, "X")
+        self.rows, self.n = X.shape
+        self.d = None
+        self.kernel = None
+        self.bandwidth = None
+        self.device = X.device
+        h = ctypes.c_void_p()
+        check(_ffi.lib().kop_create_ridge(_ptr(X), self.rows, self.n, _stream(stream), ctypes.byref(h)),
+              "kop_create_ridge")
+        self._h = h
+
+
 class Nystrom:
     """Randomized Nystrom preconditioner of an operator: nys_build / nys_apply."""
 
