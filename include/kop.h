@@ -249,7 +249,13 @@ int nys_factor(nys_t ny, float* U_out, void* stream);
  * The preconditioner of column c uses damping mu[s] (host; NULL: mu = lambdas).
  *   lambdas      host, n_shifts values > 0
  *   B            device, n x nrhs
- *   Xout         device, n x (nrhs * n_shifts), FP64 (x0 = 0).  The iterate is
+ *   X0           device or NULL, n x (nrhs * n_shifts) FP64: warm start (NULL:
+ *                x0 = 0; columns with b = 0 return 0).  The first residual is
+ *                b - (A + lam I) x0 with `check_mode`; a column whose start
+ *                already meets the tolerance returns x0 after 0 iterations.
+ *                (The inner solves of ADMM, App. A.4's NysADMM, warm-start
+ *                from the previous x with a changing shift rho.)
+ *   Xout         device, n x (nrhs * n_shifts), FP64.  The iterate is
  *                accumulated in FP64: FP32 storage of x alone would bound the
  *                attainable FP64 residual near 2^-24 ||A|| ||x|| / ||b||.
  *   iters        host, nrhs * n_shifts ints (operator products per column)
@@ -259,7 +265,7 @@ int nys_factor(nys_t ny, float* U_out, void* stream);
  * Returns KOP_OK, KOP_NOT_CONVERGED (outputs written), KOP_ENOTPD on a
  * breakdown.  Synchronizes `stream`.                                         */
 int pcg_solve(kop_t op, nys_t ny, const double* lambdas, int32_t n_shifts, const double* mu,
-              int32_t adaptive, const float* B, int32_t nrhs, double tol, int32_t maxit,
+              int32_t adaptive, const float* B, int32_t nrhs, const double* X0, double tol, int32_t maxit,
               int32_t refine_every, int32_t inner_mode, int32_t refine_mode, int32_t check_mode,
               double* Xout, int32_t* iters, double* res_hist, double* true_relres, void* stream);
 

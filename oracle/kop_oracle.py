@@ -244,6 +244,13 @@ def ridge_exact_solution(V, g, alpha, lam):
     return V @ ((s / (s * s + lam)) * (g / np.linalg.norm(g)))
 
 
+def shifted_solve(A, rhs, shift):
+    """x = (A + shift I)^-1 rhs for a dense symmetric A (the linear system of an
+    ADMM x-update, App. A.4), by a dense FP64 solve."""
+    A = np.asarray(A, dtype=np.float64)
+    return np.linalg.solve(A + shift * np.eye(A.shape[0]), np.asarray(rhs, dtype=np.float64))
+
+
 def nystrom_rho(lam_hat, mu, adaptive=True):
     """Damping of the complement subspace (App. A.5 NystromConfig):
     adaptive adds the smallest retained eigenvalue lam_hat_r to mu."""

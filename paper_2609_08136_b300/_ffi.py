@@ -37,7 +37,7 @@ SIGNATURES = {
     "nys_apply_noalloc": (c_int, [c_vp, P(c_dbl), c_i32, c_vp, c_i32, c_vp, c_vp]),
     "nys_eigs": (c_int, [c_vp, P(c_dbl), P(c_dbl), P(c_i32)]),
     "nys_factor": (c_int, [c_vp, c_vp, c_vp]),
-    "pcg_solve": (c_int, [c_vp, c_vp, P(c_dbl), c_i32, P(c_dbl), c_i32, c_vp, c_i32, c_dbl, c_i32, c_i32,
+    "pcg_solve": (c_int, [c_vp, c_vp, P(c_dbl), c_i32, P(c_dbl), c_i32, c_vp, c_i32, c_vp, c_dbl, c_i32, c_i32,
                           c_i32, c_i32, c_i32, c_vp, P(c_i32), P(c_dbl), P(c_dbl), c_vp]),
     "pcg_adjoint": (c_int, [c_vp, c_vp, c_dbl, c_i32, c_vp, c_vp, c_dbl, c_i32, c_i32, c_i32, c_i32, c_i32, c_vp,
                             P(c_i32), P(c_dbl), P(c_dbl), c_vp]),

@@ -241,6 +241,7 @@ struct PcgProblem {
   std::vector<double> lam, mu;
   int adaptive = 1;
   const float* B = nullptr;
+  const double* X0 = nullptr;  // optional warm start (n x cols FP64)
   double* Xout = nullptr;
   double tol = 1e-6;
   int maxit = 1000, refine_every = 0, inner_mode = KOP_FAST, refine_mode = KOP_ACCURATE, check_mode = KOP_PLAIN;
@@ -261,6 +262,12 @@ static int device_status(kop_s* op, cudaStream_t st, int* h) {
   KOP_CUDA_TRY(cudaMemcpyAsync(h, op->status, sizeof(int), cudaMemcpyDeviceToHost, st));
   KOP_CUDA_TRY(cudaStreamSynchronize(st));
   return KOP_OK;
+}
+
+// X[i][c] = 0 for the columns c that are not active.
+__global__ void zero_inactive_kernel(double* __restrict__ X, int64_t nc, int cols, const int* __restrict__ active) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < nc && !active[t % cols]) X[t] = 0.0;
 }
 
 int pcg_core(PcgProblem& pb, cudaStream_t st) {
@@ -302,7 +309,7 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
   double* X = pb.Xout;
 
   std::vector<int> act(cols, 1);
-  std::vector<double> hb(cols), nb(cols), rel(cols, 0.0);
+  std::vector<double> hb(cols), nb(cols), rel(cols, 0.0), hr0(cols);
   KOP_CUDA_TRY(cudaMemcpyAsync(lam, pb.lam.data(), sizeof(double) * cols, cudaMemcpyHostToDevice, st));
   KOP_CUDA_TRY(cudaMemcpyAsync(mu, pb.mu.data(), sizeof(double) * cols, cudaMemcpyHostToDevice, st));
   KOP_CUDA_TRY(cudaMemsetAsync(op->status, 0, sizeof(int), st));
@@ -358,6 +365,38 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
   for (int it = 1; pb.res_hist && it <= pb.maxit; ++it)
     for (int c = 0; c < cols; ++c) pb.res_hist[(size_t)it * cols + c] = NAN;
   KOP_CUDA_TRY(cudaMemcpyAsync(active, act.data(), sizeof(int) * cols, cudaMemcpyHostToDevice, st));
+  if (pb.X0 && any) {
+    // warm start: x = x0 (columns with b = 0 keep x = 0), r0 = b - (A + lam I) x0
+    // with the check operator; a column whose start already meets the
+    // tolerance stops after 0 iterations
+    KOP_CUDA_TRY(cudaMemcpyAsync(X, pb.X0, sizeof(double) * nc, cudaMemcpyDeviceToDevice, st));
+    zero_inactive_kernel<<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(X, (int64_t)nc, cols, active);
+    KOP_LAUNCHED();
+    int rmode = pb.check_mode == KOP_PLAIN ? KOP_PLAIN_CHECK : pb.check_mode;
+    if (rmode == KOP_EXACT) {
+      if ((rc = op_apply_f64(op, X, cols, cols, T64, cols, st))) return rc;
+      if ((rc = vec_launch<OP_RES64>(va, st))) return rc;
+    } else {
+      if ((rc = vec_launch<OP_SPLIT>(va, st))) return rc;
+      if ((rc = matvec2(V2, T, rmode))) return rc;
+      if ((rc = vec_launch<OP_RES>(va, st))) return rc;
+    }
+    KOP_CUDA_TRY(cudaMemcpyAsync(hr0.data(), acc, sizeof(double) * cols, cudaMemcpyDeviceToHost, st));
+    KOP_CUDA_TRY(cudaStreamSynchronize(st));
+    any = false;
+    for (int c = 0; c < cols; ++c) {
+      if (!act[c]) continue;
+      const double tr = std::sqrt(hr0[c]) / nb[c];
+      if (pb.res_hist) pb.res_hist[c] = tr;
+      if (pb.true_relres) pb.true_relres[c] = tr;
+      if (tr <= pb.tol) {
+        act[c] = 0;
+        if (pb.iters) pb.iters[c] = 0;
+      }
+      any = any || act[c];
+    }
+    KOP_CUDA_TRY(cudaMemcpyAsync(active, act.data(), sizeof(int) * cols, cudaMemcpyHostToDevice, st));
+  }
   if ((rc = apply_prec())) return rc;
   va.acc = rz;
   if ((rc = vec_launch<OP_DOT>(va, st))) return rc;
@@ -457,9 +496,10 @@ using namespace kop;
 static bool valid_mode(int m) { return m >= KOP_FAST && m <= KOP_EXACT; }
 
 extern "C" int pcg_solve(kop_t op, nys_t ny, const double* lambdas, int32_t n_shifts, const double* mu,
-                         int32_t adaptive, const float* B, int32_t nrhs, double tol, int32_t maxit,
-                         int32_t refine_every, int32_t inner_mode, int32_t refine_mode, int32_t check_mode,
-                         double* Xout, int32_t* iters, double* res_hist, double* true_relres, void* stream) {
+                         int32_t adaptive, const float* B, int32_t nrhs, const double* X0, double tol,
+                         int32_t maxit, int32_t refine_every, int32_t inner_mode, int32_t refine_mode,
+                         int32_t check_mode, double* Xout, int32_t* iters, double* res_hist, double* true_relres,
+                         void* stream) {
   if (!op || !lambdas || !B || !Xout || !iters) return fail(KOP_EINVAL, "pcg_solve: NULL argument");
   if (ny && ny->op != op) return fail(KOP_EINVAL, "pcg_solve: preconditioner built for another operator");
   if (n_shifts < 1 || nrhs < 1 || (int64_t)n_shifts * nrhs > 4096)
@@ -484,6 +524,7 @@ extern "C" int pcg_solve(kop_t op, nys_t ny, const double* lambdas, int32_t n_sh
   }
   pb.adaptive = adaptive ? 1 : 0;
   pb.B = B;
+  pb.X0 = X0;
   pb.Xout = Xout;
   pb.tol = tol;
   pb.maxit = maxit;

@@ -259,9 +259,9 @@ class SolveResult:
 def pcg_solve(op: KernelOperator, B: torch.Tensor, lambdas, nys: Nystrom | None = None, mu=None,
               adaptive: bool = True, tol: float = 1e-6, maxit: int = 1000, refine_every: int = 30,
               inner_mode: int = FAST, refine_mode: int = PLAIN, check_mode: int = PLAIN, history: bool = False,
-              stream=None):
+              x0: torch.Tensor | None = None, stream=None):
     """Block PCG for (K + lam_s I) x = B[:, j] over all shifts s and columns j
-    (column s * nrhs + j of the result)."""
+    (column s * nrhs + j of the result), from x0 (n x cols FP64) or 0."""
     vec = B.dim() == 1
     B2 = _dev_f32(B, "B")
     nrhs = B2.shape[1]
@@ -274,11 +274,15 @@ def pcg_solve(op: KernelOperator, B: torch.Tensor, lambdas, nys: Nystrom | None 
         mus = [float(mu)] * ns if not hasattr(mu, "__len__") else [float(x) for x in mu]
         mu_arr = (ctypes.c_double * ns)(*mus)
     X = torch.empty((op.n, cols), dtype=torch.float64, device=B2.device)
+    X0 = None
+    if x0 is not None:
+        X0 = x0.reshape(op.n, cols).to(device=B2.device, dtype=torch.float64).contiguous()
     iters = (ctypes.c_int32 * cols)()
     hist = (ctypes.c_double * ((maxit + 1) * cols))() if history else None
     tr = (ctypes.c_double * cols)()
     rc = check(_ffi.lib().pcg_solve(op.handle, nys.handle if nys is not None else None, lam_arr, ns, mu_arr,
-                                    int(bool(adaptive)), _ptr(B2), nrhs, float(tol), int(maxit), int(refine_every),
+                                    int(bool(adaptive)), _ptr(B2), nrhs, _ptr(X0) if X0 is not None else None,
+                                    float(tol), int(maxit), int(refine_every),
                                     int(inner_mode), int(refine_mode), int(check_mode), _ptr(X), iters, hist, tr,
                                     _stream(stream)), "pcg_solve")
     h = None
@@ -345,6 +349,42 @@ def solve_grad_points(op: KernelOperator, x: torch.Tensor, g: torch.Tensor, mode
     operator, for x = (K(X) + lam I)^{-1} b and the adjoint g = (K + lam I)^{-1} dL/dx
     (pcg_adjoint): dL/dX = -d(g^T K(X) x)/dX (kop_grad_points), n x d."""
     return -op.grad_points(g.reshape(-1).float(), x.reshape(-1).float(), mode=mode)
+
+
+class NysADMMLinearSolver:
+    """The linear solve inside NysADMM (ADMMConfig, App. A.4): the k-th call
+    solves (A + (rho + sigma) I) x = rhs (A the operator: X^T X or K) to the
+    relative tolerance max(tol_min, k^-gamma), warm-started from the previous
+    call's x, with one Nystrom preconditioner of A (damping rho + sigma)
+    rebuilt every `update_freq` calls from the test matrix Omega.  The paper
+    lists sigma, gamma and preconditioner_update_freq without the formulas;
+    the tolerance schedule above is this library's reading of gamma."""
+
+    def __init__(self, op: KernelOperator, Omega: torch.Tensor, update_freq: int = 20, sigma: float = 1e-6,
+                 gamma: float = 1.2, tol_min: float = 1e-8, maxit: int = 1000, nys_mode: int = FAST, **pcg_kw):
+        self.op, self.Omega = op, Omega
+        self.update_freq, self.sigma, self.gamma, self.tol_min, self.maxit = update_freq, sigma, gamma, tol_min, maxit
+        self.nys_mode, self.pcg_kw = nys_mode, pcg_kw
+        self.k = 0
+        self.builds = 0
+        self.nys = None
+        self.x = None
+        self.last = None
+
+    def solve(self, rhs: torch.Tensor, rho: float) -> torch.Tensor:
+        self.k += 1
+        if self.nys is None or (self.update_freq > 0 and (self.k - 1) % self.update_freq == 0):
+            if self.nys is not None:
+                self.nys.close()
+            self.nys = Nystrom(self.op, self.Omega, mode=self.nys_mode)
+            self.builds += 1
+        shift = float(rho) + self.sigma
+        tol = max(self.tol_min, float(self.k) ** -self.gamma)
+        res = pcg_solve(self.op, rhs, [shift], nys=self.nys, tol=tol, maxit=self.maxit,
+                        x0=self.x.reshape(-1, 1) if self.x is not None else None, **self.pcg_kw)
+        self.x = res.x.reshape(-1)
+        self.last = res
+        return self.x
 
 
 def krr_val_loss_and_grad(op: KernelOperator, nys: Nystrom | None, y: torch.Tensor, Xv: torch.Tensor,
