@@ -23,7 +23,12 @@ What it computes, and where the paper defines it:
   PCGStoppingCriteria);
 * the adjoint gradient of a validation loss through the solve (Sec. 3.2,
   Eq. "rlaopt-bilevel"; computed here by an adjoint solve instead of unrolled
-  backpropagation, which gives the same gradient at convergence).
+  backpropagation, which gives the same gradient at convergence), and the
+  gradient of a^T K(X) b with respect to the points X;
+* the ridge normal operator X^T X, the right-hand side X^T y and the closed-form
+  solution of the ridge data construction (Sec. 5.1, Eqs. "experiment-ridge"
+  and "experiment-ridge-data"), and the dense shifted solve of an ADMM
+  x-update (App. A.4).
 
 Parity status: every function here is pinned by tests/test_oracle_pins.py
 against closed forms, brute force, library direct solves, exact-recovery and

@@ -55,3 +55,14 @@ def test_adaptive_build_rejects_bad_arguments_without_gpu():
     assert lib.nys_build_adaptive(None, ctypes.c_void_p(16), 8, 4, 8, 10, 1e-2, ctypes.c_void_p(16), 0.0, 0,
                                   None, ctypes.byref(out), ctypes.byref(r), ctypes.byref(e), None, None, 0) == -1
     assert b"NULL" in lib.kop_last_error()
+
+
+def test_ridge_and_gradient_entry_points_reject_bad_arguments_without_gpu():
+    import ctypes
+    lib = _ffi.lib()
+    h = ctypes.c_void_p()
+    assert lib.kop_create_ridge(None, 10, 4, None, ctypes.byref(h)) == -1
+    assert lib.kop_create_ridge(ctypes.c_void_p(16), 0, 4, None, ctypes.byref(h)) == -1
+    assert lib.kop_create_ridge(ctypes.c_void_p(16), 10, 0, None, ctypes.byref(h)) == -1
+    assert lib.kop_grad_points(None, ctypes.c_void_p(16), ctypes.c_void_p(16), 0, ctypes.c_void_p(16), None) == -1
+    assert b"NULL" in lib.kop_last_error()
