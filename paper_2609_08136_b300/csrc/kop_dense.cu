@@ -299,31 +299,67 @@ KOP_DEV void ff_add_prod(float& s, float& e, float a, float b) {
   s = t;
 }
 
+// W[k][c] += sum_i U[i][k] V[i][c] (m <= MB columns).  A CTA of 256 threads
+// takes a block of rows and 512 columns (grid.y over the column chunks); each
+// thread owns the columns k = k0 + tid + 256 j, j < 2, and sweeps its rows RU
+// at a time with every load of the RU rows issued before the first update, so
+// that enough of U is in flight to run at the HBM rate.  The block's sums go
+// to W with FP64 atomics.
+template <int MB>
 __global__ void __launch_bounds__(256) utv_ff_kernel(const float* __restrict__ U, int ldu, int64_t n, int p,
                                                      const float* __restrict__ V, int m, int64_t rows_per_block,
                                                      double* __restrict__ W) {
+  constexpr int J = 2, RU = MB <= 2 ? 8 : 4;
   const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
   const int64_t r1 = r0 + rows_per_block < n ? r0 + rows_per_block : n;
-  for (int k = threadIdx.x; k < p; k += blockDim.x) {
-    float s[8], e[8];
+  int k[J];
+  bool act[J];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) s[c] = e[c] = 0.0f;
-#pragma unroll 4
-    for (int64_t i = r0; i < r1; ++i) {
-      const float u = U[i * ldu + k];
+  for (int j = 0; j < J; ++j) {
+    k[j] = (int)blockIdx.y * 512 + (int)threadIdx.x + 256 * j;
+    act[j] = k[j] < p;
+  }
+  float s[J][MB], e[J][MB];
 #pragma unroll
-      for (int c = 0; c < 8; ++c)
-        if (c < m) ff_add_prod(s[c], e[c], u, V[i * m + c]);
+  for (int j = 0; j < J; ++j)
+#pragma unroll
+    for (int c = 0; c < MB; ++c) s[j][c] = e[j][c] = 0.0f;
+  int64_t i = r0;
+  for (; i + RU <= r1; i += RU) {
+    float u[RU][J], v[RU][MB];
+#pragma unroll
+    for (int q = 0; q < RU; ++q) {
+#pragma unroll
+      for (int j = 0; j < J; ++j) u[q][j] = act[j] ? U[(i + q) * ldu + k[j]] : 0.0f;
+#pragma unroll
+      for (int c = 0; c < MB; ++c) v[q][c] = c < m ? __ldg(V + (i + q) * m + c) : 0.0f;
     }
 #pragma unroll
-    for (int c = 0; c < 8; ++c)
-      if (c < m) atomicAdd(&W[(int64_t)k * m + c], (double)s[c] + (double)e[c]);
+    for (int q = 0; q < RU; ++q)
+#pragma unroll
+      for (int j = 0; j < J; ++j)
+#pragma unroll
+        for (int c = 0; c < MB; ++c) ff_add_prod(s[j][c], e[j][c], u[q][j], v[q][c]);
   }
+  for (; i < r1; ++i) {
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const float u = act[j] ? U[i * ldu + k[j]] : 0.0f;
+#pragma unroll
+      for (int c = 0; c < MB; ++c) ff_add_prod(s[j][c], e[j][c], u, c < m ? __ldg(V + i * m + c) : 0.0f);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < J; ++j)
+#pragma unroll
+    for (int c = 0; c < MB; ++c)
+      if (act[j] && c < m) atomicAdd(&W[(int64_t)k[j] * m + c], (double)s[j][c] + (double)e[j][c]);
 }
 
 // O[i][c] = alpha[c] V[i][c] + sum_k U[i][k] W[k][c]; W is given as pairs
 // hi + lo of FP32 values (FP64 arithmetic is slow on this GPU, so the split is
-// made once per W, not once per row), one warp per row.
+// made once per W, not once per row), one warp per row.  General form, any p
+// and m <= 8.
 __global__ void __launch_bounds__(256) uw_ff_kernel(const float* __restrict__ U, int ldu, int64_t n, int p,
                                                     const float2* __restrict__ W, const float* __restrict__ V, int m,
                                                     const double* __restrict__ alpha, float* __restrict__ O) {
@@ -353,21 +389,135 @@ __global__ void __launch_bounds__(256) uw_ff_kernel(const float* __restrict__ U,
   }
 }
 
+// (s, e) += (s2, e2) for float-float values (TwoSum on the leading parts).
+KOP_DEV void ff_add_pair(float& s, float& e, float s2, float e2) {
+  const float t = s + s2;
+  const float bb = t - s;
+  e += ((s - (t - bb)) + (s2 - bb)) + e2;
+  s = t;
+}
+
+// The same product for p <= 512 and m <= MB <= 2, the shape of the PCG's
+// apply: persistent warps, each holding its 16 W pairs per column in
+// registers (lane owns k = lane + 32 t), take two rows per step with all 32
+// loads of U issued first; the cross-lane sum and the alpha V term are
+// float-float too, so no FP64 arithmetic runs per row.
+template <int MB>
+__global__ void __launch_bounds__(256) uw_ff_reg_kernel(const float* __restrict__ U, int ldu, int64_t n, int p,
+                                                        const float2* __restrict__ W, const float* __restrict__ V,
+                                                        int m, const double* __restrict__ alpha,
+                                                        float* __restrict__ O) {
+  constexpr int T = 16, RR = 2;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  float2 w[T][MB];
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    const int k = lane + 32 * t;
+#pragma unroll
+    for (int c = 0; c < MB; ++c) w[t][c] = (k < p && c < m) ? W[(int64_t)k * m + c] : make_float2(0.0f, 0.0f);
+  }
+  float ah[MB], al[MB];
+#pragma unroll
+  for (int c = 0; c < MB; ++c) {
+    const double a = c < m ? alpha[c] : 0.0;
+    ah[c] = (float)a;
+    al[c] = (float)(a - (double)ah[c]);
+  }
+  for (int64_t row0 = warp * RR; row0 < n; row0 += nwarps * RR) {
+    float u[RR][T];
+#pragma unroll
+    for (int q = 0; q < RR; ++q) {
+      const int64_t row = row0 + q;
+#pragma unroll
+      for (int t = 0; t < T; ++t) {
+        const int k = lane + 32 * t;
+        u[q][t] = (row < n && k < p) ? U[row * ldu + k] : 0.0f;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < RR; ++q) {
+      const int64_t row = row0 + q;
+#pragma unroll
+      for (int c = 0; c < MB; ++c) {
+        float s = 0.0f, e = 0.0f;
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+          ff_add_prod(s, e, u[q][t], w[t][c].x);
+          e = fmaf(u[q][t], w[t][c].y, e);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          const float s2 = __shfl_xor_sync(0xffffffffu, s, off);
+          const float e2 = __shfl_xor_sync(0xffffffffu, e, off);
+          ff_add_pair(s, e, s2, e2);
+        }
+        if (lane == c && c < m && row < n) {
+          const float v = V[row * m + c];
+          const float pr = ah[c] * v;
+          const float pe = fmaf(ah[c], v, -pr) + al[c] * v;
+          ff_add_pair(s, e, pr, pe);
+          O[row * m + c] = s + e;
+        }
+      }
+    }
+  }
+}
+
+// Resident 256-thread CTAs per SM of a kernel (queried once per instance).
+template <typename Kern>
+static int ctas_per_sm(Kern kern) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, 256, 0) != cudaSuccess || nb < 1) nb = 1;
+  return nb;
+}
+
+template <int MB>
+static void utv_ff_launch(const float* U, int ldu, int64_t n, int p, const float* V, int m, double* W,
+                          cudaStream_t st) {
+  static const int occ = ctas_per_sm(utv_ff_kernel<MB>);
+  const int chunks = (p + 511) / 512;
+  int64_t rblocks = ((int64_t)occ * num_sms() + chunks - 1) / chunks;
+  int64_t rpb = (n + rblocks - 1) / rblocks;
+  if (rpb < 16) rpb = 16;
+  rblocks = (n + rpb - 1) / rpb;
+  utv_ff_kernel<MB><<<dim3((unsigned)rblocks, (unsigned)chunks), 256, 0, st>>>(U, ldu, n, p, V, m, rpb, W);
+}
+
 int utv_ff(const float* U, int ldu, int64_t n, int p, const float* V, int m, double* W, cudaStream_t st) {
+  if (m < 1 || m > 8) return fail(KOP_EINVAL, "utv_ff: m must be in [1, 8]");
   KOP_CUDA_TRY(cudaMemsetAsync(W, 0, sizeof(double) * (size_t)p * m, st));
-  int64_t blocks = 8 * num_sms();
-  int64_t rpb = (n + blocks - 1) / blocks;
-  if (rpb < 32) rpb = 32;
-  blocks = (n + rpb - 1) / rpb;
-  utv_ff_kernel<<<(unsigned)blocks, 256, 0, st>>>(U, ldu, n, p, V, m, rpb, W);
+  if (m == 1) utv_ff_launch<1>(U, ldu, n, p, V, m, W, st);
+  else if (m == 2) utv_ff_launch<2>(U, ldu, n, p, V, m, W, st);
+  else if (m <= 4) utv_ff_launch<4>(U, ldu, n, p, V, m, W, st);
+  else utv_ff_launch<8>(U, ldu, n, p, V, m, W, st);
   KOP_LAUNCHED();
   return KOP_OK;
 }
 
+template <int MB>
+static void uw_ff_reg_launch(const float* U, int ldu, int64_t n, int p, const float2* W, const float* V, int m,
+                             const double* alpha, float* O, cudaStream_t st) {
+  static const int occ = ctas_per_sm(uw_ff_reg_kernel<MB>);
+  // one wave of persistent CTAs, but no more warps than row pairs
+  int64_t blocks = (int64_t)occ * num_sms();
+  const int64_t need = (n + 15) / 16;  // 8 warps x 2 rows per CTA
+  if (blocks > need) blocks = need;
+  uw_ff_reg_kernel<MB><<<(unsigned)blocks, 256, 0, st>>>(U, ldu, n, p, W, V, m, alpha, O);
+}
+
 int uw_ff(const float* U, int ldu, int64_t n, int p, const float2* W, const float* V, int m, const double* alpha,
           float* O, cudaStream_t st) {
-  const int64_t threads = n * 32;
-  uw_ff_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(U, ldu, n, p, W, V, m, alpha, O);
+  if (m < 1 || m > 8) return fail(KOP_EINVAL, "uw_ff: m must be in [1, 8]");
+  if (p <= 512 && m == 1) {
+    uw_ff_reg_launch<1>(U, ldu, n, p, W, V, m, alpha, O, st);
+  } else if (p <= 512 && m == 2) {
+    uw_ff_reg_launch<2>(U, ldu, n, p, W, V, m, alpha, O, st);
+  } else {
+    const int64_t threads = n * 32;
+    uw_ff_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(U, ldu, n, p, W, V, m, alpha, O);
+  }
   KOP_LAUNCHED();
   return KOP_OK;
 }
