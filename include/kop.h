@@ -119,6 +119,31 @@ int kop_destroy(kop_t op);
 /* Change the bandwidth in place (the points are kept). */
 int kop_set_bandwidth(kop_t op, double bandwidth);
 
+/* Keep the kernel matrix of the solver's checks in device memory: n rows of
+ * ld = ceil(n / 128) * 128 FP32 (n^2 * 4 bytes, 160 GB at n = 200000).
+ * While it is set, the first product of a pcg_solve / pcg_adjoint call with
+ * the check operator KOP_PLAIN_CHECK (refine_mode or check_mode KOP_PLAIN)
+ * computes K(X, X) by direct differences as that operator does and stores
+ * it, and the call's later check products multiply the stored matrix with
+ * the same error-free contraction: about the cost of streaming it once,
+ * instead of recomputing n^2 distances.  The stored values serve that one
+ * call only; every call recomputes them.  Results equal those without the
+ * matrix up to the order of the compensated sums.
+ *   enable = 0: stop using it; memory the library reserved is freed (the
+ *               device is synchronized first).
+ *   enable != 0, buffer = NULL: the library reserves the matrix (kept until
+ *               disabled or kop_destroy); KOP_ENOMEM, reserving nothing, when
+ *               it and 4 GB of headroom do not fit in the free device memory.
+ *   enable != 0, buffer != NULL: the caller's device memory of buffer_floats
+ *               >= n * ld floats, 16-byte aligned (KOP_EINVAL otherwise); the
+ *               caller keeps ownership and may free it once the solves that
+ *               used it have completed on their streams.
+ * Solves on one handle that overlap in time share the matrix: run them one
+ * after another while it is set.  KOP_EINVAL for ridge operators.  Not in the
+ * paper: a trade of HBM capacity for the check's distance work that a B300's
+ * 270 GB makes possible.                                                    */
+int kop_set_check_cache(kop_t op, int32_t enable, float* buffer, int64_t buffer_floats);
+
 /* O (n x m) = K(X, X) V for V (n x m).  mode: enum kop_mode.  Asynchronous;
  * the device status of the operator is read by kop_sync(). */
 int kop_matvec(kop_t op, const float* V, int32_t m, float* O, int32_t mode, void* stream);

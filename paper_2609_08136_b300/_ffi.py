@@ -22,6 +22,7 @@ SIGNATURES = {
     "kop_create": (c_int, [c_vp, c_i64, c_i32, c_i32, c_dbl, c_vp, P(c_vp)]),
     "kop_destroy": (c_int, [c_vp]),
     "kop_set_bandwidth": (c_int, [c_vp, c_dbl]),
+    "kop_set_check_cache": (c_int, [c_vp, c_i32, c_vp, c_i64]),
     "kop_matvec": (c_int, [c_vp, c_vp, c_i32, c_vp, c_i32, c_vp]),
     "kop_cross_matvec": (c_int, [c_vp, c_vp, c_i64, c_vp, c_i32, c_vp, c_i32, c_i32, c_i32, c_vp]),
     "kop_dbw_matvec": (c_int, [c_vp, c_vp, c_i32, c_vp, c_i32, c_vp]),

@@ -92,6 +92,7 @@ extern "C" int kop_destroy(kop_t op) {
     return KOP_OK;
   }
   pointset_free(op->pts, 0);
+  if (op->kc_owned) cudaFree(op->kc);
   cudaFree(op->mean);
   cudaDeviceSynchronize();
   delete op;
@@ -103,6 +104,38 @@ extern "C" int kop_set_bandwidth(kop_t op, double bandwidth) {
   if (int rc = need_kernel(op, "kop_set_bandwidth")) return rc;
   if (!(bandwidth > 0.0) || !std::isfinite(bandwidth)) return fail(KOP_EINVAL, "kop_set_bandwidth: bandwidth must be > 0");
   op->bw = bandwidth;
+  return KOP_OK;
+}
+
+static int check_cache_release(kop_s* op) {
+  if (op->kc && op->kc_owned) {
+    KOP_CUDA_TRY(cudaDeviceSynchronize());
+    KOP_CUDA_TRY(cudaFree(op->kc));
+  }
+  op->kc = nullptr;
+  op->kc_ld = 0;
+  op->kc_owned = 0;
+  return KOP_OK;
+}
+
+extern "C" int kop_set_check_cache(kop_t op, int32_t enable, float* buffer, int64_t buffer_floats) {
+  if (!op) return fail(KOP_EINVAL, "kop_set_check_cache: NULL handle");
+  if (int rc = need_kernel(op, "kop_set_check_cache")) return rc;
+  if (!enable) return check_cache_release(op);
+  if (!buffer) {
+    if (op->kc_owned) return KOP_OK;
+    if (int rc = check_cache_release(op)) return rc;
+    return check_cache_reserve(op);
+  }
+  const int64_t ld = check_cache_ld(op->pts.n);
+  if (buffer_floats < op->pts.n * ld)
+    return fail(KOP_EINVAL, "kop_set_check_cache: buffer smaller than n * ceil(n / 128) * 128 floats");
+  if (reinterpret_cast<uintptr_t>(buffer) % 16 != 0)
+    return fail(KOP_EINVAL, "kop_set_check_cache: buffer not 16-byte aligned");
+  if (int rc = check_cache_release(op)) return rc;
+  op->kc = buffer;
+  op->kc_ld = ld;
+  op->kc_owned = 0;
   return KOP_OK;
 }
 

@@ -122,6 +122,11 @@ struct kop_s {
   float* rX = nullptr;  // device n x p copy of X
   int64_t rn = 0;       // rows of X
   int rp = 0;           // columns of X: the operator's dimension
+  // the stored direct-difference kernel matrix of the solver's checks
+  // (kop_set_check_cache): n x kc_ld FP32, or NULL
+  float* kc = nullptr;
+  int64_t kc_ld = 0;
+  int kc_owned = 0;  // kc was allocated by the library (else the caller's)
 };
 
 namespace kop {
@@ -135,6 +140,14 @@ int op_apply(kop_s* op, int mode, const float* V, int m, int ldv, float* O, int 
 int op_apply_f64(kop_s* op, const double* V, int m, int ldv, double* O, int ldo, cudaStream_t st);
 int ridge_apply(const kop_s* op, int mode, const float* V, int m, int ldv, float* O, int ldo, cudaStream_t st);
 int ridge_apply_f64(const kop_s* op, const double* V, int m, int ldv, double* O, int ldo, cudaStream_t st);
+// Row pitch (floats) of the stored kernel matrix of an n-point operator.
+inline int64_t check_cache_ld(int64_t n) { return (n + 127) / 128 * 128; }
+// Reserve op->kc for the kernel matrix (KOP_ENOMEM when it does not fit).
+int check_cache_reserve(kop_s* op);
+// The compensated direct-difference product (KOP_PLAIN_CHECK) of a kernel
+// operator with op->kc set: build = true computes it by direct differences
+// and stores K in op->kc; build = false multiplies the stored K.
+int check_matvec_cached(kop_s* op, bool build, const float* V, int m, int ldv, float* O, int ldo, cudaStream_t st);
 }  // namespace kop
 
 // Stream-ordered device scratch, freed on the same stream when it goes out of scope.

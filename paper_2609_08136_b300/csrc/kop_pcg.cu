@@ -346,6 +346,16 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
   auto matvec2 = [&](const float* V, float* O, int mode) -> int {
     return op_apply(op, mode, V, 2 * cols, 2 * cols, O, 2 * cols, st);
   };
+  // check products: with the kernel matrix set in HBM, the first one of this
+  // solve stores K and later ones multiply the stored K (its contents are
+  // never reused across solves)
+  bool kc_built = false;
+  auto check2 = [&](int mode) -> int {
+    if (mode != KOP_PLAIN_CHECK || op->ridge || !op->kc) return matvec2(V2, T, mode);
+    const int rc2 = check_matvec_cached(op, !kc_built, V2, 2 * cols, 2 * cols, T, 2 * cols, st);
+    if (rc2 == KOP_OK) kc_built = true;
+    return rc2;
+  };
 
   // x0 = 0, r0 = b, ||b|| per column
   if ((rc = vec_launch<OP_INIT>(va, st))) return rc;
@@ -378,7 +388,7 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
       if ((rc = vec_launch<OP_RES64>(va, st))) return rc;
     } else {
       if ((rc = vec_launch<OP_SPLIT>(va, st))) return rc;
-      if ((rc = matvec2(V2, T, rmode))) return rc;
+      if ((rc = check2(rmode))) return rc;
       if ((rc = vec_launch<OP_RES>(va, st))) return rc;
     }
     KOP_CUDA_TRY(cudaMemcpyAsync(hr0.data(), acc, sizeof(double) * cols, cudaMemcpyDeviceToHost, st));
@@ -450,7 +460,7 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
         if ((rc = vec_launch<OP_RES64>(va, st))) return rc;
       } else {
         if ((rc = vec_launch<OP_SPLIT>(va, st))) return rc;
-        if ((rc = matvec2(V2, T, rmode))) return rc;
+        if ((rc = check2(rmode))) return rc;
         if ((rc = vec_launch<OP_RES>(va, st))) return rc;
       }
       KOP_CUDA_TRY(cudaMemcpyAsync(hr.data(), acc, sizeof(double) * cols, cudaMemcpyDeviceToHost, st));

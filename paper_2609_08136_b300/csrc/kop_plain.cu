@@ -63,10 +63,14 @@ KOP_DEV float plain_kernel_value(float d2, const PlainConst& p) {
   }
 }
 
+// Kst != NULL: the column block 0 also stores every kernel value it computes,
+// Kst[i * ldk + j] for the rows i < nq and all keys of its tiles (0 for the
+// padding keys j >= nk); ldk a multiple of 4.
 template <int KF, int MV, bool COMP>
 __global__ void __launch_bounds__(K2_ROWS) k2_plain_kernel(const float* __restrict__ Q, const float* __restrict__ Xk,
                                                            const float* __restrict__ V, float* __restrict__ O, int nq,
-                                                           int nk, int dp, int m, int ldv, int ldo, PlainConst pc) {
+                                                           int nk, int dp, int m, int ldv, int ldo, PlainConst pc,
+                                                           float* __restrict__ Kst, int64_t ldk) {
   extern __shared__ float sm[];
   float* Qs = sm;                              // dp x (K2_ROWS + 1), transposed
   float* Xs = Qs + dp * (K2_ROWS + 1);         // K2_KEYS x dp
@@ -75,6 +79,8 @@ __global__ void __launch_bounds__(K2_ROWS) k2_plain_kernel(const float* __restri
   const int row0 = blockIdx.x * K2_ROWS;
   const int col0 = blockIdx.y * MV;
   const int mc = (m - col0) < MV ? (m - col0) : MV;
+  const int gi = row0 + tid;
+  float* const krow = (Kst != nullptr && blockIdx.y == 0 && gi < nq) ? Kst + (int64_t)gi * ldk : nullptr;
   for (int idx = tid; idx < K2_ROWS * dp; idx += K2_ROWS) {
     const int r = idx / dp, k = idx - r * dp;
     Qs[k * (K2_ROWS + 1) + r] = Q[(int64_t)(row0 + r) * dp + k];
@@ -120,9 +126,21 @@ __global__ void __launch_bounds__(K2_ROWS) k2_plain_kernel(const float* __restri
     float part[MV], perr[MV];
 #pragma unroll
     for (int c = 0; c < MV; ++c) part[c] = perr[c] = 0.0f;
+    // kernel values in place of the distances
+#pragma unroll
+    for (int jj = 0; jj < K2_KEYS; ++jj) d2[jj] = plain_kernel_value<KF>(d2[jj], pc);
+    if (krow != nullptr) {
+#pragma unroll
+      for (int j4 = 0; j4 < K2_KEYS; j4 += 4) {
+        const int j = j0 + j4;
+        *reinterpret_cast<float4*>(krow + j) =
+            make_float4(j + 0 < nk ? d2[j4 + 0] : 0.0f, j + 1 < nk ? d2[j4 + 1] : 0.0f,
+                        j + 2 < nk ? d2[j4 + 2] : 0.0f, j + 3 < nk ? d2[j4 + 3] : 0.0f);
+      }
+    }
 #pragma unroll
     for (int jj = 0; jj < K2_KEYS; ++jj) {
-      const float kv = plain_kernel_value<KF>(d2[jj], pc);
+      const float kv = d2[jj];
 #pragma unroll
       for (int c = 0; c < MV; ++c) {
         const float v = Vs[jj * MV + c];
@@ -144,7 +162,6 @@ __global__ void __launch_bounds__(K2_ROWS) k2_plain_kernel(const float* __restri
       acc_e[c] += perr[c];
     }
   }
-  const int gi = row0 + tid;
   if (gi < nq) {
 #pragma unroll
     for (int c = 0; c < MV; ++c)
@@ -175,7 +192,7 @@ static PlainConst plain_constants(int kf, double bw) {
 
 template <int KF, int MV, bool COMP>
 static int launch_plain_t(const PointSet& Q, const PointSet& Ks, const float* V, int m, int ldv, float* O, int ldo,
-                          const PlainConst& pc, cudaStream_t st) {
+                          const PlainConst& pc, cudaStream_t st, float* Kst, int64_t ldk) {
   auto kern = k2_plain_kernel<KF, MV, COMP>;
   const int dp = Q.dp;
   const size_t smem = sizeof(float) * ((size_t)dp * (K2_ROWS + 1) + (size_t)K2_KEYS * dp + K2_KEYS * MV);
@@ -185,30 +202,30 @@ static int launch_plain_t(const PointSet& Q, const PointSet& Ks, const float* V,
     attr_set = true;
   }
   dim3 grid((unsigned)((Q.n + K2_ROWS - 1) / K2_ROWS), (unsigned)((m + MV - 1) / MV));
-  kern<<<grid, K2_ROWS, smem, st>>>(Q.xc, Ks.xc, V, O, (int)Q.n, (int)Ks.n, dp, m, ldv, ldo, pc);
+  kern<<<grid, K2_ROWS, smem, st>>>(Q.xc, Ks.xc, V, O, (int)Q.n, (int)Ks.n, dp, m, ldv, ldo, pc, Kst, ldk);
   KOP_LAUNCHED();
   return KOP_OK;
 }
 
 template <int KF, bool COMP>
 static int launch_plain_kf(const PointSet& Q, const PointSet& Ks, const float* V, int m, int ldv, float* O, int ldo,
-                           const PlainConst& pc, cudaStream_t st) {
-  if (m == 1) return launch_plain_t<KF, 1, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st);
-  if (m == 2) return launch_plain_t<KF, 2, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st);
-  if (m <= 4) return launch_plain_t<KF, 4, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st);
-  return launch_plain_t<KF, 8, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st);
+                           const PlainConst& pc, cudaStream_t st, float* Kst, int64_t ldk) {
+  if (m == 1) return launch_plain_t<KF, 1, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st, Kst, ldk);
+  if (m == 2) return launch_plain_t<KF, 2, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st, Kst, ldk);
+  if (m <= 4) return launch_plain_t<KF, 4, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st, Kst, ldk);
+  return launch_plain_t<KF, 8, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st, Kst, ldk);
 }
 
 template <bool COMP>
 static int plain_dispatch(int kf, const PointSet& Q, const PointSet& Ks, const float* V, int m, int ldv, float* O,
-                          int ldo, const PlainConst& pc, cudaStream_t st) {
+                          int ldo, const PlainConst& pc, cudaStream_t st, float* Kst = nullptr, int64_t ldk = 0) {
   switch (kf) {
-    case KF_RBF: return launch_plain_kf<KF_RBF, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st);
-    case KF_LAPLACE: return launch_plain_kf<KF_LAPLACE, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st);
-    case KF_MATERN: return launch_plain_kf<KF_MATERN, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st);
-    case KF_DRBF: return launch_plain_kf<KF_DRBF, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st);
-    case KF_DLAPLACE: return launch_plain_kf<KF_DLAPLACE, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st);
-    default: return launch_plain_kf<KF_DMATERN, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st);
+    case KF_RBF: return launch_plain_kf<KF_RBF, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st, Kst, ldk);
+    case KF_LAPLACE: return launch_plain_kf<KF_LAPLACE, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st, Kst, ldk);
+    case KF_MATERN: return launch_plain_kf<KF_MATERN, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st, Kst, ldk);
+    case KF_DRBF: return launch_plain_kf<KF_DRBF, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st, Kst, ldk);
+    case KF_DLAPLACE: return launch_plain_kf<KF_DLAPLACE, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st, Kst, ldk);
+    default: return launch_plain_kf<KF_DMATERN, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st, Kst, ldk);
   }
 }
 
@@ -218,6 +235,130 @@ int plain_matvec(const PointSet& Q, const PointSet& Ks, bool /*self*/, int kf, c
   const PlainConst pc = plain_constants(kf, kc.bw);
   return compensated ? plain_dispatch<true>(kf, Q, Ks, V, m, ldv, O, ldo, pc, st)
                      : plain_dispatch<false>(kf, Q, Ks, V, m, ldv, O, ldo, pc, st);
+}
+
+// ---------------------------------------------------------------------------
+// The check operator with the kernel matrix kept in HBM.  K(X, X) in FP32 is
+// n^2 * 4 bytes (160 GB at n = 200000, which a B300 holds).  The first check
+// product of a solve computes it by direct differences as above and stores
+// it; later check products of the same solve stream the stored matrix with
+// the same error-free contraction instead of recomputing the distances.
+
+// O[i][c0 + c] = sum_{j < nk} Kc[i][j] V[j][c0 + c], TwoProduct + TwoSum per
+// entry as in the direct kernel.  A warp takes RW rows (8; 4 for 8 columns);
+// lane l reads the float4 of keys j = jb + 4 l of each row and the V rows of
+// those 4 keys once for the RW rows.  Keys j >= nk (the tail of a row up to
+// ldk) count as 0.
+template <int MV>
+__global__ void __launch_bounds__(256) kcache_gemv_kernel(const float* __restrict__ Kc, int64_t ldk, int nq, int nk,
+                                                          const float* __restrict__ V, int m, int ldv,
+                                                          float* __restrict__ O, int ldo) {
+  constexpr int RW = MV <= 4 ? 8 : 4;
+  const int lane = threadIdx.x & 31;
+  const int64_t i0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * RW;
+  if (i0 >= nq) return;  // warp-uniform
+  const int nr = nq - i0 < RW ? (int)(nq - i0) : RW;
+  const int c0 = blockIdx.y * MV;
+  const int mc = m - c0 < MV ? m - c0 : MV;
+  float s[RW][MV], e[RW][MV];
+#pragma unroll
+  for (int r = 0; r < RW; ++r)
+#pragma unroll
+    for (int c = 0; c < MV; ++c) s[r][c] = e[r][c] = 0.0f;
+  for (int jb = 0; jb < nk; jb += 128) {
+    const int j = jb + 4 * lane;
+    float v[4][MV];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int c = 0; c < MV; ++c) v[q][c] = (j + q < nk && c < mc) ? __ldg(V + (int64_t)(j + q) * ldv + c0 + c) : 0.0f;
+    float4 k[RW];
+#pragma unroll
+    for (int r = 0; r < RW; ++r)
+      k[r] = r < nr ? *reinterpret_cast<const float4*>(Kc + (i0 + r) * ldk + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+    if (jb + 128 > nk) {  // the last block of keys: entries past nk are not data
+#pragma unroll
+      for (int r = 0; r < RW; ++r) {
+        if (j + 0 >= nk) k[r].x = 0.0f;
+        if (j + 1 >= nk) k[r].y = 0.0f;
+        if (j + 2 >= nk) k[r].z = 0.0f;
+        if (j + 3 >= nk) k[r].w = 0.0f;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < RW; ++r) {
+      const float kr[4] = {k[r].x, k[r].y, k[r].z, k[r].w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int c = 0; c < MV; ++c) {
+          const float p = kr[q] * v[q][c];
+          const float pe = fmaf(kr[q], v[q][c], -p);
+          const float t = s[r][c] + p;
+          const float bb = t - s[r][c];
+          e[r][c] += ((s[r][c] - (t - bb)) + (p - bb)) + pe;
+          s[r][c] = t;
+        }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < RW; ++r)
+#pragma unroll
+    for (int c = 0; c < MV; ++c) {
+      float a = s[r][c], b = e[r][c];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const float a2 = __shfl_xor_sync(0xffffffffu, a, off);
+        const float b2 = __shfl_xor_sync(0xffffffffu, b, off);
+        const float t = a + a2;
+        const float bb = t - a;
+        b += ((a - (t - bb)) + (a2 - bb)) + b2;
+        a = t;
+      }
+      if (lane == 0 && r < nr && c < mc) O[(i0 + r) * ldo + c0 + c] = a + b;
+    }
+}
+
+template <int MV>
+static void kcache_launch(const float* Kc, int64_t ldk, int nq, int nk, const float* V, int m, int ldv, float* O,
+                          int ldo, cudaStream_t st) {
+  constexpr int rows_per_cta = 8 * (MV <= 4 ? 8 : 4);
+  const dim3 grid((unsigned)((nq + rows_per_cta - 1) / rows_per_cta), (unsigned)((m + MV - 1) / MV));
+  kcache_gemv_kernel<MV><<<grid, 256, 0, st>>>(Kc, ldk, nq, nk, V, m, ldv, O, ldo);
+}
+
+int check_cache_reserve(kop_s* op) {
+  if (op->kc) return KOP_OK;
+  const int64_t n = op->pts.n;
+  const int64_t ld = check_cache_ld(n);
+  const size_t bytes = sizeof(float) * (size_t)n * (size_t)ld;
+  size_t fr = 0, tot = 0;
+  KOP_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
+  // keep 4 GB for the solver's own buffers and the caller's
+  if (fr < bytes + (size_t(4) << 30)) return fail(KOP_ENOMEM, "kop_set_check_cache: not enough free device memory");
+  const cudaError_t e = cudaMalloc(&op->kc, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    op->kc = nullptr;
+    return fail(KOP_ENOMEM, "kop_set_check_cache: cudaMalloc failed");
+  }
+  op->kc_ld = ld;
+  op->kc_owned = 1;
+  return KOP_OK;
+}
+
+int check_matvec_cached(kop_s* op, bool build, const float* V, int m, int ldv, float* O, int ldo, cudaStream_t st) {
+  const int n = (int)op->pts.n;
+  if (build) {
+    const PlainConst pc = plain_constants(op->kernel, op->bw);
+    return plain_dispatch<true>(op->kernel, op->pts, op->pts, V, m, ldv, O, ldo, pc, st, op->kc, op->kc_ld);
+  }
+  if (m == 1) kcache_launch<1>(op->kc, op->kc_ld, n, n, V, m, ldv, O, ldo, st);
+  else if (m == 2) kcache_launch<2>(op->kc, op->kc_ld, n, n, V, m, ldv, O, ldo, st);
+  else if (m <= 4) kcache_launch<4>(op->kc, op->kc_ld, n, n, V, m, ldv, O, ldo, st);
+  else kcache_launch<8>(op->kc, op->kc_ld, n, n, V, m, ldv, O, ldo, st);
+  KOP_LAUNCHED();
+  return KOP_OK;
 }
 
 }  // namespace kop

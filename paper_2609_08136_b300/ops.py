@@ -80,6 +80,24 @@ class KernelOperator:
         check(_ffi.lib().kop_set_bandwidth(self._h, float(bw)), "kop_set_bandwidth")
         self.bandwidth = float(bw)
 
+    def check_cache_floats(self) -> int:
+        """Floats of the stored check matrix: n rows padded to 128 columns."""
+        return self.n * ((self.n + 127) // 128 * 128)
+
+    def set_check_cache(self, enable: bool = True, buffer: torch.Tensor | None = None):
+        """Keep the kernel matrix of the solver's direct-difference checks in
+        device memory (kop_set_check_cache): in `buffer` (a CUDA float32
+        tensor of at least check_cache_floats() elements, which must outlive
+        its use), else reserved by the library.  Raises KopError (KOP_ENOMEM)
+        when the library's reservation does not fit."""
+        ptr, size = None, 0
+        if enable and buffer is not None:
+            if buffer.dtype != torch.float32 or not buffer.is_cuda or not buffer.is_contiguous():
+                raise TypeError("buffer must be a contiguous CUDA float32 tensor")
+            ptr, size = _ptr(buffer), buffer.numel()
+        self._check_buffer = buffer if enable else None
+        check(_ffi.lib().kop_set_check_cache(self._h, int(bool(enable)), ptr, size), "kop_set_check_cache")
+
     def matvec(self, V: torch.Tensor, mode: int = FAST, out: torch.Tensor | None = None, stream=None):
         vec = V.dim() == 1
         V2 = _dev_f32(V, "V")

@@ -66,3 +66,9 @@ def test_ridge_and_gradient_entry_points_reject_bad_arguments_without_gpu():
     assert lib.kop_create_ridge(ctypes.c_void_p(16), 10, 0, None, ctypes.byref(h)) == -1
     assert lib.kop_grad_points(None, ctypes.c_void_p(16), ctypes.c_void_p(16), 0, ctypes.c_void_p(16), None) == -1
     assert b"NULL" in lib.kop_last_error()
+
+
+def test_check_cache_rejects_null_handle_without_gpu():
+    lib = _ffi.lib()
+    assert lib.kop_set_check_cache(None, 1, None, 0) == -1
+    assert b"NULL" in lib.kop_last_error()

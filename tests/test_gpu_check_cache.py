@@ -1,0 +1,147 @@
+"""Solves with the kernel matrix of the checks kept in device memory
+(kop_set_check_cache) against the same solves without it.  The first check
+product of a solve stores K(X, X) as the direct-difference operator computes
+it; later checks of that solve multiply the stored matrix with the same
+error-free contraction.  So the solver takes the same decisions, its outputs
+agree up to the order of the compensated sums, and the true residual it
+reports matches the oracle's FP64 residual of the returned iterate to within
+the FP32 entry error of the check operator."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import kop_oracle as O
+from paper_2609_08136_b300 import ops
+from paper_2609_08136_b300 import workloads as W
+from paper_2609_08136_b300._ffi import KopError
+
+pytestmark = pytest.mark.gpu
+
+_KIND = {ops.RBF: O.RBF, ops.LAPLACE: O.LAPLACE, ops.MATERN52: O.MATERN52}
+
+
+def _solve(op, B, lams, ny, cache, **kw):
+    if cache == "library":
+        op.set_check_cache(True)
+    elif cache == "buffer":
+        # caller-owned memory, one float past the end to spare
+        op.set_check_cache(True, torch.empty(op.check_cache_floats() + 1, device="cuda"))
+    try:
+        return ops.pcg_solve(op, torch.from_numpy(B).cuda(), lams, nys=ny, **kw)
+    finally:
+        op.set_check_cache(False)
+
+
+# n ragged against the 32-key tiles, the 128-column padding of the stored
+# rows and the 8-row warps of the stored product; 2 x cols = 2, 6 and 10
+# columns cover one, one and two column blocks
+@pytest.mark.parametrize("kind,n,nrhs,lams", [
+    (ops.LAPLACE, 3001, 1, [1e-3]),
+    (ops.RBF, 2000, 3, [1e-3]),
+    (ops.MATERN52, 1500, 1, [1e-3, 3e-3, 1e-2, 3e-2, 1e-1]),
+    (ops.LAPLACE, 37, 2, [1e-2]),
+])
+def test_cached_checks_match_direct_checks(kind, n, nrhs, lams):
+    d = 8
+    X = W.random_points(n, d, seed=n)
+    bw = 2.0 * np.sqrt(d)
+    B = W.random_block(n, nrhs, seed=n + 1)
+    lam_abs = [l * n for l in lams]
+    op = ops.KernelOperator(torch.from_numpy(X).cuda(), kind, bw)
+    r = min(64, n)
+    ny = ops.Nystrom(op, torch.from_numpy(W.gaussian_sketch(n, r, seed=n)).cuda())
+    # refinement every 5 iterations: many check products per solve
+    kw = dict(tol=5e-7, maxit=400, refine_every=5)
+    a = _solve(op, B, lam_abs, ny, None, **kw)
+    b = _solve(op, B, lam_abs, ny, "library", **kw)
+    c = _solve(op, B, lam_abs, ny, "buffer", **kw)
+    assert a.converged and b.converged and c.converged
+    assert a.iters == b.iters == c.iters
+    xa, xb, xc = a.x.cpu().numpy(), b.x.cpu().numpy(), c.x.cpu().numpy()
+    assert np.max(np.abs(xa - xb)) <= 1e-6 * np.max(np.abs(xa))
+    assert np.max(np.abs(xc - xb)) <= 1e-6 * np.max(np.abs(xa))
+    # the check's output K x is rounded to FP32: the two contraction orders can
+    # round an element to neighbouring floats, moving the relative residual by
+    # about 2^-24 |(K x)_i| / ||b|| per such element (~1e-9 here)
+    np.testing.assert_allclose(b.true_relres, a.true_relres, rtol=1e-4, atol=1e-8)
+    np.testing.assert_allclose(c.true_relres, a.true_relres, rtol=1e-4, atol=1e-8)
+    # the reported true residuals against the oracle's FP64 residuals: they
+    # differ by the check operator's FP32 entry errors (direct-difference
+    # distance, square root and exp: below 4e-6 of each entry here), rounding
+    # errors of different entries, which add up in quadrature:
+    # ||dr|| ~ 4e-6 || sqrt((K o K)(x o x)) ||.  (An FP32 emulation of the
+    # check's entries puts its error 55-90x below this bound in every case
+    # here; at lam = 1e-3 n it reaches 1.3e-6 for the Matern kernel, so the
+    # FP64 residual of an accepted iterate may exceed the tolerance there.)
+    K = O.kernel_matrix(_KIND[kind], X, X, bw)
+    xb2 = xb.reshape(n, -1)
+    for col in range(xb2.shape[1]):
+        bc = B[:, col % nrhs].astype(np.float64)
+        lam = lam_abs[col // nrhs]
+        nb = np.linalg.norm(bc)
+        rr = np.linalg.norm(K @ xb2[:, col] + lam * xb2[:, col] - bc) / nb
+        bound = 4e-6 * np.linalg.norm(np.sqrt((K * K) @ (xb2[:, col] ** 2))) / nb
+        assert abs(b.true_relres[col] - rr) <= bound, (col, b.true_relres[col], rr, bound)
+
+
+def test_cached_checks_in_the_adjoint():
+    n, d = 2500, 8
+    X = W.random_points(n, d, seed=3)
+    bw = 2.0 * np.sqrt(d)
+    lam = 1e-3 * n
+    op = ops.KernelOperator(torch.from_numpy(X).cuda(), ops.RBF, bw)
+    ny = ops.Nystrom(op, torch.from_numpy(W.gaussian_sketch(n, 64, seed=3)).cuda())
+    x = torch.from_numpy(W.random_block(n, 1, seed=4)[:, 0].astype(np.float64)).cuda()
+    dl = torch.from_numpy(W.random_block(n, 1, seed=5)[:, 0].astype(np.float64)).cuda()
+    kw = dict(tol=5e-7, maxit=400, refine_every=5)
+    g0, dlam0, dbw0, it0 = ops.pcg_adjoint(op, x, dl, lam, nys=ny, **kw)
+    op.set_check_cache(True)
+    try:
+        g1, dlam1, dbw1, it1 = ops.pcg_adjoint(op, x, dl, lam, nys=ny, **kw)
+    finally:
+        op.set_check_cache(False)
+    assert it0 == it1
+    assert torch.max(torch.abs(g0 - g1)).item() <= 1e-6 * torch.max(torch.abs(g0)).item()
+    assert abs(dlam1 - dlam0) <= 1e-6 * abs(dlam0) and abs(dbw1 - dbw0) <= 1e-6 * abs(dbw0)
+
+
+def test_cache_reserves_and_frees_memory():
+    n = 3001
+    op = ops.KernelOperator(torch.from_numpy(W.random_points(n, 4, seed=1)).cuda(), ops.RBF, 2.0)
+    need = n * 3072 * 4  # rows padded to a multiple of 128 floats
+    torch.cuda.synchronize()
+    f0 = torch.cuda.mem_get_info()[0]
+    op.set_check_cache(True)
+    op.set_check_cache(True)  # already reserved: no second buffer
+    f1 = torch.cuda.mem_get_info()[0]
+    op.set_check_cache(False)
+    f2 = torch.cuda.mem_get_info()[0]
+    assert need <= f0 - f1 <= need + (64 << 20)
+    assert f2 - f1 >= need
+
+
+def test_cache_refused_when_it_does_not_fit_and_for_ridge():
+    # 300000^2 * 4 bytes = 360 GB: more than the device holds, nothing reserved
+    n = 300_000
+    op = ops.KernelOperator(torch.from_numpy(W.random_points(n, 1, seed=2)).cuda(), ops.RBF, 1.0)
+    f0 = torch.cuda.mem_get_info()[0]
+    with pytest.raises(KopError, match="not enough free device memory"):
+        op.set_check_cache(True)
+    assert torch.cuda.mem_get_info()[0] >= f0 - (64 << 20)
+    rop = ops.RidgeOperator(torch.from_numpy(W.random_block(50, 8, seed=1)).cuda())
+    with pytest.raises(KopError, match="ridge"):
+        rop.set_check_cache(True)
+
+
+def test_caller_buffer_checked():
+    n = 500
+    op = ops.KernelOperator(torch.from_numpy(W.random_points(n, 4, seed=6)).cuda(), ops.RBF, 2.0)
+    need = op.check_cache_floats()
+    assert need == n * 512
+    with pytest.raises(KopError, match="buffer smaller"):
+        op.set_check_cache(True, torch.empty(need - 1, device="cuda"))
+    buf = torch.empty(need + 4, device="cuda")
+    with pytest.raises(KopError, match="aligned"):
+        op.set_check_cache(True, buf[1:])
+    op.set_check_cache(True, buf)
+    op.set_check_cache(False)
