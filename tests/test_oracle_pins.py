@@ -402,3 +402,42 @@ def test_ridge_nystrom_pcg_reaches_the_closed_form_solution():
     wd = np.linalg.solve(X.T @ X + wl.lam * np.eye(200), b)
     assert np.linalg.norm(w - wd) / np.linalg.norm(wd) <= 1e-8
     assert it < 60
+
+
+def test_shifted_solve_spectral_closed_form():
+    # (Q diag(a) Q^T + s I)^-1 b = Q diag(1 / (a + s)) Q^T b
+    rng = np.random.default_rng(11)
+    Q, _ = np.linalg.qr(rng.standard_normal((50, 50)))
+    a = np.logspace(-3, 2, 50)
+    A = (Q * a) @ Q.T
+    b = rng.standard_normal(50)
+    for s in (1e-4, 0.3, 7.0):
+        ref = Q @ ((Q.T @ b) / (a + s))
+        np.testing.assert_allclose(O.shifted_solve(A, b, s), ref, rtol=1e-9, atol=1e-12)
+
+
+def test_pcg_warm_start():
+    # the warm start begins from r = b - A x0: (i) an exact x0 stops after 0
+    # products; (ii) on a matrix with 3 distinct eigenvalues CG terminates in
+    # 3 steps from any x0 (the initial error spans at most 3 eigenspaces);
+    # (iii) a warm run equals x0 plus a cold run on b - A x0 (same Krylov
+    # space), over a fixed number of steps.  Starting from r = b instead
+    # fails (ii) and (iii).
+    ev = np.repeat([1.0, 10.0, 100.0], [40, 30, 30])
+    A = _spd_with_spectrum(ev, 7)
+    rng = np.random.default_rng(8)
+    b = rng.standard_normal(100)
+    xs = np.linalg.solve(A, b)
+    x, it, hist = O.pcg(lambda v: A @ v, b, None, tol=1e-10, maxit=50, x0=xs)
+    assert it == 0 and hist[0] <= 1e-10
+    x0 = xs + rng.standard_normal(100)
+    x, it, _ = O.pcg(lambda v: A @ v, b, None, tol=1e-30, maxit=3, x0=x0)
+    assert it == 3
+    assert np.linalg.norm(A @ x - b) / np.linalg.norm(b) < 1e-9
+    B2 = _spd_with_spectrum(np.logspace(0, 3, 100), 9)
+    D = np.diag(1.0 / np.linspace(1, 4, 100))
+    x0 = rng.standard_normal(100)
+    xw, iw, _ = O.pcg(lambda v: B2 @ v, b, lambda v: D @ v, tol=1e-30, maxit=8, x0=x0)
+    dc, ic, _ = O.pcg(lambda v: B2 @ v, b - B2 @ x0, lambda v: D @ v, tol=1e-30, maxit=8)
+    assert iw == ic == 8
+    np.testing.assert_allclose(xw, x0 + dc, rtol=1e-10, atol=1e-10)
