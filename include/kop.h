@@ -185,8 +185,9 @@ int kop_sync(kop_t op, void* stream);
  *
  * nys_build: Omega (device, n x r FP32) is the caller's test matrix (the
  * library does not orthonormalize it; Gaussian N(0,1)/sqrt(n) entries are
- * expected).  It is rounded to BF16 once and the rounded matrix is used in
- * every step (the result is the exact Nystrom approximation for it).  Steps: Y = K Omega (fused operator, `mode`),
+ * expected).  It is used as given in every step (the sketch's tensor-core
+ * contraction carries it as a BF16 hi + lo pair, about 2^-16 relative, like
+ * the fast operator's kernel values).  Steps: Y = K Omega (fused operator, `mode`),
  * nu = nu_rel * ||Y||_2 (nu_rel <= 0 selects 2^-16 for KOP_FAST and 2^-21
  * otherwise), Y_nu = Y + nu Omega, C = chol(sym(Omega^T Y_nu)) in FP64 (on a
  * failed pivot nu grows 10x, at most 3 times, then KOP_ENOTPD),
@@ -227,7 +228,9 @@ int nys_build_adaptive(kop_t op, const float* Omega, int32_t ld_omega, int32_t r
  *   rho = lam_hat_r + mu (adaptive != 0) or mu (adaptive == 0).
  * This is the inverse of the damped Nystrom preconditioner of App. A.5
  * ("damping_mode") divided by rho; PCG iterates do not depend on that
- * scale.  V, O: device n x m.                                               */
+ * scale.  V, O: device n x m.  mu[c] must be finite and > 0; mu[c] = 0 is
+ * accepted only with adaptive != 0 and lam_hat_r > 0 (else 1 / (lam_k + mu)
+ * would divide by zero): KOP_EINVAL otherwise.                              */
 int nys_apply(nys_t ny, const double* mu, int32_t adaptive, const float* V, int32_t m, float* O,
               void* stream);
 
@@ -239,7 +242,8 @@ int nys_apply(nys_t ny, const double* mu, int32_t adaptive, const float* V, int3
  * is a fixed array of 16448 doubles (128.5 KB) inside the library's device
  * image, held on every GPU that loads the library until the process exits;
  * r * m + m must fit in it (r <= 2048 with m <= 8 always does), else
- * KOP_EINVAL.  All calls share that array: calls whose GPU work overlaps race,
+ * KOP_EINVAL.  mu as for nys_apply.  The arithmetic is nys_apply's
+ * (float-float projections).  All calls share that array: calls whose GPU work overlaps race,
  * so order them on one stream.  The first call on a device looks up the
  * array's address and should come before any stream capture.               */
 int nys_apply_noalloc(nys_t ny, const double* mu, int32_t adaptive, const float* V, int32_t m,
@@ -256,8 +260,19 @@ int nys_factor(nys_t ny, float* U_out, void* stream);
  *     (K + lambdas[s] I) x_c = B[:, j]
  * with its own alpha and beta; each column stops when its recursive residual
  * satisfies ||r|| <= tol ||b|| (PCGStoppingCriteria, App. A.1: the
- * condition must hold for every right-hand side) AND the true residual,
- * recomputed with `check_mode`, does too.  Every `refine_every` iterations
+ * condition must hold for every right-hand side) AND its float64 relative
+ * residual ||b - (A + lam I) x|| / ||b|| (the paper's acceptance test,
+ * App. B.2) is certified to be <= tol.  Certification: the true residual r
+ * is recomputed with `check_mode` on all n rows; unless that is KOP_EXACT,
+ * the exact FP64 residual r64 of the rows i_k = floor((2k+1) n / (2s)),
+ * k < s, corrects it by the difference estimator
+ *     est^2 = sum_i r_i^2 + (n/s) sum_k (r64_ik^2 - r_ik^2)
+ * and the column is accepted when est^2 plus three standard errors of the
+ * correction is <= tol^2 ||b||^2.  s = n (every row: the test is exact) for
+ * n <= 4096, else s = 1024 (ridge operators: every row).  What the check
+ * operator missed lowers the column's next candidate threshold; when it is
+ * above 0.8 tol^2 ||b||^2 the check operator cannot certify the tolerance and
+ * the solve's later checks and refinements use KOP_EXACT.  Every `refine_every` iterations
  * (0 = only at candidate stops and at maxit) the recursive residual is
  * replaced by the true one computed with `refine_mode` (iterative refinement:
  * operator products with `inner_mode`).  Recommended: inner KOP_FAST, refine
@@ -286,7 +301,8 @@ int nys_factor(nys_t ny, float* U_out, void* stream);
  *   iters        host, nrhs * n_shifts ints (operator products per column)
  *   res_hist     host or NULL, (maxit + 1) x cols doubles: recursive
  *                ||r_k|| / ||b|| per iteration (NaN after a column stops)
- *   true_relres  host or NULL, cols doubles: final true relative residual
+ *   true_relres  host or NULL, cols doubles: the certified FP64 relative
+ *                residual (est / ||b||) of the last check of each column
  * Returns KOP_OK, KOP_NOT_CONVERGED (outputs written), KOP_ENOTPD on a
  * breakdown.  Synchronizes `stream`.                                         */
 int pcg_solve(kop_t op, nys_t ny, const double* lambdas, int32_t n_shifts, const double* mu,

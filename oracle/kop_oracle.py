@@ -315,13 +315,6 @@ def pcg(apply_A, b, apply_Pinv=None, tol=1e-6, maxit=1000, x0=None):
     return x, it, hist
 
 
-def shifted_operator(kind, X, bw, lam, K=None):
-    """v -> (K + lam I) v, with K explicit if given, else matrix-free."""
-    if K is not None:
-        return lambda v: K @ v + lam * v
-    return lambda v: kernel_matvec(kind, X, v, bw) + lam * v
-
-
 def krr_solve(kind, X, B, bw, lambdas, Omega=None, mu=None, adaptive=True, tol=1e-6,
               maxit=1000, nu_rel=None, explicit=True):
     """Nystrom PCG over all columns of B and all shifts (column c = rhs j,

@@ -8,7 +8,10 @@
 // residual floor near 1e-6.  B300's FP64 rate makes this about two orders of
 // magnitude slower than the fused product, so it is used for the periodic
 // true residual, not for the inner iterations.  One thread per query row;
-// tiles of 32 points and their V rows are staged in shared memory.
+// tiles of 32 points and their V rows are staged in shared memory.  When the
+// query rows alone cannot fill the GPU (the solver's sampled FP64 residual
+// rows), the keys are split over the grid's second dimension and the partial
+// sums are added with FP64 atomics.
 #include <cmath>
 
 #include "kop_device.cuh"
@@ -51,7 +54,7 @@ template <int KF, int MV>
 __global__ void __launch_bounds__(K4_ROWS) k4_exact_kernel(const float* __restrict__ Q, const float* __restrict__ Xk,
                                                            int d, const double* __restrict__ V, int ldv,
                                                            double* __restrict__ O, int ldo, int nq, int nk, int m,
-                                                           double bw) {
+                                                           double bw, int kchunk) {
   extern __shared__ double sd[];
   double* Qs = sd;                          // d x (K4_ROWS + 1), transposed
   double* Xs = Qs + d * (K4_ROWS + 1);      // K4_KEYS x d
@@ -65,18 +68,21 @@ __global__ void __launch_bounds__(K4_ROWS) k4_exact_kernel(const float* __restri
   double acc[MV];
 #pragma unroll
   for (int c = 0; c < MV; ++c) acc[c] = 0.0;
-  for (int j0 = 0; j0 < nk; j0 += K4_KEYS) {
+  // keys [kb, ke) of this CTA: all of them, or one chunk of a split grid
+  const int kb = blockIdx.y * kchunk;
+  const int ke = (nk - kb) < kchunk ? nk : kb + kchunk;
+  for (int j0 = kb; j0 < ke; j0 += K4_KEYS) {
     __syncthreads();
     for (int idx = tid; idx < K4_KEYS * d; idx += K4_ROWS) {
       const int jj = idx / d;
-      Xs[idx] = (j0 + jj < nk) ? (double)Xk[(int64_t)j0 * d + idx] : 0.0;
+      Xs[idx] = (j0 + jj < ke) ? (double)Xk[(int64_t)j0 * d + idx] : 0.0;
     }
     for (int idx = tid; idx < K4_KEYS * MV; idx += K4_ROWS) {
       const int jj = idx / MV, c = idx - jj * MV;
-      Vs[idx] = (j0 + jj < nk && c < m) ? V[(int64_t)(j0 + jj) * ldv + c] : 0.0;
+      Vs[idx] = (j0 + jj < ke && c < m) ? V[(int64_t)(j0 + jj) * ldv + c] : 0.0;
     }
     __syncthreads();
-    const int jn = nk - j0 < K4_KEYS ? nk - j0 : K4_KEYS;
+    const int jn = ke - j0 < K4_KEYS ? ke - j0 : K4_KEYS;
     for (int jj = 0; jj < jn; ++jj) {
       double d2 = 0.0;
       for (int k = 0; k < d; ++k) {
@@ -92,8 +98,26 @@ __global__ void __launch_bounds__(K4_ROWS) k4_exact_kernel(const float* __restri
   if (gi < nq) {
 #pragma unroll
     for (int c = 0; c < MV; ++c)
-      if (c < m) O[(int64_t)gi * ldo + c] = acc[c];
+      if (c < m) {
+        if (gridDim.y > 1)
+          atomicAdd(O + (int64_t)gi * ldo + c, acc[c]);
+        else
+          O[(int64_t)gi * ldo + c] = acc[c];
+      }
   }
+}
+
+// Key chunk of a split grid for nq query rows: about four CTAs per SM in
+// all, chunks of whole 32-key tiles; nk (no split) when the row blocks alone
+// fill the GPU.  A split grid accumulates into O, which must be zero.
+static int exact_key_chunk(int64_t nq, int64_t nk) {
+  const int64_t rb = (nq + K4_ROWS - 1) / K4_ROWS;
+  const int64_t want = 4 * (int64_t)num_sms();
+  if (rb >= want / 2 || nk <= 4 * K4_KEYS) return (int)nk;
+  int64_t splits = (want + rb - 1) / rb;
+  int64_t chunk = (nk + splits - 1) / splits;
+  chunk = (chunk + K4_KEYS - 1) / K4_KEYS * K4_KEYS;
+  return (int)chunk;
 }
 
 template <int KF, int MV>
@@ -107,8 +131,13 @@ static int launch_exact_t(const PointSet& Q, const PointSet& Ks, const double* V
     KOP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_limit_bytes()));
     attr_set = true;
   }
-  dim3 grid((unsigned)((Q.n + K4_ROWS - 1) / K4_ROWS));
-  kern<<<grid, K4_ROWS, smem, st>>>(Q.xorig, Ks.xorig, d, V, ldv, O, ldo, (int)Q.n, (int)Ks.n, m, bw);
+  const int kchunk = exact_key_chunk(Q.n, Ks.n);
+  dim3 grid((unsigned)((Q.n + K4_ROWS - 1) / K4_ROWS), (unsigned)((Ks.n + kchunk - 1) / kchunk));
+  if (grid.y > 1) {
+    // split keys: the CTAs add into O (column block of m <= MV columns)
+    KOP_CUDA_TRY(cudaMemset2DAsync(O, sizeof(double) * ldo, 0, sizeof(double) * m, Q.n, st));
+  }
+  kern<<<grid, K4_ROWS, smem, st>>>(Q.xorig, Ks.xorig, d, V, ldv, O, ldo, (int)Q.n, (int)Ks.n, m, bw, kchunk);
   KOP_LAUNCHED();
   return KOP_OK;
 }

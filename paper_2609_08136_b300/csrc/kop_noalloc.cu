@@ -9,7 +9,8 @@
 //
 // Properties of that array, for users of this entry point:
 //  - it holds 16448 doubles (128.5 KB) on every GPU that
-//    loads the library, until the process exits;
+//    loads the library, until the process exits; r * m + m doubles of it are
+//    used, which any Nystrom rank (r <= 2048) with m <= 8 columns fits;
 //  - every call uses the same array and it keeps the last call's contents;
 //    the accumulators are cleared on the stream at the start of each call;
 //  - calls whose GPU work overlaps (different streams, or host threads
@@ -37,14 +38,18 @@ struct NoallocMu {
   double mu[kNoallocMaxCols];
 };
 
-// W[k][c] *= 1 / (lam_k + mu_c) - 1 / rho_c; alpha[c] = 1 / rho_c.
+// w = W[k][c] (1 / (lam_k + mu_c) - 1 / rho_c), stored in W's own slot as the
+// FP32 pair hi + lo (exact to 2^-48) that the float-float product U w reads;
+// alpha[c] = 1 / rho_c.
 __global__ void noalloc_scale_kernel(double* __restrict__ W, int r, int m, const double* __restrict__ lam,
                                      NoallocMu mu, int adaptive, double* __restrict__ alpha) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= r * m) return;
   const int k = t / m, c = t - k * m;
   const double rho = adaptive ? lam[r - 1] + mu.mu[c] : mu.mu[c];
-  W[t] *= 1.0 / (lam[k] + mu.mu[c]) - 1.0 / rho;
+  const double w = W[t] * (1.0 / (lam[k] + mu.mu[c]) - 1.0 / rho);
+  const float hi = (float)w;
+  reinterpret_cast<float2*>(W)[t] = make_float2(hi, (float)(w - (double)hi));
   if (k == 0) alpha[c] = 1.0 / rho;
 }
 
@@ -80,9 +85,12 @@ extern "C" int nys_apply_noalloc(nys_t ny, const double* mu, int32_t adaptive, c
                                 " exceeds the fixed scratch of " + std::to_string(kNoallocScratchDoubles) + " doubles");
   NoallocMu mus;
   for (int c = 0; c < kNoallocMaxCols; ++c) mus.mu[c] = 0.0;
+  // mu = 0 needs lam_hat_r > 0 (adaptive): otherwise 1 / (lam_k + mu) divides by zero
+  const bool zero_ok = adaptive && ny->lam_host[ny->r - 1] > 0.0;
   for (int c = 0; c < m; ++c) {
-    if (!(mu[c] >= 0.0) || !std::isfinite(mu[c]) || (!adaptive && !(mu[c] > 0.0)))
-      return fail(KOP_EINVAL, "nys_apply_noalloc: mu must be finite, >= 0 (and > 0 when non-adaptive)");
+    if (!(mu[c] >= 0.0) || !std::isfinite(mu[c]) || (!zero_ok && !(mu[c] > 0.0)))
+      return fail(KOP_EINVAL,
+                  "nys_apply_noalloc: mu must be finite and > 0 (mu = 0 only when adaptive with lam_hat_r > 0)");
     mus.mu[c] = mu[c];
   }
   double* scratch = nullptr;
@@ -92,9 +100,10 @@ extern "C" int nys_apply_noalloc(nys_t ny, const double* mu, int32_t adaptive, c
   const int r = ny->r;
   double* W = scratch;                 // r x m
   double* alpha = scratch + (size_t)r * m;  // m
-  rc = utv64(ny->U, r, ny->n, r, V, m, W, st);  // clears W, then W = U^T V
+  // the same float-float projections as nys_apply (error-free FP32 pairs)
+  rc = utv_ff(ny->U, r, ny->n, r, V, m, W, st);  // clears W, then W = U^T V
   if (rc) return rc;
   noalloc_scale_kernel<<<(r * m + 255) / 256, 256, 0, st>>>(W, r, m, ny->lam_dev, mus, adaptive ? 1 : 0, alpha);
   KOP_LAUNCHED();
-  return uw64(ny->U, r, ny->n, r, W, V, m, alpha, O, st);
+  return uw_ff(ny->U, r, ny->n, r, reinterpret_cast<const float2*>(W), V, m, alpha, O, st);
 }

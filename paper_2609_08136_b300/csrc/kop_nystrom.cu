@@ -12,9 +12,10 @@
 // tall product.  All r x r work is FP64 on the device; the O(n r^2) Gram and
 // product passes read FP32 and accumulate in FP64 / FP32.  One Cholesky-QR
 // pass afterwards restores the orthonormality of U lost to FP32 rounding.
-// The test matrix is rounded to BF16 once on entry and the rounded Omega is
-// used in every step: the result is the exact Nystrom approximation for that
-// test matrix, and the sketch's contraction needs no lo split of Omega.
+// The caller's FP32 test matrix is used as given in every step: the sketch's
+// contraction carries it as a BF16 hi + lo pair (about 2^-16 relative, the
+// accuracy of the fast operator's kernel values), the Gram blocks read it in
+// FP32.
 #include <cmath>
 #include <vector>
 
@@ -79,11 +80,6 @@ int nys_apply_dev(const nys_s* ny, const double* mu_dev, int adaptive, const flo
   return tall_gemm(ny->U, nullptr, 0.0f, r, n, r, Wf, m, m, V, m, alpha_f, O, m, st);
 }
 
-__global__ void round_bf16_kernel(const float* __restrict__ a, float* __restrict__ b, int64_t n) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) b[i] = __bfloat162float(__float2bfloat16_rn(a[i]));
-}
-
 static int read_info(const int* dev, int* host, cudaStream_t st) {
   KOP_CUDA_TRY(cudaMemcpyAsync(host, dev, sizeof(int), cudaMemcpyDeviceToHost, st));
   KOP_CUDA_TRY(cudaStreamSynchronize(st));
@@ -109,16 +105,9 @@ extern "C" int nys_build(kop_t op, const float* Omega, int32_t r, double nu_rel,
   const size_t rr = (size_t)r * r;
   const int64_t n_pad = op_dim_pad(op);
   // workspace
-  DevBuf wsY, wsR, wsU, wsO;
-  wsY.st = wsR.st = wsU.st = wsO.st = st;
+  DevBuf wsY, wsR, wsU;
+  wsY.st = wsR.st = wsU.st = st;
   KOP_CUDA_TRY(cudaMallocAsync(&wsY.p, sizeof(float) * (size_t)n * r, st));
-  KOP_CUDA_TRY(cudaMallocAsync(&wsO.p, sizeof(float) * (size_t)n * r, st));
-  {
-    const int64_t tot = (int64_t)n * r;
-    round_bf16_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(Omega, (float*)wsO.p, tot);
-    KOP_LAUNCHED();
-    Omega = (const float*)wsO.p;
-  }
   const size_t nd = 9 * rr + 4 * (size_t)r + 16 + sym_eig_work_doubles(r);
   KOP_CUDA_TRY(cudaMallocAsync(&wsR.p, sizeof(double) * nd + sizeof(float) * rr + sizeof(int) * (r + 8), st));
   KOP_CUDA_TRY(cudaMallocAsync(&wsU.p, sizeof(float) * (size_t)n_pad * r, st));
@@ -143,7 +132,7 @@ extern "C" int nys_build(kop_t op, const float* Omega, int32_t r, double nu_rel,
 
   int rc;
   // 1. sketch Y = K Omega (fused operator, m = r)
-  rc = op_apply(op, mode, Omega, r, r, Y, r, st, true);
+  rc = op_apply(op, mode, Omega, r, r, Y, r, st);
   if (rc) return rc;
   // 2. Gram blocks
   if ((rc = gram(Omega, r, Omega, r, n, r, r, Goo, r, st))) return rc;
@@ -265,9 +254,11 @@ extern "C" int nys_apply(nys_t ny, const double* mu, int32_t adaptive, const flo
                          void* stream) {
   if (!ny || !mu || !V || !O) return fail(KOP_EINVAL, "nys_apply: NULL argument");
   if (m < 1) return fail(KOP_EINVAL, "nys_apply: m must be >= 1");
+  // mu = 0 needs lam_hat_r > 0 (adaptive): otherwise 1 / (lam_k + mu) divides by zero
+  const bool zero_ok = adaptive && ny->lam_host[ny->r - 1] > 0.0;
   for (int c = 0; c < m; ++c)
-    if (!(mu[c] >= 0.0) || !std::isfinite(mu[c]) || (!adaptive && !(mu[c] > 0.0)))
-      return fail(KOP_EINVAL, "nys_apply: mu must be finite, >= 0 (and > 0 when non-adaptive)");
+    if (!(mu[c] >= 0.0) || !std::isfinite(mu[c]) || (!zero_ok && !(mu[c] > 0.0)))
+      return fail(KOP_EINVAL, "nys_apply: mu must be finite and > 0 (mu = 0 only when adaptive with lam_hat_r > 0)");
   cudaStream_t st = (cudaStream_t)stream;
   const size_t r = ny->r;
   DevBuf ws;

@@ -14,10 +14,13 @@
 // K use the fast operator; every `refine_every` iterations, and whenever a
 // column's recursive residual meets the tolerance, the true residual
 // b - (K + lam I) x is recomputed with the accurate operator and replaces the
-// recursive one (iterative refinement), and a column stops only when the true
-// residual meets the tolerance too.  Vector updates run in fused passes over
-// the n x cols block with FP64 per-column reductions; the scalars alpha and
-// beta never leave the device.
+// recursive one (iterative refinement).  A column stops only when its float64
+// relative residual (the paper's acceptance test, App. B.2) is certified to
+// meet the tolerance: the check operator's residual over all n rows is
+// corrected by the exact FP64 residual of a stride sample of rows (a
+// difference estimator with a 3-sigma margin; exact when the sample is every
+// row).  Vector updates run in fused passes over the n x cols block with FP64
+// per-column reductions; the scalars alpha and beta never leave the device.
 #include <cmath>
 #include <vector>
 
@@ -28,6 +31,17 @@
 namespace kop {
 
 constexpr double kNearTol = 8.0;
+// Rows of the FP64 residual that certifies a candidate stop: every row when
+// n <= kCertAll, else a stride sample of kCertRows rows.
+constexpr int64_t kCertAll = 4096;
+constexpr int64_t kCertRows = 1024;
+// One-sided margin of the certification, in standard errors of the sampled
+// correction.
+constexpr double kCertSigmas = 3.0;
+// A check operator whose certified excess over its own residual is above
+// this fraction of tol^2 cannot certify the tolerance: the solve switches
+// its checks and refinements to the FP64 operator.
+constexpr double kEscalate = 0.8;
 
 enum { OP_INIT = 0, OP_PQ = 1, OP_XR = 2, OP_DOT = 3, OP_P = 4, OP_RES = 5, OP_DOT2 = 6, OP_SPLIT = 7, OP_RES64 = 8 };
 
@@ -234,6 +248,78 @@ __global__ void dot64_kernel(const double* a, const double* b, int64_t n, double
   }
 }
 
+// Rows of the certification sample: i_k = floor((2k + 1) n / (2 s)), k < s
+// (every row when s = n).
+__host__ __device__ inline int64_t cert_row(int64_t k, int64_t n, int64_t s) { return ((2 * k + 1) * n) / (2 * s); }
+
+__global__ void gather_rows_kernel(const float* __restrict__ X, int d, int64_t n, int64_t s, float* __restrict__ Xs) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= s * d) return;
+  const int64_t k = t / d;
+  Xs[t] = X[cert_row(k, n, s) * d + (t - k * d)];
+}
+
+// Per column c over the sampled rows i: with the FP64 product O64 (s x cols)
+// and the check's product T (n x 2 cols, the two columns of x's exact split),
+//   r64 = b_i - O64_kc - lam_c x_ic,  rchk = b_i - (T_i,c + T_i,cols+c) - lam_c x_ic,
+//   d = r64^2 - rchk^2;   sd_c += d, sd2_c += d^2.
+__global__ void __launch_bounds__(256) certify_kernel(int64_t n, int64_t s, int cols, int nrhs,
+                                                      const float* __restrict__ B, const double* __restrict__ X,
+                                                      const float* __restrict__ T, const double* __restrict__ O64,
+                                                      const double* __restrict__ lam, double* sd, double* sd2) {
+  const int c = blockIdx.y * 32 + threadIdx.x;
+  double a = 0.0, a2 = 0.0;
+  if (c < cols)
+    for (int64_t k = (int64_t)blockIdx.x * 8 + threadIdx.y; k < s; k += (int64_t)gridDim.x * 8) {
+      const int64_t i = cert_row(k, n, s);
+      const double bx = (double)B[i * nrhs + (c % nrhs)] - lam[c] * X[i * cols + c];
+      const double r64 = bx - O64[k * cols + c];
+      const int64_t t = i * 2 * cols + c;
+      const double rc = bx - ((double)T[t] + (double)T[t + cols]);
+      const double dd = (r64 - rc) * (r64 + rc);
+      a += dd;
+      a2 += dd * dd;
+    }
+  __shared__ double red[2][8][33];
+  red[0][threadIdx.y][threadIdx.x] = a;
+  red[1][threadIdx.y][threadIdx.x] = a2;
+  __syncthreads();
+  if (threadIdx.y == 0 && c < cols) {
+    double u = 0.0, u2 = 0.0;
+    for (int y = 0; y < 8; ++y) {
+      u += red[0][y][threadIdx.x];
+      u2 += red[1][y][threadIdx.x];
+    }
+    atomicAdd(sd + c, u);
+    atomicAdd(sd2 + c, u2);
+  }
+}
+
+// The certified squared residual of one column from the check's all-row sum
+// S = sum_i rchk_i^2 and the sample sums of d_i = r64_i^2 - rchk_i^2:
+//   est2 = S + (n / s) sum d   (the difference estimator of sum_i r64_i^2),
+//   ub2  = est2 + kCertSigmas * n sqrt((1 - s/n) var(d) / s),
+// exact (ub2 = est2 = sum r64^2) when s = n.
+struct Cert {
+  double est2, ub2;
+};
+static Cert certify_column(double S, double sd, double sd2, int64_t n, int64_t s) {
+  const double ns = (double)n / (double)s;
+  Cert ct;
+  ct.est2 = S + ns * sd;
+  ct.ub2 = ct.est2;
+  if (s < n && s > 1) {
+    const double mean = sd / (double)s;
+    double var = (sd2 / (double)s - mean * mean) * ((double)s / (double)(s - 1));
+    if (var < 0.0) var = 0.0;
+    const double fpc = 1.0 - (double)s / (double)n;
+    ct.ub2 += kCertSigmas * (double)n * std::sqrt(var * fpc / (double)s);
+  }
+  if (ct.est2 < 0.0) ct.est2 = 0.0;
+  if (ct.ub2 < ct.est2) ct.ub2 = ct.est2;
+  return ct;
+}
+
 struct PcgProblem {
   kop_s* op = nullptr;
   nys_s* ny = nullptr;
@@ -281,10 +367,33 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
   const size_t fbytes = sizeof(float) * (8 * nc + (size_t)r * cols + cols);
   const size_t dbytes = sizeof(double) * (12 * (size_t)cols + (size_t)r * cols);
   const size_t ibytes = sizeof(int) * (size_t)cols;
-  const size_t xbytes = (pb.refine_mode == KOP_EXACT || pb.check_mode == KOP_EXACT) ? sizeof(double) * nc : 0;
+  size_t xbytes = (pb.refine_mode == KOP_EXACT || pb.check_mode == KOP_EXACT) ? sizeof(double) * nc : 0;
+  // certification of candidate stops: the sampled rows' points, their FP64
+  // product (s x cols; every row of a ridge operator) and two sums per column
+  const int64_t s_rows = (op->ridge || n <= kCertAll) ? n : kCertRows;
+  const int dpt = op->ridge ? 0 : op->pts.d;
+  const size_t cbytes = sizeof(double) * ((size_t)s_rows * cols + 2 * (size_t)cols) +
+                        sizeof(float) * (size_t)s_rows * dpt + 64;
   KOP_CUDA_TRY(cudaMallocAsync(&ws.p, xbytes + dbytes + fbytes + ibytes + 256, st));
-  double* T64 = (double*)ws.p;
-  double* lam = T64 + (xbytes / sizeof(double));
+  Workspace wc;
+  wc.st = st;
+  KOP_CUDA_TRY(cudaMallocAsync(&wc.p, cbytes, st));
+  double* O64 = (double*)wc.p;
+  double* csd = O64 + (size_t)s_rows * cols;
+  double* csd2 = csd + cols;
+  float* samp_x = (float*)(csd2 + cols);
+  PointSet qs;
+  if (!op->ridge) {
+    qs.n = s_rows;
+    qs.d = dpt;
+    qs.xorig = samp_x;
+    gather_rows_kernel<<<(unsigned)((s_rows * dpt + 255) / 256), 256, 0, st>>>(op->pts.xorig, dpt, n, s_rows, samp_x);
+    KOP_LAUNCHED();
+  }
+  Workspace wx;  // the FP64 product of checks escalated to the exact operator
+  wx.st = st;
+  double* T64 = xbytes ? (double*)ws.p : nullptr;
+  double* lam = (double*)ws.p + (xbytes / sizeof(double));
   double* mu = lam + cols;
   double* alpha = mu + cols;
   double* beta = alpha + cols;
@@ -309,7 +418,7 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
   double* X = pb.Xout;
 
   std::vector<int> act(cols, 1);
-  std::vector<double> hb(cols), nb(cols), rel(cols, 0.0), hr0(cols);
+  std::vector<double> hb(cols), nb(cols), rel(cols, 0.0), hr(cols);
   KOP_CUDA_TRY(cudaMemcpyAsync(lam, pb.lam.data(), sizeof(double) * cols, cudaMemcpyHostToDevice, st));
   KOP_CUDA_TRY(cudaMemcpyAsync(mu, pb.mu.data(), sizeof(double) * cols, cudaMemcpyHostToDevice, st));
   KOP_CUDA_TRY(cudaMemsetAsync(op->status, 0, sizeof(int), st));
@@ -357,6 +466,62 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
     return rc2;
   };
 
+  // certified FP64 residual per column (relative to ||b||): trel = the
+  // estimate, urel = its upper bound; excess = (ub2 - S) / ||b||^2, what the
+  // check operator's residual S misses, which lowers the column's candidate
+  // threshold tol^2 - excess
+  std::vector<double> hsd(cols), hsd2(cols), trel(cols, 0.0), urel(cols, 0.0), excess(cols, 0.0);
+  // The true residual r = b - (A + lam I) x with the operator `mode` replaces
+  // R; with `certify`, a non-FP64 check is corrected by the sampled FP64
+  // residual.  Fills trel / urel / excess for the active columns.
+  auto true_residual = [&](int mode, bool certify) -> int {
+    int rmode = mode == KOP_PLAIN ? KOP_PLAIN_CHECK : mode;
+    const bool exact = rmode == KOP_EXACT;
+    if (exact) {
+      if (!T64) {
+        KOP_CUDA_TRY(cudaMallocAsync(&wx.p, sizeof(double) * nc, st));
+        T64 = (double*)wx.p;
+        va.T64 = T64;
+      }
+      if ((rc = op_apply_f64(op, X, cols, cols, T64, cols, st))) return rc;
+      if ((rc = vec_launch<OP_RES64>(va, st))) return rc;
+    } else {
+      if ((rc = vec_launch<OP_SPLIT>(va, st))) return rc;
+      if ((rc = check2(rmode))) return rc;
+      if ((rc = vec_launch<OP_RES>(va, st))) return rc;
+    }
+    KOP_CUDA_TRY(cudaMemcpyAsync(hr.data(), acc, sizeof(double) * cols, cudaMemcpyDeviceToHost, st));
+    const bool corr = certify && !exact;
+    if (corr) {
+      if (op->ridge) {
+        if ((rc = op_apply_f64(op, X, cols, cols, O64, cols, st))) return rc;
+      } else {
+        if ((rc = exact_matvec(qs, op->pts, op->kernel, op->bw, X, cols, cols, O64, cols, st))) return rc;
+      }
+      KOP_CUDA_TRY(cudaMemsetAsync(csd, 0, sizeof(double) * 2 * cols, st));
+      const unsigned gy = (unsigned)((cols + 31) / 32);
+      int64_t gx = (s_rows + 7) / 8;
+      if (gx > 2 * num_sms()) gx = 2 * num_sms();
+      certify_kernel<<<dim3((unsigned)gx, gy), dim3(32, 8), 0, st>>>(n, s_rows, cols, pb.nrhs, pb.B, X, T, O64, lam,
+                                                                    csd, csd2);
+      KOP_LAUNCHED();
+      KOP_CUDA_TRY(cudaMemcpyAsync(hsd.data(), csd, sizeof(double) * cols, cudaMemcpyDeviceToHost, st));
+      KOP_CUDA_TRY(cudaMemcpyAsync(hsd2.data(), csd2, sizeof(double) * cols, cudaMemcpyDeviceToHost, st));
+    }
+    KOP_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int c = 0; c < cols; ++c) {
+      if (!act[c]) continue;
+      const double nb2 = nb[c] * nb[c];
+      Cert ct{hr[c], hr[c]};
+      if (corr) ct = certify_column(hr[c], hsd[c], hsd2[c], n, s_rows);
+      trel[c] = std::sqrt(ct.est2 / nb2);
+      urel[c] = std::sqrt(ct.ub2 / nb2);
+      if (corr) excess[c] = (ct.ub2 - hr[c]) / nb2 > 0.0 ? (ct.ub2 - hr[c]) / nb2 : 0.0;
+      else if (exact) excess[c] = 0.0;
+    }
+    return KOP_OK;
+  };
+
   // x0 = 0, r0 = b, ||b|| per column
   if ((rc = vec_launch<OP_INIT>(va, st))) return rc;
   KOP_CUDA_TRY(cudaMemcpyAsync(hb.data(), acc, sizeof(double) * cols, cudaMemcpyDeviceToHost, st));
@@ -382,28 +547,24 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
     KOP_CUDA_TRY(cudaMemcpyAsync(X, pb.X0, sizeof(double) * nc, cudaMemcpyDeviceToDevice, st));
     zero_inactive_kernel<<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(X, (int64_t)nc, cols, active);
     KOP_LAUNCHED();
-    int rmode = pb.check_mode == KOP_PLAIN ? KOP_PLAIN_CHECK : pb.check_mode;
-    if (rmode == KOP_EXACT) {
-      if ((rc = op_apply_f64(op, X, cols, cols, T64, cols, st))) return rc;
-      if ((rc = vec_launch<OP_RES64>(va, st))) return rc;
-    } else {
-      if ((rc = vec_launch<OP_SPLIT>(va, st))) return rc;
-      if ((rc = check2(rmode))) return rc;
-      if ((rc = vec_launch<OP_RES>(va, st))) return rc;
-    }
-    KOP_CUDA_TRY(cudaMemcpyAsync(hr0.data(), acc, sizeof(double) * cols, cudaMemcpyDeviceToHost, st));
-    KOP_CUDA_TRY(cudaStreamSynchronize(st));
+    if ((rc = true_residual(pb.check_mode, true))) return rc;
     any = false;
+    bool escalate = false;
     for (int c = 0; c < cols; ++c) {
       if (!act[c]) continue;
-      const double tr = std::sqrt(hr0[c]) / nb[c];
-      if (pb.res_hist) pb.res_hist[c] = tr;
-      if (pb.true_relres) pb.true_relres[c] = tr;
-      if (tr <= pb.tol) {
+      if (pb.res_hist) pb.res_hist[c] = trel[c];
+      if (pb.true_relres) pb.true_relres[c] = trel[c];
+      if (urel[c] <= pb.tol) {
         act[c] = 0;
         if (pb.iters) pb.iters[c] = 0;
+      } else if (excess[c] > kEscalate * pb.tol * pb.tol) {
+        escalate = true;
       }
       any = any || act[c];
+    }
+    if (escalate) {
+      pb.check_mode = pb.refine_mode = KOP_EXACT;
+      for (int c = 0; c < cols; ++c) excess[c] = 0.0;
     }
     KOP_CUDA_TRY(cudaMemcpyAsync(active, act.data(), sizeof(int) * cols, cudaMemcpyHostToDevice, st));
   }
@@ -413,9 +574,9 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
   va.acc = acc;
   KOP_CUDA_TRY(cudaMemcpyAsync(P, Z, sizeof(float) * nc, cudaMemcpyDeviceToDevice, st));
 
+  const double tol2 = pb.tol * pb.tol;
   int it = 0;
   bool breakdown = false;
-  std::vector<double> hr(cols);
   std::vector<char> cand(cols);
   for (it = 1; any && it <= pb.maxit; ++it) {
     if ((rc = matvec(P, Q, pb.inner_mode))) return rc;
@@ -439,7 +600,9 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
       if (!act[c]) continue;
       rel[c] = std::sqrt(hr[c]) / nb[c];
       if (pb.res_hist) pb.res_hist[(size_t)it * cols + c] = rel[c];
-      if (rel[c] <= pb.tol) {
+      // a candidate stop once the recursive residual leaves room for what
+      // the last certification found the check operator to miss
+      if (rel[c] * rel[c] <= tol2 - excess[c]) {
         cand[c] = 1;
         any_cand = true;
       }
@@ -452,29 +615,30 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
     const bool refine = any_cand || periodic || it == pb.maxit;
     if (refine) {
       // the true residual replaces the recursive one: the refinement operator
-      // for periodic replacement, the check operator when a column may stop
-      int rmode = (any_cand || it == pb.maxit) ? pb.check_mode : pb.refine_mode;
-      if (rmode == KOP_PLAIN) rmode = KOP_PLAIN_CHECK;
-      if (rmode == KOP_EXACT) {
-        if ((rc = op_apply_f64(op, X, cols, cols, T64, cols, st))) return rc;
-        if ((rc = vec_launch<OP_RES64>(va, st))) return rc;
-      } else {
-        if ((rc = vec_launch<OP_SPLIT>(va, st))) return rc;
-        if ((rc = check2(rmode))) return rc;
-        if ((rc = vec_launch<OP_RES>(va, st))) return rc;
-      }
-      KOP_CUDA_TRY(cudaMemcpyAsync(hr.data(), acc, sizeof(double) * cols, cudaMemcpyDeviceToHost, st));
-      KOP_CUDA_TRY(cudaStreamSynchronize(st));
+      // for periodic replacement, the check operator (certified) when a
+      // column may stop
+      const bool stopping = any_cand || it == pb.maxit;
+      if ((rc = true_residual(stopping ? pb.check_mode : pb.refine_mode, stopping))) return rc;
       any = false;
+      bool escalate = false;
       for (int c = 0; c < cols; ++c) {
         if (!act[c]) continue;
-        const double tr = std::sqrt(hr[c]) / nb[c];
-        if (pb.true_relres) pb.true_relres[c] = tr;
-        if (cand[c] && tr <= pb.tol) {
+        if (stopping && pb.true_relres) pb.true_relres[c] = trel[c];
+        if (cand[c] && urel[c] <= pb.tol) {
           act[c] = 0;
           if (pb.iters) pb.iters[c] = it;
+        } else if (stopping && excess[c] > kEscalate * tol2) {
+          // any active column, candidate or not: its threshold tol^2 - excess
+          // would otherwise leave it no room to become a candidate again
+          escalate = true;
         }
         any = any || act[c];
+      }
+      // the check operator cannot certify the tolerance on this system: later
+      // checks and refinements use the FP64 operator
+      if (escalate) {
+        pb.check_mode = pb.refine_mode = KOP_EXACT;
+        for (int c = 0; c < cols; ++c) excess[c] = 0.0;
       }
       KOP_CUDA_TRY(cudaMemcpyAsync(active, act.data(), sizeof(int) * cols, cudaMemcpyHostToDevice, st));
       if (!any) break;

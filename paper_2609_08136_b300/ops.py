@@ -6,6 +6,7 @@ computation runs in the library's CUDA kernels.  Names follow include/kop.h.
 from __future__ import annotations
 
 import ctypes
+import warnings
 
 import torch
 
@@ -265,6 +266,17 @@ class Nystrom:
         return O[:, 0] if vec else O
 
 
+class NotConvergedWarning(RuntimeWarning):
+    """A solve returned KOP_NOT_CONVERGED: maxit was reached and the outputs
+    are the last iterate, whose certified residual is above the tolerance."""
+
+
+def _warn_unconverged(rc: int, where: str):
+    if rc == 1:
+        warnings.warn(f"{where}: maxit reached before the tolerance (KOP_NOT_CONVERGED)", NotConvergedWarning,
+                      stacklevel=3)
+
+
 class SolveResult:
     def __init__(self, x, iters, res_hist, true_relres, status):
         self.x, self.iters, self.res_hist, self.true_relres, self.status = x, iters, res_hist, true_relres, status
@@ -324,11 +336,12 @@ def pcg_adjoint(op: KernelOperator, x: torch.Tensor, dLdx: torch.Tensor, lam: fl
     it = ctypes.c_int32()
     dl = ctypes.c_double()
     db = ctypes.c_double()
-    check(_ffi.lib().pcg_adjoint(op.handle, nys.handle if nys is not None else None, float(lam),
-                                 int(bool(adaptive)), _ptr(x2), _ptr(d2), float(tol), int(maxit), int(refine_every),
-                                 int(inner_mode), int(refine_mode), int(check_mode), _ptr(g), ctypes.byref(it),
-                                 ctypes.byref(dl),
-                                 ctypes.byref(db), _stream(stream)), "pcg_adjoint")
+    rc = check(_ffi.lib().pcg_adjoint(op.handle, nys.handle if nys is not None else None, float(lam),
+                                      int(bool(adaptive)), _ptr(x2), _ptr(d2), float(tol), int(maxit),
+                                      int(refine_every), int(inner_mode), int(refine_mode), int(check_mode), _ptr(g),
+                                      ctypes.byref(it), ctypes.byref(dl), ctypes.byref(db), _stream(stream)),
+               "pcg_adjoint")
+    _warn_unconverged(rc, "pcg_adjoint")
     return g, dl.value, db.value, it.value
 
 
@@ -339,9 +352,12 @@ class _KRRSolve(torch.autograd.Function):
     def forward(ctx, b, bw, lam, op, nys, kw):
         op.set_bandwidth(float(bw))
         res = pcg_solve(op, b.detach().to(torch.float32), [float(lam)], nys=nys, **kw)
+        _warn_unconverged(res.status, "krr_solve")
         x = res.x.reshape(b.shape)
         ctx.save_for_backward(x)
-        ctx.op, ctx.nys, ctx.kw, ctx.lam = op, nys, kw, float(lam)
+        # the operator is shared and mutable: the backward pass restores the
+        # bandwidth this solve used
+        ctx.op, ctx.nys, ctx.kw, ctx.lam, ctx.bw = op, nys, kw, float(lam), float(bw)
         ctx.b_dtype, ctx.bw_dtype, ctx.lam_dtype = b.dtype, bw.dtype, lam.dtype
         return x
 
@@ -349,6 +365,7 @@ class _KRRSolve(torch.autograd.Function):
     def backward(ctx, gx):
         (x,) = ctx.saved_tensors
         kw = {k: v for k, v in ctx.kw.items() if k != "history"}
+        ctx.op.set_bandwidth(ctx.bw)
         g, dlam, dbw, _ = pcg_adjoint(ctx.op, x, gx, ctx.lam, nys=ctx.nys, **kw)
         return (g.reshape(x.shape).to(ctx.b_dtype), torch.tensor(dbw, dtype=ctx.bw_dtype),
                 torch.tensor(dlam, dtype=ctx.lam_dtype), None, None, None)

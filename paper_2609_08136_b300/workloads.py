@@ -66,19 +66,10 @@ def _f32(a):
     return np.ascontiguousarray(np.asarray(a, dtype=np.float64).astype(np.float32))
 
 
-def _round_bf16(a: np.ndarray) -> np.ndarray:
-    """Round FP32 values to the nearest BF16-representable value (ties to even)."""
-    b = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
-    b = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
-    return b.astype(np.uint32).view(np.float32)
-
-
 def gaussian_sketch(n: int, r: int, seed: int) -> np.ndarray:
-    """Omega in R^{n x r}, N(0,1)/sqrt(n) drawn with seed 1000+seed, stored as
-    FP32 values that are exactly representable in BF16 (the solver uses its
-    test matrix at BF16 precision, so both sides then see the same Omega)."""
+    """Omega in R^{n x r}, N(0,1)/sqrt(n) drawn with seed 1000+seed, in FP32."""
     rng = np.random.default_rng(1000 + seed)
-    return _round_bf16(_f32(rng.standard_normal((n, r)) / np.sqrt(n)))
+    return _f32(rng.standard_normal((n, r)) / np.sqrt(n))
 
 
 def krr_rbf_small(seed: int = 0, n: int = 4096, d: int = 16) -> Workload:

@@ -3,9 +3,10 @@
 product of a solve stores K(X, X) as the direct-difference operator computes
 it; later checks of that solve multiply the stored matrix with the same
 error-free contraction.  So the solver takes the same decisions, its outputs
-agree up to the order of the compensated sums, and the true residual it
-reports matches the oracle's FP64 residual of the returned iterate to within
-the FP32 entry error of the check operator."""
+agree up to the order of the compensated sums, the residual it reports is
+the certified FP64 residual, which matches the oracle's, and the oracle's
+FP64 residual of every accepted iterate meets the tolerance (the paper's
+acceptance test, App. B.2)."""
 import numpy as np
 import pytest
 import torch
@@ -51,7 +52,7 @@ def test_cached_checks_match_direct_checks(kind, n, nrhs, lams):
     r = min(64, n)
     ny = ops.Nystrom(op, torch.from_numpy(W.gaussian_sketch(n, r, seed=n)).cuda())
     # refinement every 5 iterations: many check products per solve
-    kw = dict(tol=5e-7, maxit=400, refine_every=5)
+    kw = dict(tol=1e-6, maxit=400, refine_every=5)
     a = _solve(op, B, lam_abs, ny, None, **kw)
     b = _solve(op, B, lam_abs, ny, "library", **kw)
     c = _solve(op, B, lam_abs, ny, "buffer", **kw)
@@ -65,14 +66,10 @@ def test_cached_checks_match_direct_checks(kind, n, nrhs, lams):
     # about 2^-24 |(K x)_i| / ||b|| per such element (~1e-9 here)
     np.testing.assert_allclose(b.true_relres, a.true_relres, rtol=1e-4, atol=1e-8)
     np.testing.assert_allclose(c.true_relres, a.true_relres, rtol=1e-4, atol=1e-8)
-    # the reported true residuals against the oracle's FP64 residuals: they
-    # differ by the check operator's FP32 entry errors (direct-difference
-    # distance, square root and exp: below 4e-6 of each entry here), rounding
-    # errors of different entries, which add up in quadrature:
-    # ||dr|| ~ 4e-6 || sqrt((K o K)(x o x)) ||.  (An FP32 emulation of the
-    # check's entries puts its error 55-90x below this bound in every case
-    # here; at lam = 1e-3 n it reaches 1.3e-6 for the Matern kernel, so the
-    # FP64 residual of an accepted iterate may exceed the tolerance there.)
+    # the oracle's FP64 residual of each accepted iterate meets the tolerance,
+    # and the reported residual is that FP64 residual: exact here (n <= 4096,
+    # so the solver's FP64 certification covers every row) up to the FP64
+    # rounding of the two products
     K = O.kernel_matrix(_KIND[kind], X, X, bw)
     xb2 = xb.reshape(n, -1)
     for col in range(xb2.shape[1]):
@@ -80,8 +77,8 @@ def test_cached_checks_match_direct_checks(kind, n, nrhs, lams):
         lam = lam_abs[col // nrhs]
         nb = np.linalg.norm(bc)
         rr = np.linalg.norm(K @ xb2[:, col] + lam * xb2[:, col] - bc) / nb
-        bound = 4e-6 * np.linalg.norm(np.sqrt((K * K) @ (xb2[:, col] ** 2))) / nb
-        assert abs(b.true_relres[col] - rr) <= bound, (col, b.true_relres[col], rr, bound)
+        assert rr <= 1e-6, (col, rr)
+        assert abs(b.true_relres[col] - rr) <= 1e-3 * rr, (col, b.true_relres[col], rr)
 
 
 def test_cached_checks_in_the_adjoint():
@@ -93,7 +90,7 @@ def test_cached_checks_in_the_adjoint():
     ny = ops.Nystrom(op, torch.from_numpy(W.gaussian_sketch(n, 64, seed=3)).cuda())
     x = torch.from_numpy(W.random_block(n, 1, seed=4)[:, 0].astype(np.float64)).cuda()
     dl = torch.from_numpy(W.random_block(n, 1, seed=5)[:, 0].astype(np.float64)).cuda()
-    kw = dict(tol=5e-7, maxit=400, refine_every=5)
+    kw = dict(tol=1e-6, maxit=400, refine_every=5)
     g0, dlam0, dbw0, it0 = ops.pcg_adjoint(op, x, dl, lam, nys=ny, **kw)
     op.set_check_cache(True)
     try:
