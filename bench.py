@@ -1,11 +1,21 @@
-"""Benchmark: Nystrom-PCG time-to-relres on the Laplace-mixture KRR workload.
+"""Benchmark: Nystrom-PCG time-to-relres on kernel-ridge-regression workloads.
 
 One step = the whole hot path on one batch of resident synthetic inputs:
 kop_create (centre + BF16 split), nys_build (sketch K Omega on the fused
-operator, r x r FP64 core, U), pcg_solve to relative residual <= 5e-7 with
-true-residual replacement (so that the FP64 relative residual is <= 1e-6).
-Workload: n = 200000, d = 64, 20-cluster Gaussian mixture, Laplace kernel
-sigma = 8, lam = 1e-6 n, Nystrom rank 500, one right-hand side.
+operator, r x r FP64 core, U), pcg_solve until the float64 relative residual
+is certified <= 1e-6 (the solver's checks are corrected by an exact FP64
+residual of sampled rows).  The hyper-parameter workload adds the validation
+loss and its gradient (pcg_adjoint_val) to the step.
+
+Workloads (--workload; default krr_laplace_mix):
+  krr_laplace_mix   n = 200000, d = 64, 20-cluster Gaussian mixture, Laplace
+                    sigma = 8, lam = 1e-6 n, rank 500, one right-hand side
+  krr_rbf_small     n = 4096, d = 16, RBF sigma = 4, lam = 1e-4 n, rank 100
+  krr_matern_large  n = 1e6, d = 32, z-scored uniform, Matern-5/2 l = 1
+                    (--lengthscale for the sqrt(d) variant), lam = 1e-7 n,
+                    rank 1000, refinement every 20 iterations
+  krr_rbf_hyper     train n = 1e5, val n = 2e4, d = 32, RBF sigma = sqrt(d),
+                    lam = 1e-4 n, rank 500: solve + validation-loss gradient
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
 on a bounded sample of the same workload instead.
@@ -27,8 +37,18 @@ sys.path.insert(0, ROOT)
 METRIC = "PCG time-to-relres 1e-6 & fused kernel-matvec TFLOP/s vs plain FP32 path"
 TOL = 1e-6
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the FAST
-# single-column product, keyed by (n, d); mean of two launches at full size
-TRAFFIC_BYTES = {(200_000, 64): 74.46e6}
+# single-column product, keyed by (kernel, n, d); mean of two launches at full
+# size, taken on the kernel as it stands
+TRAFFIC_BYTES = {(1, 200_000, 64): 74.46e6}
+
+# name: (generator kwargs, description, refine_every, maxit)
+WORKLOADS = {
+    "krr_laplace_mix": ("krr_laplace_mix n=200000 d=64 laplace sigma=8 lam=0.2 r=500 rhs=1", 30, 500),
+    "krr_rbf_small": ("krr_rbf_small n=4096 d=16 rbf sigma=4 lam=0.4096 r=100 rhs=1", 30, 500),
+    "krr_matern_large": ("krr_matern_large n=1000000 d=32 matern52 l={l} lam=0.1 r=1000 rhs=1", 20, 500),
+    "krr_rbf_hyper": ("krr_rbf_hyper n=100000 nval=20000 d=32 rbf sigma=sqrt(32) lam=10 r=500: solve + "
+                      "validation-loss gradient", 30, 500),
+}
 
 
 def _args():
@@ -37,15 +57,45 @@ def _args():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="native", choices=["native", "reference"])
-    p.add_argument("--n", type=int, default=200_000)
-    p.add_argument("--rank", type=int, default=500)
+    p.add_argument("--workload", default="krr_laplace_mix", choices=sorted(WORKLOADS))
+    p.add_argument("--lengthscale", type=float, default=1.0, help="krr_matern_large: Matern lengthscale")
+    p.add_argument("--n", type=int, default=None, help="override the workload's n (parity / probing only)")
+    p.add_argument("--rank", type=int, default=None)
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-plain", action="store_true")
-    p.add_argument("--check-cache", action="store_true",
-                   help="keep the kernel matrix of the checks in HBM (n^2 * 4 bytes); each solve recomputes it")
+    p.add_argument("--plain", action="store_true", help="time the plain FP32 path on workloads other than the default")
+    p.add_argument("--no-fp64-check", action="store_true")
+    p.add_argument("--no-check-cache", action="store_true",
+                   help="recompute the checks' kernel matrix instead of keeping it in HBM (n^2 * 4 bytes)")
     return p.parse_args()
+
+
+def _workload(a, seed):
+    from paper_2609_08136_b300 import workloads as W
+    kw = {}
+    if a.n is not None:
+        kw["n"] = a.n
+    if a.rank is not None:
+        kw["rank"] = a.rank
+    if a.workload == "krr_laplace_mix":
+        return W.krr_laplace_mix(seed=seed, **kw)
+    if a.workload == "krr_rbf_small":
+        wl = W.krr_rbf_small(seed=seed, **{k: v for k, v in kw.items() if k == "n"})
+        if a.rank is not None:
+            wl.rank = a.rank
+        return wl
+    if a.workload == "krr_matern_large":
+        return W.krr_matern_large(seed=seed, lengthscale=a.lengthscale, **kw)
+    return W.krr_rbf_hyper(seed=seed, **kw)
+
+
+def _describe(a):
+    d = WORKLOADS[a.workload][0].format(l=a.lengthscale)
+    if a.n is not None or a.rank is not None:
+        d += f" (override n={a.n} rank={a.rank})"
+    return d
 
 
 def _peaks():
@@ -128,7 +178,7 @@ def max_over_ranks(value: float, dist=None, device=None) -> float:
     return float(t.item())
 
 
-def _cpu_oracle_rate(wl, iters, rank_r, budget_s=15.0):
+def _cpu_oracle_rate(wl, iters, rank_r, budget_s=15.0, extra_matvecs=0.0):
     """FP64 oracle (host C, all cores): matvec and sketch times extrapolated
     from a bounded sample of rows.  Returns (solve_seconds, sample text, cores)."""
     import numpy as np
@@ -137,7 +187,7 @@ def _cpu_oracle_rate(wl, iters, rank_r, budget_s=15.0):
     n = wl.n
     cores = cmatvec.max_threads()
     v = np.random.default_rng(1).standard_normal(n)
-    rows = 64
+    rows = min(n, 64)
     t0 = time.perf_counter()
     cmatvec.kernel_matvec(wl.kernel, X, v, wl.bandwidth, Z=X[:rows])
     t_rows = time.perf_counter() - t0
@@ -151,36 +201,64 @@ def _cpu_oracle_rate(wl, iters, rank_r, budget_s=15.0):
     t0 = time.perf_counter()
     cmatvec.kernel_matvec(wl.kernel, X, om, wl.bandwidth, Z=X[:rows3])
     t_sk = (time.perf_counter() - t0) * n / rows3
-    total = t_sk + iters * t_mv
+    total = t_sk + (iters + extra_matvecs) * t_mv
+    extra = f" + {extra_matvecs:.1f} matvec-equivalents of validation products" if extra_matvecs else ""
     sample = (f"FP64 oracle K(X[:{rows2}],X)v and K(X[:{rows3}],X)Omega (r={rank_r}) on {cores} threads, "
-              f"extrapolated to full n: sketch {t_sk:.1f}s + {iters} matvecs x {t_mv:.1f}s")
+              f"extrapolated to full n: sketch {t_sk:.1f}s + {iters} matvecs x {t_mv:.1f}s{extra}")
     return total, sample, cores
+
+
+# iterations of the native solve on each workload (seed 0; the native arm
+# reports its own), used to extrapolate the oracle arm
+NATIVE_ITERS = {"krr_laplace_mix": 60, "krr_rbf_small": 45, "krr_matern_large": 3, "krr_rbf_hyper": 80}
+
+
+def _extra_matvecs(wl):
+    # the validation loss gradient: K(Xv, X) x, K(X, Xv) e, dK(Xv, X)/dbw x and
+    # the train derivative product, in units of one n x n product
+    if wl.Xval is None:
+        return 0.0
+    return 3.0 * wl.Xval.shape[0] / wl.n + 1.0
 
 
 def run_reference(a):
     world, rank, _ = _dist()
     if rank != 0:
         return
-    from paper_2609_08136_b300 import workloads as W
-    wl = W.krr_laplace_mix(seed=a.seed, n=a.n, rank=a.rank)
-    iters = 62  # the native solve's iteration count on this workload (it reports its own)
+    wl = _workload(a, a.seed)
+    iters = NATIVE_ITERS[a.workload] * (2 if wl.Xval is not None else 1)
     times = []
     sample = ""
     cores = 0
     for s in range(a.warmup + a.steps):
-        t, sample, cores = _cpu_oracle_rate(wl, iters, a.rank, budget_s=8.0)
+        t, sample, cores = _cpu_oracle_rate(wl, iters, wl.rank, budget_s=8.0, extra_matvecs=_extra_matvecs(wl))
         if s >= a.warmup:
             times.append(t)
     t = statistics.mean(times)
     out = {"metric": METRIC, "value": 1.0 / t, "unit": "solves/s", "impl": "reference", "n_gpus": a.gpus,
            "steps": a.steps, "warmup": a.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "krr_laplace_mix n=200000 d=64 laplace sigma=8 lam=0.2 r=500 rhs=1",
-                      "n": wl.n, "d": wl.d, "rank": a.rank, "extrapolated_iters": iters},
+           "config": {"workload": _describe(a), "n": wl.n, "d": wl.d, "rank": wl.rank, "extrapolated_iters": iters},
            "cpu_baseline": {"value": 1.0 / t, "unit": "solves/s", "cores": cores, "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": 1.0 / t, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
+
+
+def _fp64_relres(wl, x, full_limit=200_000, rows=4096):
+    """The oracle's FP64 relative residual of x (host cores): every row when
+    n <= full_limit, else a random sample of rows scaled to n."""
+    import numpy as np
+    from oracle import cmatvec
+    b = wl.B[:, 0].astype(np.float64)
+    lam = float(wl.lambdas[0])
+    if wl.n <= full_limit:
+        kx = cmatvec.kernel_matvec(wl.kernel, wl.X, x, wl.bandwidth)
+        return float(np.linalg.norm(b - kx - lam * x) / np.linalg.norm(b)), "all rows"
+    idx = np.sort(np.random.default_rng(7).choice(wl.n, size=rows, replace=False))
+    kx = cmatvec.kernel_matvec(wl.kernel, wl.X, x, wl.bandwidth, Z=wl.X[idx])
+    r = b[idx] - kx - lam * x[idx]
+    return float(np.sqrt(wl.n / rows) * np.linalg.norm(r) / np.linalg.norm(b)), f"{rows} random rows"
 
 
 def run_native(a):
@@ -197,51 +275,57 @@ def run_native(a):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
+    desc, refine_every, maxit = _describe(a), WORKLOADS[a.workload][1], WORKLOADS[a.workload][2]
+    hyper = a.workload == "krr_rbf_hyper"
     # each rank solves its own independent problems (weak scaling, no data-path
     # collective); timed step j solves the instance of seed a.seed + (j mod 3)
     n_inst = 3
     insts = []
     for j in range(n_inst):
         seed = replica_seed(a.seed, rank, j, n_inst)
-        wl_j = W.krr_laplace_mix(seed=seed, n=a.n, rank=a.rank)
-        Omh_j = torch.from_numpy(W.gaussian_sketch(wl_j.n, a.rank, seed=seed)).pin_memory()
-        Xh_j = torch.from_numpy(wl_j.X).pin_memory()
-        Bh_j = torch.from_numpy(wl_j.B).pin_memory()
-        insts.append({"seed": seed, "wl": wl_j, "Xh": Xh_j, "Bh": Bh_j, "Omh": Omh_j, "X": Xh_j.to(dev),
-                      "B": Bh_j.to(dev), "Om": Omh_j.to(dev)})
-    wl, Xh, Bh, Omh = insts[0]["wl"], insts[0]["Xh"], insts[0]["Bh"], insts[0]["Omh"]
-    lam = float(wl.lambdas[0])
+        wl_j = _workload(a, seed)
+        host = {"X": torch.from_numpy(wl_j.X).pin_memory(), "B": torch.from_numpy(wl_j.B).pin_memory(),
+                "Om": torch.from_numpy(W.gaussian_sketch(wl_j.n, wl_j.rank, seed=seed)).pin_memory()}
+        if hyper:
+            host["Xv"] = torch.from_numpy(wl_j.Xval).pin_memory()
+            host["yv"] = torch.from_numpy(wl_j.yval).pin_memory()
+        insts.append({"seed": seed, "wl": wl_j, "host": host, "dev": {k: v.to(dev) for k, v in host.items()}})
+    wl = insts[0]["wl"]
+    n, d, r_rank = wl.n, wl.d, wl.rank
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
     stream = torch.cuda.current_stream()
     # device memory for the kernel matrix of the checks (n^2 * 4 bytes), held
     # across steps like any workspace; each solve recomputes its contents
     kbuf = None
-    if a.check_cache:
-        need = a.n * ((a.n + 127) // 128 * 128)
-        if 4 * need + (8 << 30) <= torch.cuda.mem_get_info(dev)[0]:
+    if not a.no_check_cache:
+        need = n * ((n + 127) // 128 * 128)
+        if 4 * need + (16 << 30) <= torch.cuda.mem_get_info(dev)[0]:
             kbuf = torch.empty(need, dtype=torch.float32, device=dev)
 
-    # refinement and acceptance both with the direct-difference operator: the
-    # tensor-core accurate operator's own residual floor on this data (~1.2e-6)
-    # is as large as the residuals it would replace
-    def step(j, inner=ops.FAST, refine=ops.PLAIN, check=ops.PLAIN, build=ops.FAST, cache=True):
-        ins = insts[j % n_inst]
-        w = ins["wl"]
-        op = ops.KernelOperator(ins["X"], w.kernel, w.bandwidth)
+    # refinement and acceptance with the direct-difference operator (the
+    # tensor-core accurate operator's own residual floor on clustered data is
+    # as large as the residuals it would replace); stops certified in FP64
+    def step(tensors, w, inner=ops.FAST, refine=ops.PLAIN, check=ops.PLAIN, build=ops.FAST, cache=True):
+        op = ops.KernelOperator(tensors["X"], w.kernel, w.bandwidth)
         if cache and kbuf is not None:
             op.set_check_cache(True, kbuf)
-        ny = ops.Nystrom(op, ins["Om"], mode=build)
-        res = ops.pcg_solve(op, ins["B"], [float(w.lambdas[0])], nys=ny, tol=TOL, maxit=500, refine_every=30,
-                            inner_mode=inner, refine_mode=refine, check_mode=check)
-        return op, ny, res
+        ny = ops.Nystrom(op, tensors["Om"], mode=build)
+        kw = dict(tol=TOL, maxit=maxit, refine_every=refine_every, inner_mode=inner, refine_mode=refine,
+                  check_mode=check)
+        res = ops.pcg_solve(op, tensors["B"], [float(w.lambdas[0])], nys=ny, **kw)
+        if hyper:
+            h = ops.pcg_adjoint_val(op, res.x, tensors["Xv"], tensors["yv"], float(w.lambdas[0]), nys=ny, **kw)
+            return op, ny, res, h[:3]
+        return op, ny, res, None
 
     for _ in range(a.warmup):
-        op, ny, res = step(0)
+        op, ny, res, _h = step(insts[0]["dev"], insts[0]["wl"])
         del ny, op
-    times, iters_seen, launches, by_seed = [], [], [], {}
+    times, iters_seen, launches, by_seed, certified = [], [], [], {}, []
     clk = ClockSampler(local)
     clk.start()
     for j in range(a.steps):
+        ins = insts[j % n_inst]
         flush.fill_(1.0)
         torch.cuda.synchronize()
         if dist:
@@ -250,29 +334,31 @@ def run_native(a):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        op, ny, res = step(j)
+        op, ny, res, hres = step(ins["dev"], ins["wl"])
         e1.record(stream)
         torch.cuda.synchronize()
         launches.append(_ffi.lib().kop_launch_count() - l0)
         times.append(e0.elapsed_time(e1) / 1e3)
         iters_seen.append(res.iters[0])
-        by_seed.setdefault(insts[j % n_inst]["seed"], []).append(times[-1])
-        last = (op, ny, res, insts[j % n_inst]["wl"])
+        certified.append(res.true_relres[0])
+        by_seed.setdefault(ins["seed"], []).append(times[-1])
+        last = (op, ny, res, hres, ins["wl"])
         del ny, op
     clocks = clk.stop()
     t_step = max_over_ranks(statistics.mean(times), dist, dev)
-    op, ny, res, wl_last = last
+    op, ny, res, hres, wl_last = last
     value = world / t_step
     seed_t = [statistics.mean(v) for v in by_seed.values()]
     # the same PCG on the plain FP32 CUDA-core path: direct-difference kernel
     # values and FP32 FMAs for every product (sketch, iterations, refinement)
     plain_path = None
-    if not a.no_plain:
+    if (a.workload == "krr_laplace_mix" and not a.no_plain) or a.plain:
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        opp, nyp, resp = step(0, inner=ops.PLAIN, refine=ops.PLAIN, check=ops.PLAIN, build=ops.PLAIN, cache=False)
+        opp, nyp, resp, _h = step(insts[0]["dev"], insts[0]["wl"], inner=ops.PLAIN, refine=ops.PLAIN,
+                                  check=ops.PLAIN, build=ops.PLAIN, cache=False)
         e1.record(stream)
         torch.cuda.synchronize()
         tp = e0.elapsed_time(e1) / 1e3
@@ -281,45 +367,56 @@ def run_native(a):
                       if insts[0]["seed"] in by_seed else None}
         del nyp, opp
 
-    # fused operator product alone (m = 1), timed on the launching stream
-    V = torch.randn(wl.n, 1, device=dev)
+    # fused operator products alone, timed on the launching stream: the PCG
+    # product (m = 1) and the sketch product (m = r)
+    V = torch.randn(n, 1, device=dev)
     O = torch.empty_like(V)
+    Om0 = insts[0]["dev"]["Om"]
+    Osk = torch.empty_like(Om0)
 
-    def time_mv(mode, reps):
-        op.matvec(V, mode=mode, out=O)
+    def time_mv(mode, reps, Vin=V, Oout=O):
+        op.matvec(Vin, mode=mode, out=Oout)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(reps):
-            op.matvec(V, mode=mode, out=O)
+            op.matvec(Vin, mode=mode, out=Oout)
         e1.record(stream)
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / 1e3 / reps
 
     t_fast = time_mv(ops.FAST, 5)
-    t_plain = None if a.no_plain else time_mv(ops.PLAIN, 1)
-    n, d = wl.n, wl.d
+    t_plain = None if plain_path is None else time_mv(ops.PLAIN, 1)
+    t_sketch = time_mv(ops.FAST, 2, Om0, Osk)
+    del Osk
     flops = 2.0 * n * n * (d + 1)  # distance GEMM + contraction per K v
+    flops_sketch = 2.0 * n * n * (d + r_rank)
     peaks, peak_src = _peaks()
-    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0)
     # SFU roofline of the m = 1 product, with the SFU rates measured live on
-    # this GPU: a Laplace entry needs one sqrt and one ex2
+    # this GPU by the library's probe (MEASURED_PEAKS.json has no SFU figure):
+    # an RBF entry needs one ex2; Laplace and Matern one sqrt and one ex2
     rates = ops.sfu_rates()
-    peak_entries = 1.0 / (1.0 / rates["ex2"] + 1.0 / rates["sqrt"])
+    if wl.kernel == W.RBF:
+        peak_entries, per_entry = rates["ex2"], "1 ex2"
+    else:
+        peak_entries, per_entry = 1.0 / (1.0 / rates["ex2"] + 1.0 / rates["sqrt"]), "1 sqrt + 1 ex2"
     achieved_entries = n * n / t_fast
     # DRAM bytes per launch of that kernel, from one ncu capture of this
-    # workload (the ncu summary of this kernel); algorithmic bytes: X as
-    # two BF16 splits, scaled norms, v and the output, each once
-    traffic = TRAFFIC_BYTES.get((n, d))
-    alg_bytes = n * d * 2 * 2 + 3 * n * 4
+    # workload (the ncu summary of this kernel); algorithmic bytes: X as two
+    # BF16 splits, scaled norms, v and the output, each once
+    traffic = TRAFFIC_BYTES.get((wl.kernel, n, d))
+    dp = 16 if d <= 16 else (32 if d <= 32 else (64 if d <= 64 else 128))
+    alg_bytes = n * dp * 2 * 2 + 3 * n * 4
+    knames = {W.RBF: "RBF", W.LAPLACE: "LAPLACE", W.MATERN52: "MATERN"}
     out = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16x2-split/f32/f64", "data": "synthetic",
-        "config": {"workload": "krr_laplace_mix n=200000 d=64 laplace sigma=8 lam=0.2 r=500 rhs=1",
-                   "n": n, "d": d, "rank": a.rank, "tol": TOL, "l2": "flushed (256 MB write) before each step",
-                   "parallelism": f"replicas x{world}",
+        "config": {"workload": desc, "n": n, "d": d, "rank": r_rank, "tol": TOL,
+                   "acceptance": "float64 relative residual, certified by the solver (FP64 residual of sampled "
+                                 "rows corrects its FP32 check)",
+                   "l2": "flushed (256 MB write) before each step", "parallelism": f"replicas x{world}",
                    "check_matrix": ("stored in HBM, recomputed by every solve" if kbuf is not None
                                     else "recomputed in every check product")},
         "time_to_relres_s": t_step,
@@ -327,59 +424,60 @@ def run_native(a):
                                      "min": min(seed_t), "max": max(seed_t)},
         "plain_path": plain_path,
         "pcg_iters": iters_seen,
-        "true_relres_accurate_op": res.true_relres[0],
-        "matvec_ms": {"fused_fast": t_fast * 1e3, "plain_fp32": None if t_plain is None else t_plain * 1e3},
-        "matvec_tflops": {"fused_fast": flops / t_fast / 1e12,
-                          "plain_fp32": None if t_plain is None else flops / t_plain / 1e12},
+        "certified_fp64_relres": certified,
+        "matvec_ms": {"fused_fast_m1": t_fast * 1e3, "plain_fp32_m1": None if t_plain is None else t_plain * 1e3,
+                      "sketch_fast_m%d" % r_rank: t_sketch * 1e3},
+        "matvec_tflops": {"fused_fast_m1": flops / t_fast / 1e12,
+                          "plain_fp32_m1": None if t_plain is None else flops / t_plain / 1e12,
+                          "sketch_fast_m%d" % r_rank: flops_sketch / t_sketch / 1e12,
+                          "sketch_frac_of_bf16_burst": flops_sketch / t_sketch / 1e12 / peaks["bf16_tflops"]},
         "kernel_evals_per_s": achieved_entries,
         "roofline": {"bound": "alu", "achieved": achieved_entries / 1e12, "peak": peak_entries / 1e12,
                      "unit": "Tentries/s", "frac": achieved_entries / peak_entries, "traffic": traffic,
                      "traffic_unit": "bytes per launch (DRAM read + write, ncu)", "algorithmic_bytes": alg_bytes,
-                     "kernel": "k1_fma_kernel<LAPLACE,2,1,128,4> (K v, m = 1)",
-                     "peak_source": ("SFU rates measured live by kop_sfu_rates (ex2 %.2f, sqrt %.2f Tops/s); "
-                                     "one Laplace entry = 1 sqrt + 1 ex2" % (rates["ex2"] / 1e12, rates["sqrt"] / 1e12))},
+                     "kernel": "k1_fma_kernel<%s> (K v, m = 1)" % knames[wl.kernel],
+                     "peak_source": ("SFU rates measured live by the library's own probe kop_sfu_rates (ex2 %.2f, "
+                                     "sqrt %.2f Tops/s); one entry = %s" % (rates["ex2"] / 1e12,
+                                                                           rates["sqrt"] / 1e12, per_entry))},
         "clocks": clocks,
         "gpu_launches": int(statistics.mean(launches)),
         "peaks_source": peak_src,
     }
+    if hres is not None:
+        out["hypergradient"] = {"loss": hres[0], "dL_dsigma": hres[1], "dL_dlam": hres[2]}
     if not a.no_e2e:
-        # end to end through the public API with host buffers: H2D of X, y, Omega
-        # from pinned memory, the solve, D2H of x, all inside the timed region
-        xh = torch.empty(n, dtype=torch.float64).pin_memory()
-        ets = []
-        for i in range(2):
+        # end to end through the public API with host buffers: H2D of the inputs
+        # from pinned memory, the solve, D2H of x (and of the gradient scalars),
+        # inside the timed region; one run per seed, averaged like `value`
+        ets, hb = [], 0
+        for ins in insts:
+            w = ins["wl"]
+            xh = torch.empty(n, dtype=torch.float64).pin_memory()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            Xd = Xh.to(dev, non_blocking=True)
-            Bd = Bh.to(dev, non_blocking=True)
-            Omd = Omh.to(dev, non_blocking=True)
-            op2 = ops.KernelOperator(Xd, wl.kernel, wl.bandwidth)
-            if kbuf is not None:
-                op2.set_check_cache(True, kbuf)
-            ny2 = ops.Nystrom(op2, Omd, mode=ops.FAST)
-            r2 = ops.pcg_solve(op2, Bd, [lam], nys=ny2, tol=TOL, maxit=500, refine_every=30,
-                               refine_mode=ops.PLAIN, check_mode=ops.PLAIN)
+            tens = {k: v.to(dev, non_blocking=True) for k, v in ins["host"].items()}
+            op2, ny2, r2, _h = step(tens, w)
             xh.copy_(r2.x.reshape(-1), non_blocking=True)
             torch.cuda.synchronize()
             ets.append(time.perf_counter() - t0)
-            del ny2, op2
-        te = min(ets)
-        hb = Xh.numel() * 4 + Bh.numel() * 4 + Omh.numel() * 4
-        out["e2e"] = {"value": world / te, "unit": "solves/s", "h2d_bytes_per_step": hb, "d2h_bytes_per_step": n * 8}
-    # FP64 check of the returned x on sampled rows (host oracle, outside the timed region)
-    try:
-        from oracle import cmatvec
-        xs = res.x.reshape(-1).cpu().numpy()
-        wv = wl_last
-        rows = np.random.default_rng(7).choice(wv.n, size=min(256, wv.n), replace=False)
-        kx = cmatvec.kernel_matvec(wv.kernel, wv.X, xs, wv.bandwidth, Z=wv.X[rows])
-        bvec = wv.B[:, 0].astype(np.float64)
-        r_s = bvec[rows] - kx - float(wv.lambdas[0]) * xs[rows]
-        out["fp64_relres_sampled"] = float(np.sqrt(wv.n / len(rows)) * np.linalg.norm(r_s) / np.linalg.norm(bvec))
-    except Exception as e:  # the check is informational
-        out["fp64_relres_sampled"] = f"unavailable: {e}"
+            hb = sum(v.numel() * v.element_size() for v in ins["host"].values())
+            del ny2, op2, tens
+        te = statistics.mean(ets)
+        out["e2e"] = {"value": world / te, "unit": "solves/s", "h2d_bytes_per_step": hb, "d2h_bytes_per_step": n * 8,
+                      "estimator": "mean over seeds 0-2, one run each"}
+    if not a.no_fp64_check:
+        # the oracle's FP64 residual of the last timed solve (host cores,
+        # outside the timed region)
+        try:
+            t0 = time.perf_counter()
+            rr, how = _fp64_relres(wl_last, res.x.reshape(-1).cpu().numpy())
+            out["fp64_relres_oracle"] = {"value": rr, "rows": how, "certified_by_solver": res.true_relres[0],
+                                         "seconds": time.perf_counter() - t0}
+        except Exception as e:  # the check is informational
+            out["fp64_relres_oracle"] = f"unavailable: {e}"
     if rank == 0 and not a.no_cpu_baseline:
-        total, sample, cores = _cpu_oracle_rate(wl, int(statistics.mean(iters_seen)), a.rank)
+        it_cpu = int(statistics.mean(iters_seen)) * (2 if hyper else 1)
+        total, sample, cores = _cpu_oracle_rate(wl, it_cpu, r_rank, extra_matvecs=_extra_matvecs(wl))
         out["cpu_baseline"] = {"value": 1.0 / total, "unit": "solves/s", "cores": cores, "kind": "oracle",
                                "sample": sample}
     if dist:

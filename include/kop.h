@@ -325,6 +325,54 @@ int pcg_adjoint(kop_t op, nys_t ny, double lam, int32_t adaptive, const double* 
                 int32_t inner_mode, int32_t refine_mode, int32_t check_mode, double* g_out,
                 int32_t* iters, double* dLdlam, double* dLdbw, void* stream);
 
+/* Gradient of a validation loss through the solve (the paper's bilevel
+ * hyper-parameter problem, Sec. 3.2, Eq. "rlaopt-bilevel", for kernel ridge
+ * regression): with x the solution of (K + lam I) x = y (device, n FP64, from
+ * pcg_solve) and the validation set (Xval: device nval x d FP32, yval: device
+ * nval FP32), all in the library:
+ *     e = K(Xval, X) x - yval,            L = e^T e / nval,
+ *     dL/dx = (2 / nval) K(X, Xval) e,    g = (K + lam I)^-1 dL/dx (adjoint
+ *     PCG with the same preconditioner, mu = lam),
+ *     dL/dlam = -g^T x,
+ *     dL/dbw  = (2 / nval) e^T (dK(Xval, X)/dbw) x - g^T (dK/dbw) x,
+ * (dL/dy = g).  The cross and derivative products use `check_mode` (KOP_PLAIN:
+ * direct differences with error-free sums, on the exact two-term split of
+ * each FP64 vector; KOP_EXACT: FP64).  Writes g_out (device, n FP64) and the
+ * host scalars loss, dLdlam, dLdbw; iters: host int (may be NULL).  Kernel
+ * operators only (KOP_EINVAL for ridge).  Returns as pcg_solve for the
+ * adjoint solve.  Synchronizes `stream`.                                    */
+int pcg_adjoint_val(kop_t op, nys_t ny, double lam, int32_t adaptive, const double* x, const float* Xval,
+                    int64_t nval, const float* yval, double tol, int32_t maxit, int32_t refine_every,
+                    int32_t inner_mode, int32_t refine_mode, int32_t check_mode, double* g_out, int32_t* iters,
+                    double* loss, double* dLdlam, double* dLdbw, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * The linear solve inside NysADMM (ADMMConfig, App. A.4: sigma, gamma,
+ * preconditioner_update_freq; NysADMM is cited in Sec. 2.3 and Sec. 4.3).
+ * The k-th admm_solve call (k = 1, 2, ...) solves
+ *     (A + (rho_k + sigma) I) x_k = rhs_k
+ * with pcg_solve, warm-started from x_{k-1} (x_0 = 0), to the relative
+ * tolerance max(tol_min, k^-gamma), preconditioned by the randomized Nystrom
+ * approximation of A built from the handle's copy of Omega (device n x r FP32)
+ * in `nys_mode` on call 1 and every update_freq calls after it (update_freq
+ * = 0: built once), damped by rho_k + sigma.  The paper lists these controls
+ * without formulas; the schedule above is this library's reading.
+ * A: any operator (kernel or ridge); the handle must not outlive it.
+ * admm_create: 1 <= r <= min(n, 2048), update_freq >= 0, sigma >= 0, gamma >= 0,
+ *   0 < tol_min < 1, maxit >= 1, refine_every >= 0, modes as for pcg_solve;
+ *   synchronizes `stream`.
+ * admm_solve: rhs device n FP32, rho >= 0 with rho + sigma > 0; writes x_out
+ *   (device n FP64) and the host values iters, true_relres (the certified FP64
+ *   relative residual), tol_used and rebuilt (1 when this call rebuilt the
+ *   preconditioner), each optional.  Returns as pcg_solve.                  */
+typedef struct admm_s* admm_t;
+int admm_create(kop_t op, const float* Omega, int32_t r, int32_t update_freq, double sigma, double gamma,
+                double tol_min, int32_t maxit, int32_t refine_every, int32_t nys_mode, int32_t inner_mode,
+                int32_t refine_mode, int32_t check_mode, void* stream, admm_t* out);
+int admm_solve(admm_t a, const float* rhs, double rho, double* x_out, int32_t* iters, double* true_relres,
+               double* tol_used, int32_t* rebuilt, void* stream);
+int admm_destroy(admm_t a);
+
 #ifdef __cplusplus
 }
 #endif

@@ -42,6 +42,12 @@ SIGNATURES = {
                           c_i32, c_i32, c_i32, c_vp, P(c_i32), P(c_dbl), P(c_dbl), c_vp]),
     "pcg_adjoint": (c_int, [c_vp, c_vp, c_dbl, c_i32, c_vp, c_vp, c_dbl, c_i32, c_i32, c_i32, c_i32, c_i32, c_vp,
                             P(c_i32), P(c_dbl), P(c_dbl), c_vp]),
+    "admm_create": (c_int, [c_vp, c_vp, c_i32, c_i32, c_dbl, c_dbl, c_dbl, c_i32, c_i32, c_i32, c_i32, c_i32, c_i32,
+                            c_vp, P(c_vp)]),
+    "admm_solve": (c_int, [c_vp, c_vp, c_dbl, c_vp, P(c_i32), P(c_dbl), P(c_dbl), P(c_i32), c_vp]),
+    "admm_destroy": (c_int, [c_vp]),
+    "pcg_adjoint_val": (c_int, [c_vp, c_vp, c_dbl, c_i32, c_vp, c_vp, c_i64, c_vp, c_dbl, c_i32, c_i32, c_i32, c_i32,
+                                c_i32, c_vp, P(c_i32), P(c_dbl), P(c_dbl), P(c_dbl), c_vp]),
 }
 
 _lib = None

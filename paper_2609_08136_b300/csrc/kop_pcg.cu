@@ -22,6 +22,7 @@
 // row).  Vector updates run in fused passes over the n x cols block with FP64
 // per-column reductions; the scalars alpha and beta never leave the device.
 #include <cmath>
+#include <string>
 #include <vector>
 
 #include "kop_dense.h"
@@ -726,26 +727,74 @@ __global__ void split_vec_kernel(const double* __restrict__ x, float* __restrict
   v2[2 * i + 1] = (float)(x[i] - (double)hi);
 }
 
-extern "C" int pcg_adjoint(kop_t op, nys_t ny, double lam, int32_t adaptive, const double* x, const double* dLdx,
-                           double tol, int32_t maxit, int32_t refine_every, int32_t inner_mode, int32_t refine_mode,
-                           int32_t check_mode, double* g_out, int32_t* iters, double* dLdlam, double* dLdbw,
-                           void* stream) {
-  if (!op || !x || !dLdx || !g_out || !dLdlam || !dLdbw) return fail(KOP_EINVAL, "pcg_adjoint: NULL argument");
-  if (ny && ny->op != op) return fail(KOP_EINVAL, "pcg_adjoint: preconditioner built for another operator");
-  if (!(lam > 0.0) || !std::isfinite(lam)) return fail(KOP_EINVAL, "pcg_adjoint: lam must be > 0");
-  if (!(tol > 0.0) || maxit < 1 || refine_every < 0) return fail(KOP_EINVAL, "pcg_adjoint: bad tol / maxit");
-  if (!valid_mode(inner_mode) || !valid_mode(refine_mode) || !valid_mode(check_mode))
-    return fail(KOP_EINVAL, "pcg_adjoint: bad mode");
-  cudaStream_t st = (cudaStream_t)stream;
+namespace kop {
+
+// e_i = a_i + b_i - y_i in FP64 (a, b: the two product columns of an exact
+// split, stride 2), and its exact hi/lo FP32 split into e2 (n x 2).
+__global__ void residual_split_kernel(const float* __restrict__ t2, const float* __restrict__ y, int64_t n,
+                                      double* __restrict__ e, float* __restrict__ e2) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = ((double)t2[2 * i] + (double)t2[2 * i + 1]) - (double)y[i];
+  e[i] = v;
+  const float hi = (float)v;
+  e2[2 * i] = hi;
+  e2[2 * i + 1] = (float)(v - (double)hi);
+}
+
+// e_i = t64_i - y_i (FP64 product) and its split.
+__global__ void residual64_split_kernel(const double* __restrict__ t64, const float* __restrict__ y, int64_t n,
+                                        double* __restrict__ e, float* __restrict__ e2) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = t64[i] - (double)y[i];
+  e[i] = v;
+  const float hi = (float)v;
+  e2[2 * i] = hi;
+  e2[2 * i + 1] = (float)(v - (double)hi);
+}
+
+// out_i = scale * (a_i + b_i) (two product columns, stride 2) in FP64.
+__global__ void combine2_kernel(const float* __restrict__ t2, int64_t n, double scale, double* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = scale * ((double)t2[2 * i] + (double)t2[2 * i + 1]);
+}
+
+__global__ void scale64_kernel(double* __restrict__ a, int64_t n, double s) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] *= s;
+}
+
+// A product of the operator's kernel family `kf` (k or dk/dbw) between the
+// point sets Q and Ks applied to the FP64 vector v (Ks.n entries): O2 (Q.n x
+// 2 FP32, the two columns of v's exact split; their sum is the product), or
+// in KOP_EXACT mode O64 (Q.n FP64).  split: Ks.n x 2 FP32 scratch.
+static int cross_apply64(kop_s* op, const PointSet& Q, const PointSet& Ks, bool self, int kf, int mode,
+                         const double* v, float* split, float* O2, double* O64, cudaStream_t st) {
+  if (mode == KOP_EXACT) return exact_matvec(Q, Ks, kf, op->bw, v, 1, 1, O64, 1, st);
+  split_vec_kernel<<<(unsigned)((Ks.n + 255) / 256), 256, 0, st>>>(v, split, Ks.n);
+  KOP_LAUNCHED();
+  const KConst kc = kernel_constants(kf, op->bw);
+  const int m2 = mode == KOP_PLAIN ? KOP_PLAIN_CHECK : mode;
+  return op_matvec(Q, Ks, self, kf, kc, m2, split, 2, 2, O2, 2, op->status, st);
+}
+
+// The adjoint solve (K + lam I) g = dL/dx (dLdx: device FP64) with the same
+// preconditioner, then dL/dlam = -g^T x and the training term
+// dL/dbw|_K = -g^T (dK/dbw) x, the derivative product taken with check_mode.
+static int adjoint_core(kop_s* op, nys_s* ny, double lam, int adaptive, const double* x, const double* dLdx,
+                        double tol, int maxit, int refine_every, int inner_mode, int refine_mode, int check_mode,
+                        double* g_out, int32_t* iters, double* dLdlam, double* dLdbw, cudaStream_t st) {
   const int64_t n = op_dim(op);
   Workspace ws;
   ws.st = st;
-  // Bf (n) | V2 (2n) | T2 (2n) floats, acc (2) doubles
-  KOP_CUDA_TRY(cudaMallocAsync(&ws.p, sizeof(float) * 5 * (size_t)n + 2 * sizeof(double) + 64, st));
+  // Bf (n) | V2 (2n) | T2 (2n) floats, t64 (n) and acc (2) doubles
+  KOP_CUDA_TRY(cudaMallocAsync(&ws.p, sizeof(float) * 5 * (size_t)n + sizeof(double) * ((size_t)n + 2) + 64, st));
   float* Bf = (float*)ws.p;
   float* V2 = Bf + n;
   float* T2 = V2 + 2 * n;
   double* acc = (double*)(((uintptr_t)(T2 + 2 * n) + 15) & ~(uintptr_t)15);
+  double* t64 = acc + 2;
   const unsigned nb = (unsigned)((n + 255) / 256);
   d2f_vec_kernel<<<nb, 256, 0, st>>>(dLdx, Bf, n);
   KOP_LAUNCHED();
@@ -769,40 +818,138 @@ extern "C" int pcg_adjoint(kop_t op, nys_t ny, double lam, int32_t adaptive, con
   const int rc = pcg_core(pb, st);
   if (iters) *iters = it;
   if (rc < 0) return rc;
-  // dL/dbw = -g^T (dK/dbw) x with x split exactly into two FP32 columns,  dL/dlam = -g^T x
+  // dL/dlam = -g^T x through the exact split of x; g^T (dK/dbw) x through the
+  // two product columns of the split (or one FP64 product in exact mode)
   split_vec_kernel<<<nb, 256, 0, st>>>(x, V2, n);
   KOP_LAUNCHED();
   KOP_CUDA_TRY(cudaMemsetAsync(acc, 0, 2 * sizeof(double), st));
-  // g^T x through the exact split of x; g^T (dK/dbw) x through the two product
-  // columns of the split (or one FP64 product in exact mode)
   dot_kernel<<<4 * num_sms(), 256, 0, st>>>(g_out, V2, V2 + 1, n, 2, acc);
   KOP_LAUNCHED();
   if (op->ridge) {
     // X^T X has no bandwidth: dL/dbw = 0
-  } else if (check_mode == KOP_EXACT) {
-    double* t64 = nullptr;
-    KOP_CUDA_TRY(cudaMallocAsync((void**)&t64, sizeof(double) * n, st));
-    int r2 = exact_matvec(op->pts, op->pts, op->kernel + 3, op->bw, x, 1, 1, t64, 1, st);
-    if (r2 == KOP_OK) {
-      dot64_kernel<<<4 * num_sms(), 256, 0, st>>>(g_out, t64, n, acc + 1);
-      note_launch();
-    }
-    cudaFreeAsync(t64, st);
-    if (r2) return r2;
   } else {
-    const KConst kc = kernel_constants(op->kernel + 3, op->bw);
-    const int dmode = check_mode == KOP_PLAIN ? KOP_PLAIN_CHECK : check_mode;
-    int r2 = op_matvec(op->pts, op->pts, true, op->kernel + 3, kc, dmode, V2, 2, 2, T2, 2, op->status, st);
+    int r2 = cross_apply64(op, op->pts, op->pts, true, op->kernel + 3, check_mode, x, V2, T2, t64, st);
     if (r2) return r2;
-    dot_kernel<<<4 * num_sms(), 256, 0, st>>>(g_out, T2, T2 + 1, n, 2, acc + 1);
+    if (check_mode == KOP_EXACT)
+      dot64_kernel<<<4 * num_sms(), 256, 0, st>>>(g_out, t64, n, acc + 1);
+    else
+      dot_kernel<<<4 * num_sms(), 256, 0, st>>>(g_out, T2, T2 + 1, n, 2, acc + 1);
     KOP_LAUNCHED();
   }
   double h[2];
   KOP_CUDA_TRY(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, st));
   KOP_CUDA_TRY(cudaStreamSynchronize(st));
-  const int s = kop_sync(op, stream);
+  const int s = kop_sync(op, (void*)st);
   if (s != KOP_OK) return s;
   *dLdlam = -h[0];
   *dLdbw = -h[1];
+  return rc;
+}
+
+static int adjoint_args(kop_t op, nys_t ny, double lam, double tol, int32_t maxit, int32_t refine_every,
+                        int32_t inner_mode, int32_t refine_mode, int32_t check_mode, const char* where) {
+  const std::string w(where);
+  if (ny && ny->op != op) return fail(KOP_EINVAL, w + ": preconditioner built for another operator");
+  if (!(lam > 0.0) || !std::isfinite(lam)) return fail(KOP_EINVAL, w + ": lam must be > 0");
+  if (!(tol > 0.0) || maxit < 1 || refine_every < 0) return fail(KOP_EINVAL, w + ": bad tol / maxit");
+  if (!valid_mode(inner_mode) || !valid_mode(refine_mode) || !valid_mode(check_mode))
+    return fail(KOP_EINVAL, w + ": bad mode");
+  return KOP_OK;
+}
+
+}  // namespace kop
+
+extern "C" int pcg_adjoint(kop_t op, nys_t ny, double lam, int32_t adaptive, const double* x, const double* dLdx,
+                           double tol, int32_t maxit, int32_t refine_every, int32_t inner_mode, int32_t refine_mode,
+                           int32_t check_mode, double* g_out, int32_t* iters, double* dLdlam, double* dLdbw,
+                           void* stream) {
+  if (!op || !x || !dLdx || !g_out || !dLdlam || !dLdbw) return fail(KOP_EINVAL, "pcg_adjoint: NULL argument");
+  if (int rc = adjoint_args(op, ny, lam, tol, maxit, refine_every, inner_mode, refine_mode, check_mode,
+                            "pcg_adjoint"))
+    return rc;
+  return adjoint_core(op, ny, lam, adaptive, x, dLdx, tol, maxit, refine_every, inner_mode, refine_mode, check_mode,
+                      g_out, iters, dLdlam, dLdbw, (cudaStream_t)stream);
+}
+
+extern "C" int pcg_adjoint_val(kop_t op, nys_t ny, double lam, int32_t adaptive, const double* x,
+                               const float* Xval, int64_t nval, const float* yval, double tol, int32_t maxit,
+                               int32_t refine_every, int32_t inner_mode, int32_t refine_mode, int32_t check_mode,
+                               double* g_out, int32_t* iters, double* loss, double* dLdlam, double* dLdbw,
+                               void* stream) {
+  if (!op || !x || !Xval || !yval || !g_out || !loss || !dLdlam || !dLdbw)
+    return fail(KOP_EINVAL, "pcg_adjoint_val: NULL argument");
+  if (op->ridge) return fail(KOP_EINVAL, "pcg_adjoint_val: not defined for a ridge (X^T X) operator");
+  if (nval < 1 || nval >= (int64_t(1) << 31)) return fail(KOP_EINVAL, "pcg_adjoint_val: nval must be in [1, 2^31)");
+  if (int rc = adjoint_args(op, ny, lam, tol, maxit, refine_every, inner_mode, refine_mode, check_mode,
+                            "pcg_adjoint_val"))
+    return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = op->pts.n;
+  const int kf = op->kernel;
+  const double s2 = 2.0 / (double)nval;
+  PointSet zs;  // the validation points, centred with the operator's mean
+  int rc = pointset_alloc(zs, nval, op->pts.d, st);
+  if (rc) return rc;
+  struct Free {
+    PointSet* z;
+    cudaStream_t st;
+    ~Free() { pointset_free(*z, st); }
+  } free_zs{&zs, st};
+  if ((rc = pointset_fill(zs, Xval, op->mean, st))) return rc;
+  Workspace ws;
+  ws.st = st;
+  // e (nval), t64v (nval), dLdx (n), t64 (n) doubles | split (2 max(n, nval)), tv2 (2 nval), tn2 (2 n) floats,
+  // acc (2) doubles
+  const size_t nm = (size_t)(n > nval ? n : nval);
+  KOP_CUDA_TRY(cudaMallocAsync(&ws.p, sizeof(double) * (2 * (size_t)nval + 2 * (size_t)n + 2) +
+                                          sizeof(float) * (2 * nm + 2 * (size_t)nval + 2 * (size_t)n) + 64, st));
+  double* e = (double*)ws.p;
+  double* t64v = e + nval;
+  double* dLdx = t64v + nval;
+  double* t64 = dLdx + n;
+  double* acc = t64 + n;
+  float* split = (float*)(acc + 2);
+  float* tv2 = split + 2 * nm;
+  float* tn2 = tv2 + 2 * nval;
+  const unsigned bv = (unsigned)((nval + 255) / 256), bn = (unsigned)((n + 255) / 256);
+  // e = K(Xval, X) x - yval, loss = e^T e / nval
+  if ((rc = cross_apply64(op, zs, op->pts, false, kf, check_mode, x, split, tv2, t64v, st))) return rc;
+  if (check_mode == KOP_EXACT)
+    residual64_split_kernel<<<bv, 256, 0, st>>>(t64v, yval, nval, e, split);
+  else
+    residual_split_kernel<<<bv, 256, 0, st>>>(tv2, yval, nval, e, split);
+  KOP_LAUNCHED();
+  KOP_CUDA_TRY(cudaMemsetAsync(acc, 0, 2 * sizeof(double), st));
+  dot64_kernel<<<4 * num_sms(), 256, 0, st>>>(e, e, nval, acc);
+  KOP_LAUNCHED();
+  // dL/dx = (2 / nval) K(X, Xval) e, from e's exact split (already in `split`)
+  if (check_mode == KOP_EXACT) {
+    if ((rc = exact_matvec(op->pts, zs, kf, op->bw, e, 1, 1, dLdx, 1, st))) return rc;
+    scale64_kernel<<<bn, 256, 0, st>>>(dLdx, n, s2);
+  } else {
+    const KConst kc = kernel_constants(kf, op->bw);
+    const int m2 = check_mode == KOP_PLAIN ? KOP_PLAIN_CHECK : check_mode;
+    if ((rc = op_matvec(op->pts, zs, false, kf, kc, m2, split, 2, 2, tn2, 2, op->status, st))) return rc;
+    combine2_kernel<<<bn, 256, 0, st>>>(tn2, n, s2, dLdx);
+  }
+  KOP_LAUNCHED();
+  // validation term of dL/dbw: (2 / nval) e^T (dK(Xval, X)/dbw) x
+  if ((rc = cross_apply64(op, zs, op->pts, false, kf + 3, check_mode, x, split, tv2, t64v, st)))
+    return rc;
+  if (check_mode == KOP_EXACT)
+    dot64_kernel<<<4 * num_sms(), 256, 0, st>>>(e, t64v, nval, acc + 1);
+  else
+    dot_kernel<<<4 * num_sms(), 256, 0, st>>>(e, tv2, tv2 + 1, nval, 2, acc + 1);
+  KOP_LAUNCHED();
+  double h[2];
+  KOP_CUDA_TRY(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, st));
+  KOP_CUDA_TRY(cudaStreamSynchronize(st));
+  double dlam = 0.0, dbw_k = 0.0;
+  rc = adjoint_core(op, ny, lam, adaptive, x, dLdx, tol, maxit, refine_every, inner_mode, refine_mode, check_mode,
+                    g_out, iters, &dlam, &dbw_k, st);
+  if (rc < 0) return rc;
+  *loss = h[0] / (double)nval;
+  *dLdlam = dlam;
+  *dLdbw = s2 * h[1] + dbw_k;
   return rc;
 }

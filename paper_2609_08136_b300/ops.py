@@ -387,61 +387,94 @@ def solve_grad_points(op: KernelOperator, x: torch.Tensor, g: torch.Tensor, mode
 
 
 class NysADMMLinearSolver:
-    """The linear solve inside NysADMM (ADMMConfig, App. A.4): the k-th call
-    solves (A + (rho + sigma) I) x = rhs (A the operator: X^T X or K) to the
-    relative tolerance max(tol_min, k^-gamma), warm-started from the previous
-    call's x, with one Nystrom preconditioner of A (damping rho + sigma)
-    rebuilt every `update_freq` calls from the test matrix Omega.  The paper
-    lists sigma, gamma and preconditioner_update_freq without the formulas;
-    the tolerance schedule above is this library's reading of gamma."""
+    """The linear solve inside NysADMM (ADMMConfig, App. A.4) through the
+    library's admm_create / admm_solve: the k-th call solves
+    (A + (rho + sigma) I) x = rhs to the relative tolerance max(tol_min, k^-gamma),
+    warm-started from the previous call's x, with one Nystrom preconditioner of
+    A (damping rho + sigma) rebuilt every `update_freq` calls from Omega."""
 
     def __init__(self, op: KernelOperator, Omega: torch.Tensor, update_freq: int = 20, sigma: float = 1e-6,
-                 gamma: float = 1.2, tol_min: float = 1e-8, maxit: int = 1000, nys_mode: int = FAST, **pcg_kw):
-        self.op, self.Omega = op, Omega
-        self.update_freq, self.sigma, self.gamma, self.tol_min, self.maxit = update_freq, sigma, gamma, tol_min, maxit
-        self.nys_mode, self.pcg_kw = nys_mode, pcg_kw
+                 gamma: float = 1.2, tol_min: float = 1e-8, maxit: int = 1000, nys_mode: int = FAST,
+                 refine_every: int = 30, inner_mode: int = FAST, refine_mode: int = PLAIN, check_mode: int = PLAIN,
+                 stream=None):
+        Om = _dev_f32(Omega, "Omega")
+        if Om.shape[0] != op.n:
+            raise ValueError("Omega must have n rows")
+        self.op = op
+        self.device = Om.device
+        h = ctypes.c_void_p()
+        check(_ffi.lib().admm_create(op.handle, _ptr(Om), Om.shape[1], int(update_freq), float(sigma), float(gamma),
+                                     float(tol_min), int(maxit), int(refine_every), int(nys_mode), int(inner_mode),
+                                     int(refine_mode), int(check_mode), _stream(stream), ctypes.byref(h)),
+              "admm_create")
+        self._h = h
         self.k = 0
         self.builds = 0
-        self.nys = None
         self.x = None
         self.last = None
 
-    def solve(self, rhs: torch.Tensor, rho: float) -> torch.Tensor:
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _ffi.lib().admm_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, rhs: torch.Tensor, rho: float, stream=None) -> torch.Tensor:
+        r = _dev_f32(rhs.reshape(-1), "rhs")
+        x = torch.empty(self.op.n, dtype=torch.float64, device=self.device)
+        it, tr, tol, rb = ctypes.c_int32(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+        rc = check(_ffi.lib().admm_solve(self._h, _ptr(r), float(rho), _ptr(x), ctypes.byref(it), ctypes.byref(tr),
+                                         ctypes.byref(tol), ctypes.byref(rb), _stream(stream)), "admm_solve")
         self.k += 1
-        if self.nys is None or (self.update_freq > 0 and (self.k - 1) % self.update_freq == 0):
-            if self.nys is not None:
-                self.nys.close()
-            self.nys = Nystrom(self.op, self.Omega, mode=self.nys_mode)
-            self.builds += 1
-        shift = float(rho) + self.sigma
-        tol = max(self.tol_min, float(self.k) ** -self.gamma)
-        res = pcg_solve(self.op, rhs, [shift], nys=self.nys, tol=tol, maxit=self.maxit,
-                        x0=self.x.reshape(-1, 1) if self.x is not None else None, **self.pcg_kw)
-        self.x = res.x.reshape(-1)
-        self.last = res
-        return self.x
+        self.builds += int(rb.value)
+        self.x = x
+        self.last = SolveResult(x, [it.value], None, [tr.value], rc)
+        self.last.tol = tol.value
+        return x
+
+
+def pcg_adjoint_val(op: KernelOperator, x: torch.Tensor, Xv: torch.Tensor, yv: torch.Tensor, lam: float,
+                    nys: Nystrom | None = None, adaptive: bool = True, tol: float = 1e-6, maxit: int = 1000,
+                    refine_every: int = 30, inner_mode: int = FAST, refine_mode: int = PLAIN, check_mode: int = PLAIN,
+                    stream=None):
+    """Validation loss L = (1/n_val) ||K(Xv, X) x - yv||^2 of a solution x of
+    (K + lam I) x = y (FP64 device vector) and its derivatives, all in the
+    library (pcg_adjoint_val).  Returns (loss, dL/dbw, dL/dlam, g = dL/dy, iters)."""
+    x2 = x.detach().reshape(-1).to(torch.float64).contiguous()
+    Xv2 = _dev_f32(Xv, "Xv")
+    yv2 = _dev_f32(yv.reshape(-1), "yv")
+    if not x2.is_cuda or x2.shape[0] != op.n:
+        raise ValueError("x must be a CUDA vector of n entries")
+    if Xv2.shape[1] != op.d or yv2.shape[0] != Xv2.shape[0]:
+        raise ValueError("Xv must be n_val x d and yv must have n_val entries")
+    g = torch.empty_like(x2)
+    it = ctypes.c_int32()
+    loss, dl, db = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    rc = check(_ffi.lib().pcg_adjoint_val(op.handle, nys.handle if nys is not None else None, float(lam),
+                                          int(bool(adaptive)), _ptr(x2), _ptr(Xv2), Xv2.shape[0], _ptr(yv2),
+                                          float(tol), int(maxit), int(refine_every), int(inner_mode),
+                                          int(refine_mode), int(check_mode), _ptr(g), ctypes.byref(it),
+                                          ctypes.byref(loss), ctypes.byref(dl), ctypes.byref(db), _stream(stream)),
+               "pcg_adjoint_val")
+    _warn_unconverged(rc, "pcg_adjoint_val")
+    return loss.value, db.value, dl.value, g, it.value
 
 
 def krr_val_loss_and_grad(op: KernelOperator, nys: Nystrom | None, y: torch.Tensor, Xv: torch.Tensor,
                           yv: torch.Tensor, lam: float, tol: float = 1e-6, maxit: int = 1000, refine_every: int = 30,
-                          inner_mode: int = FAST, refine_mode: int = PLAIN, check_mode: int = PLAIN):
+                          inner_mode: int = FAST, refine_mode: int = PLAIN, check_mode: int = PLAIN, stream=None):
     """Validation loss L = (1/n_val) ||K(Xv, X) x - yv||^2 with x = (K + lam I)^{-1} y,
-    and its derivatives with respect to the bandwidth and lam (adjoint method)."""
-    res = pcg_solve(op, y, [lam], nys=nys, tol=tol, maxit=maxit, refine_every=refine_every, inner_mode=inner_mode,
-                    refine_mode=refine_mode, check_mode=check_mode)
-    x = res.x.reshape(-1)
-    # products with the FP64 x go through its exact two-column FP32 split
-    x_hi = x.float()
-    x2 = torch.stack([x_hi, (x - x_hi.double()).float()], dim=1).contiguous()
-    nv = Xv.shape[0]
-    kx = op.cross_matvec(Xv, x2, mode=check_mode).double().sum(dim=1)
-    e64 = kx - yv.reshape(-1).double()
-    loss = float(e64 @ e64) / nv
-    e_hi = e64.float()
-    e2 = torch.stack([e_hi, (e64 - e_hi.double()).float()], dim=1).contiguous()
-    dLdx = op.cross_matvec(Xv, e2, transpose=True, mode=check_mode).double().sum(dim=1) * (2.0 / nv)
-    g, dlam, dbw_k, _ = pcg_adjoint(op, x, dLdx, lam, nys=nys, tol=tol, maxit=maxit, refine_every=refine_every,
-                                    inner_mode=inner_mode, refine_mode=refine_mode, check_mode=check_mode)
-    dkv = op.cross_matvec(Xv, x2, deriv=True, mode=check_mode).double().sum(dim=1)
-    dbw = (2.0 / nv) * float(e64 @ dkv) + dbw_k
+    and its derivatives with respect to the bandwidth and lam: pcg_solve, then
+    pcg_adjoint_val (the loss, the adjoint solve and both derivatives in the
+    library).  Returns (loss, dL/dbw, dL/dlam)."""
+    kw = dict(tol=tol, maxit=maxit, refine_every=refine_every, inner_mode=inner_mode, refine_mode=refine_mode,
+              check_mode=check_mode)
+    res = pcg_solve(op, y, [lam], nys=nys, stream=stream, **kw)
+    _warn_unconverged(res.status, "krr_val_loss_and_grad")
+    loss, dbw, dlam, _, _ = pcg_adjoint_val(op, res.x, Xv, yv, lam, nys=nys, stream=stream, **kw)
     return loss, dbw, dlam

@@ -72,3 +72,16 @@ def test_check_cache_rejects_null_handle_without_gpu():
     lib = _ffi.lib()
     assert lib.kop_set_check_cache(None, 1, None, 0) == -1
     assert b"NULL" in lib.kop_last_error()
+
+
+def test_adjoint_val_and_admm_reject_bad_arguments_without_gpu():
+    import ctypes
+    lib = _ffi.lib()
+    d = ctypes.c_double()
+    assert lib.pcg_adjoint_val(None, None, 1.0, 1, None, None, 10, None, 1e-6, 10, 0, 0, 2, 2, None, None,
+                               ctypes.byref(d), ctypes.byref(d), ctypes.byref(d), None) == -1
+    assert b"NULL" in lib.kop_last_error()
+    h = ctypes.c_void_p()
+    assert lib.admm_create(None, None, 8, 1, 0.0, 1.0, 1e-8, 10, 0, 0, 0, 2, 2, None, ctypes.byref(h)) == -1
+    assert lib.admm_solve(None, None, 1.0, None, None, None, None, None, None) == -1
+    assert lib.admm_destroy(None) == 0

@@ -97,3 +97,35 @@ def test_cross_and_derivative_parity(kind, mode):
     got = op.dbw_matvec(torch.from_numpy(Vn).cuda(), mode=mode).cpu().numpy()
     assert _rel_err(kind, X, X, Vn, bw, got, deriv=True) < 2 * TOL[mode]
     op.sync()
+
+
+def _sampled_rel_err(kind, X, V, bw, got, rows):
+    # element-wise on sampled output rows, against the FP64 host oracle; the
+    # kernels are positive, so sum_j |K_ij| |V_jc| = (K |V|)_ic
+    from oracle import cmatvec
+    V64 = V.astype(np.float64)
+    ref = cmatvec.kernel_matvec(_KIND[kind], X, V64, bw, Z=X[rows])
+    scale = cmatvec.kernel_matvec(_KIND[kind], X, np.abs(V64), bw, Z=X[rows]) + 1e-300
+    return np.max(np.abs(got[rows].astype(np.float64) - ref) / scale)
+
+
+_KIND = {ops.RBF: O.RBF, ops.LAPLACE: O.LAPLACE, ops.MATERN52: O.MATERN52}
+
+
+# many column chunks of the tensor-core contraction (chunks of <= 256 columns:
+# m = 500 and 1024 run 2 and 4 chunks on grid.y) and row blocks that take
+# more than one wave of the one-CTA-per-SM grid (n = 40000: 313 row blocks)
+@pytest.mark.parametrize("kind", [ops.RBF, ops.LAPLACE, ops.MATERN52])
+@pytest.mark.parametrize("n,d,m,mode", [
+    (3000, 64, 256, ops.FAST), (3001, 64, 500, ops.FAST), (2500, 16, 1024, ops.FAST), (20000, 32, 500, ops.FAST),
+    (40000, 64, 1, ops.FAST), (40000, 64, 1, ops.ACCURATE), (40000, 64, 2, ops.PLAIN), (40001, 16, 8, ops.FAST),
+])
+def test_matvec_parity_wide_blocks_and_many_waves(n, d, m, mode, kind):
+    X = W.random_points(n, d, seed=n + d + m, scale=1.0, shift=1.0)
+    V = W.random_block(n, m, seed=3 * n + m)
+    bw = float(np.sqrt(d)) * (0.8 if kind == ops.RBF else 1.5)
+    op = ops.KernelOperator(torch.from_numpy(X).cuda(), kind, bw)
+    got = op.matvec(torch.from_numpy(V).cuda(), mode=mode).cpu().numpy()
+    op.sync()
+    rows = np.unique(np.concatenate([np.arange(0, n, max(1, n // 200)), [n - 1]]))
+    assert _sampled_rel_err(kind, X, V, bw, got, rows) < TOL[mode]
