@@ -10,12 +10,6 @@
 
 namespace kop {
 
-KOP_DEV float rsqrt_approx(float x) {
-  float y;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
 template <int OP>
 __global__ void __launch_bounds__(512) sfu_probe_kernel(float* out, int iters) {
   float v[16];

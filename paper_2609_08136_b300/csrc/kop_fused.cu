@@ -511,6 +511,18 @@ int fused_matvec(const PointSet& Q, const PointSet& Ks, bool self, int kf, const
   int rc = ensure_scaled_norms(const_cast<PointSet&>(Q), kc.scale, st);
   if (rc == KOP_OK && &Q != &Ks) rc = ensure_scaled_norms(const_cast<PointSet&>(Ks), kc.scale, st);
   if (rc) return rc;
+  if (self && &Q == &Ks && m == 1 && nsplit == 2) {
+    // one vector with the point set itself: each pair of row blocks once
+    if (ldv == 1 && ((uintptr_t)V % 16 == 0) && (Ks.n % 4 == 0))
+      return fused_matvec_sym(const_cast<PointSet&>(Q), kf, kc, V, 0, O, status, st);
+    float* vp = nullptr;
+    KOP_CUDA_TRY(cudaMallocAsync((void**)&vp, sizeof(float) * Ks.n_pad, st));
+    vpad_kernel<<<(unsigned)((Ks.n_pad + 255) / 256), 256, 0, st>>>(V, Ks.n, 1, ldv, Ks.n_pad, 1, vp);
+    KOP_LAUNCHED();
+    rc = fused_matvec_sym(const_cast<PointSet&>(Q), kf, kc, vp, 1, O, status, st);
+    cudaFreeAsync(vp, st);
+    return rc;
+  }
   FusedArgs a;
   a.qnorm = Q.snorm;
   a.knorm = Ks.snorm;

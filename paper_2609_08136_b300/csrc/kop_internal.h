@@ -43,6 +43,9 @@ struct PointSet {
   float* xorig = nullptr;  // the caller's points, n x d FP32 (exact operator)
   float* snorm = nullptr;  // scale * norms (n_pad), built on demand
   float snorm_scale = 0.0f;
+  // column parts of the symmetric single-vector product (built on demand)
+  float* sym_scratch = nullptr;
+  size_t sym_scratch_floats = 0;
 };
 // Make ps.snorm = scale * ps.norms (no-op if already built for this scale).
 int ensure_scaled_norms(PointSet& ps, float scale, cudaStream_t st);
@@ -61,6 +64,10 @@ int column_mean(const float* X, int64_t n, int d, double* mean, cudaStream_t st)
 int fused_matvec(const PointSet& Q, const PointSet& Ks, bool self, int kf, const KConst& kc, int nsplit,
                  const float* V, int m, int ldv, float* O, int ldo, int* status, cudaStream_t st,
                  bool v_bf16_exact = false);
+// Single-vector product of a point set with itself using the symmetry of K
+// (2-term split): v holds n floats (n_pad when v_padded), 16-byte aligned.
+int fused_matvec_sym(PointSet& P, int kf, const KConst& kc, const float* v, int v_padded, float* O, int* status,
+                     cudaStream_t st);
 // Tensor-core contraction variant for m > 8 (2-term split only).
 // v_bf16_exact: V holds BF16-representable values, so its lo split is zero.
 int fused_matvec_mma(const PointSet& Q, const PointSet& Ks, bool self, int kf, const KConst& kc, const float* V,

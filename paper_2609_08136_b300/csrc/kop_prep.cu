@@ -175,6 +175,9 @@ int pointset_alloc(PointSet& ps, int64_t n, int d, cudaStream_t st) {
 void pointset_free(PointSet& ps, cudaStream_t st) {
   if (ps.block) cudaFreeAsync(ps.block, st);
   if (ps.snorm) cudaFreeAsync(ps.snorm, st);
+  if (ps.sym_scratch) cudaFreeAsync(ps.sym_scratch, st);
+  ps.sym_scratch = nullptr;
+  ps.sym_scratch_floats = 0;
   ps.snorm = nullptr;
   ps.snorm_scale = 0.0f;
   ps.block = nullptr;

@@ -65,6 +65,22 @@ def test_exact_fp64_operator(n, d, m, kind):
     assert _rel_err(kind, X, X, V.astype(np.float32), bw, got32) < 1e-6
 
 
+@pytest.mark.parametrize("n", [1, 200, 385, 1000])
+def test_single_column_product_diagonal_is_exact(n):
+    # the single-vector FAST product takes each pair of row blocks once (both
+    # contributions of a tile from one evaluation): a unit vector e_j gives
+    # K[:, j], whose diagonal entry is exactly 1
+    X = W.random_points(n, 16, seed=n)
+    op = ops.KernelOperator(torch.from_numpy(X).cuda(), ops.LAPLACE, 4.0)
+    K = O.kernel_matrix(O.LAPLACE, X, X, 4.0)
+    for j in sorted({0, n // 3, n - 1}):
+        e = np.zeros((n, 1), dtype=np.float32)
+        e[j, 0] = 1.0
+        got = op.matvec(torch.from_numpy(e).cuda(), mode=ops.FAST).cpu().numpy()[:, 0]
+        assert got[j] == 1.0
+        assert np.max(np.abs(got - K[:, j])) < 3e-4
+
+
 @pytest.mark.parametrize("mode", [ops.FAST, ops.ACCURATE])
 def test_diagonal_is_exact(mode):
     n, d = 200, 64
@@ -119,6 +135,7 @@ _KIND = {ops.RBF: O.RBF, ops.LAPLACE: O.LAPLACE, ops.MATERN52: O.MATERN52}
 @pytest.mark.parametrize("n,d,m,mode", [
     (3000, 64, 256, ops.FAST), (3001, 64, 500, ops.FAST), (2500, 16, 1024, ops.FAST), (20000, 32, 500, ops.FAST),
     (40000, 64, 1, ops.FAST), (40000, 64, 1, ops.ACCURATE), (40000, 64, 2, ops.PLAIN), (40001, 16, 8, ops.FAST),
+    (38400, 64, 1, ops.FAST), (30001, 32, 1, ops.FAST), (12345, 128, 1, ops.FAST),
 ])
 def test_matvec_parity_wide_blocks_and_many_waves(n, d, m, mode, kind):
     X = W.random_points(n, d, seed=n + d + m, scale=1.0, shift=1.0)
