@@ -84,6 +84,10 @@ int exact_matvec(const PointSet& Q, const PointSet& Ks, int kf, double bw, const
                  int ldo, cudaStream_t st);
 int exact_matvec_f32(const PointSet& Q, const PointSet& Ks, int kf, double bw, const float* V, int m, int ldv,
                      float* O, int ldo, cudaStream_t st);
+// The same FP64 product (kernels k only) with error-free FP32 distances:
+// for few query rows (the certification of the solver's stops).
+int cert_matvec(const PointSet& Q, const PointSet& Ks, int kf, double bw, const double* V, int m, int ldv, double* O,
+                int ldo, cudaStream_t st);
 // Any mode.
 int op_matvec(const PointSet& Q, const PointSet& Ks, bool self, int kf, const KConst& kc, int mode,
               const float* V, int m, int ldv, float* O, int ldo, int* status, cudaStream_t st,

@@ -497,7 +497,7 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
       if (op->ridge) {
         if ((rc = op_apply_f64(op, X, cols, cols, O64, cols, st))) return rc;
       } else {
-        if ((rc = exact_matvec(qs, op->pts, op->kernel, op->bw, X, cols, cols, O64, cols, st))) return rc;
+        if ((rc = cert_matvec(qs, op->pts, op->kernel, op->bw, X, cols, cols, O64, cols, st))) return rc;
       }
       KOP_CUDA_TRY(cudaMemsetAsync(csd, 0, sizeof(double) * 2 * cols, st));
       const unsigned gy = (unsigned)((cols + 31) / 32);

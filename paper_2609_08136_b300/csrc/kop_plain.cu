@@ -65,8 +65,10 @@ KOP_DEV float plain_kernel_value(float d2, const PlainConst& p) {
 
 // Kst != NULL: the column block 0 also stores every kernel value it computes,
 // Kst[i * ldk + j] for the rows i < nq and all keys of its tiles (0 for the
-// padding keys j >= nk); ldk a multiple of 4.
-template <int KF, int MV, bool COMP>
+// padding keys j >= nk); ldk a multiple of 4.  BUILD: only store, for the keys
+// j >= the block's first row (the upper block triangle of a symmetric K; the
+// rest is mirrored afterwards), with no contraction and no output.
+template <int KF, int MV, bool COMP, bool BUILD = false>
 __global__ void __launch_bounds__(K2_ROWS) k2_plain_kernel(const float* __restrict__ Q, const float* __restrict__ Xk,
                                                            const float* __restrict__ V, float* __restrict__ O, int nq,
                                                            int nk, int dp, int m, int ldv, int ldo, PlainConst pc,
@@ -88,12 +90,14 @@ __global__ void __launch_bounds__(K2_ROWS) k2_plain_kernel(const float* __restri
   float acc_s[MV], acc_e[MV];
 #pragma unroll
   for (int c = 0; c < MV; ++c) acc_s[c] = acc_e[c] = 0.0f;
-  for (int j0 = 0; j0 < nk; j0 += K2_KEYS) {
+  for (int j0 = BUILD ? row0 : 0; j0 < nk; j0 += K2_KEYS) {
     __syncthreads();
     for (int idx = tid; idx < K2_KEYS * dp; idx += K2_ROWS) Xs[idx] = Xk[(int64_t)j0 * dp + idx];
-    for (int idx = tid; idx < K2_KEYS * MV; idx += K2_ROWS) {
-      const int jj = idx / MV, c = idx - jj * MV, j = j0 + jj;
-      Vs[idx] = (j < nk && c < mc) ? V[(int64_t)j * ldv + col0 + c] : 0.0f;
+    if constexpr (!BUILD) {
+      for (int idx = tid; idx < K2_KEYS * MV; idx += K2_ROWS) {
+        const int jj = idx / MV, c = idx - jj * MV, j = j0 + jj;
+        Vs[idx] = (j < nk && c < mc) ? V[(int64_t)j * ldv + col0 + c] : 0.0f;
+      }
     }
     __syncthreads();
     uint64_t d2p[K2_KEYS];  // (sum over even features, sum over odd features)
@@ -138,6 +142,7 @@ __global__ void __launch_bounds__(K2_ROWS) k2_plain_kernel(const float* __restri
                         j + 2 < nk ? d2[j4 + 2] : 0.0f, j + 3 < nk ? d2[j4 + 3] : 0.0f);
       }
     }
+    if constexpr (BUILD) continue;
 #pragma unroll
     for (int jj = 0; jj < K2_KEYS; ++jj) {
       const float kv = d2[jj];
@@ -162,10 +167,29 @@ __global__ void __launch_bounds__(K2_ROWS) k2_plain_kernel(const float* __restri
       acc_e[c] += perr[c];
     }
   }
-  if (gi < nq) {
+  if (!BUILD && gi < nq) {
 #pragma unroll
     for (int c = 0; c < MV; ++c)
       if (c < mc) O[(int64_t)gi * ldo + col0 + c] = acc_s[c] + acc_e[c];
+  }
+}
+
+// The lower block triangle of the stored symmetric K from the upper one:
+// Kc[i][j] = Kc[j][i] for the keys j below the first row of i's 128-row block
+// (32 x 32 tiles through shared memory; rows i < n, keys j < n).
+__global__ void __launch_bounds__(256) kcache_mirror_kernel(float* __restrict__ Kc, int64_t ldk, int n) {
+  __shared__ float tile[32][33];
+  const int ti = blockIdx.y * 32, tj = blockIdx.x * 32;  // destination rows ti.., keys tj..
+  if (tj >= (ti / K2_ROWS) * K2_ROWS) return;         // on or above the block diagonal: computed
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  for (int r = ty; r < 32; r += 8) {
+    const int src_row = tj + r, src_col = ti + tx;  // Kc[tj + r][ti + tx]
+    tile[r][tx] = (src_row < n && src_col < n) ? Kc[(int64_t)src_row * ldk + src_col] : 0.0f;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int row = ti + r, col = tj + tx;
+    if (row < n && col < n) Kc[(int64_t)row * ldk + col] = tile[tx][r];
   }
 }
 
@@ -347,11 +371,45 @@ int check_cache_reserve(kop_s* op) {
   return KOP_OK;
 }
 
+template <int KF>
+static int launch_build_t(const PointSet& P, const PlainConst& pc, float* Kc, int64_t ldk, cudaStream_t st) {
+  auto kern = k2_plain_kernel<KF, 1, true, true>;
+  const int dp = P.dp;
+  const size_t smem = sizeof(float) * ((size_t)dp * (K2_ROWS + 1) + (size_t)K2_KEYS * dp + K2_KEYS * 1);
+  static bool attr_set = false;
+  if (!attr_set) {
+    KOP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_limit_bytes()));
+    attr_set = true;
+  }
+  dim3 grid((unsigned)((P.n + K2_ROWS - 1) / K2_ROWS), 1);
+  kern<<<grid, K2_ROWS, smem, st>>>(P.xc, P.xc, nullptr, nullptr, (int)P.n, (int)P.n, dp, 1, 1, 1, pc, Kc, ldk);
+  KOP_LAUNCHED();
+  return KOP_OK;
+}
+
+// Store the direct-difference K(X, X) in op->kc: the upper block triangle
+// (each pair of row blocks once), then its mirror image.
+static int check_cache_build(kop_s* op, cudaStream_t st) {
+  const PlainConst pc = plain_constants(op->kernel, op->bw);
+  int rc;
+  switch (op->kernel) {
+    case KF_RBF: rc = launch_build_t<KF_RBF>(op->pts, pc, op->kc, op->kc_ld, st); break;
+    case KF_LAPLACE: rc = launch_build_t<KF_LAPLACE>(op->pts, pc, op->kc, op->kc_ld, st); break;
+    default: rc = launch_build_t<KF_MATERN>(op->pts, pc, op->kc, op->kc_ld, st); break;
+  }
+  if (rc) return rc;
+  const int n = (int)op->pts.n;
+  const unsigned t = (unsigned)((n + 31) / 32);
+  kcache_mirror_kernel<<<dim3(t, t), 256, 0, st>>>(op->kc, op->kc_ld, n);
+  KOP_LAUNCHED();
+  return KOP_OK;
+}
+
 int check_matvec_cached(kop_s* op, bool build, const float* V, int m, int ldv, float* O, int ldo, cudaStream_t st) {
   const int n = (int)op->pts.n;
   if (build) {
-    const PlainConst pc = plain_constants(op->kernel, op->bw);
-    return plain_dispatch<true>(op->kernel, op->pts, op->pts, V, m, ldv, O, ldo, pc, st, op->kc, op->kc_ld);
+    const int rc = check_cache_build(op, st);
+    if (rc) return rc;
   }
   if (m == 1) kcache_launch<1>(op->kc, op->kc_ld, n, n, V, m, ldv, O, ldo, st);
   else if (m == 2) kcache_launch<2>(op->kc, op->kc_ld, n, n, V, m, ldv, O, ldo, st);
