@@ -88,8 +88,10 @@ int64_t kop_launch_count(void);
 /* Measured SFU throughput of the current device, in operations per second:
  * rates[0] = ex2.approx, rates[1] = sqrt.approx, rates[2] = rsqrt.approx
  * (host array of 3).  The m = 1 operator product is bound by these units, so
- * they are the denominators of its roofline.  Runs three short probe kernels
- * on `stream` and synchronizes it.  Not in the paper: a measurement helper. */
+ * they are the denominators of its roofline.  Runs each of three short probe
+ * kernels four times on `stream` (the first warms up; the fastest of the
+ * others gives the rate) and synchronizes it.  Not in the paper: a
+ * measurement helper. */
 int kop_sfu_rates(double* rates, void* stream);
 
 /* ---------------------------------------------------------------------------
@@ -119,23 +121,29 @@ int kop_destroy(kop_t op);
 /* Change the bandwidth in place (the points are kept). */
 int kop_set_bandwidth(kop_t op, double bandwidth);
 
-/* Keep the kernel matrix of the solver's checks in device memory: n rows of
- * ld = ceil(n / 128) * 128 FP32 (n^2 * 4 bytes, 160 GB at n = 200000).
- * While it is set, the first product of a pcg_solve / pcg_adjoint call with
- * the check operator KOP_PLAIN_CHECK (refine_mode or check_mode KOP_PLAIN)
- * computes K(X, X) by direct differences as that operator does and stores
- * it, and the call's later check products multiply the stored matrix with
- * the same error-free contraction: about the cost of streaming it once,
- * instead of recomputing n^2 distances.  The stored values serve that one
- * call only; every call recomputes them.  Results equal those without the
- * matrix up to the order of the compensated sums.
+/* Keep the kernel matrix of the solver's checks in device memory.  K is
+ * symmetric, so each pair of 128-point row blocks is stored once: nb x
+ * (floor(nb / 2) + 1) tiles of 128 x 128 FP32, nb = ceil(n / 128) (about
+ * n^2 * 2 bytes, 80 GB at n = 200000).  While it is set, the first product of
+ * a pcg_solve / pcg_adjoint call with the check operator KOP_PLAIN_CHECK
+ * (refine_mode or check_mode KOP_PLAIN) computes those tiles by direct
+ * differences as that operator does and stores them, and every check product
+ * of the call reads each stored tile once for both of its contributions
+ * (K_IJ v_J and K_IJ^T v_I) with the same error-free contraction: about the
+ * cost of streaming half of K, instead of recomputing n^2 distances.  The
+ * stored values serve that one call only; every call recomputes them.
+ * Results equal those without the matrix up to the order of the compensated
+ * sums.  A scratch of nb x floor(nb / 2) x 128 x 16 floats at most (the
+ * column parts as sum / error pairs) is reserved on first use and freed with
+ * the matrix.
  *   enable = 0: stop using it; memory the library reserved is freed (the
  *               device is synchronized first).
  *   enable != 0, buffer = NULL: the library reserves the matrix (kept until
  *               disabled or kop_destroy); KOP_ENOMEM, reserving nothing, when
  *               it and 4 GB of headroom do not fit in the free device memory.
  *   enable != 0, buffer != NULL: the caller's device memory of buffer_floats
- *               >= n * ld floats, 16-byte aligned (KOP_EINVAL otherwise); the
+ *               >= nb * (floor(nb / 2) + 1) * 16384 floats, 16-byte aligned
+ *               (KOP_EINVAL otherwise); the
  *               caller keeps ownership and may free it once the solves that
  *               used it have completed on their streams.
  * Solves on one handle that overlap in time share the matrix: run them one

@@ -93,6 +93,7 @@ extern "C" int kop_destroy(kop_t op) {
   }
   pointset_free(op->pts, 0);
   if (op->kc_owned) cudaFree(op->kc);
+  if (op->kc_scratch) cudaFree(op->kc_scratch);
   cudaFree(op->mean);
   cudaDeviceSynchronize();
   delete op;
@@ -113,7 +114,12 @@ static int check_cache_release(kop_s* op) {
     KOP_CUDA_TRY(cudaFree(op->kc));
   }
   op->kc = nullptr;
-  op->kc_ld = 0;
+  if (op->kc_scratch) {
+    KOP_CUDA_TRY(cudaDeviceSynchronize());
+    KOP_CUDA_TRY(cudaFree(op->kc_scratch));
+  }
+  op->kc_scratch = nullptr;
+  op->kc_scratch_floats = 0;
   op->kc_owned = 0;
   return KOP_OK;
 }
@@ -127,14 +133,12 @@ extern "C" int kop_set_check_cache(kop_t op, int32_t enable, float* buffer, int6
     if (int rc = check_cache_release(op)) return rc;
     return check_cache_reserve(op);
   }
-  const int64_t ld = check_cache_ld(op->pts.n);
-  if (buffer_floats < op->pts.n * ld)
-    return fail(KOP_EINVAL, "kop_set_check_cache: buffer smaller than n * ceil(n / 128) * 128 floats");
+  if (buffer_floats < check_cache_floats(op->pts.n))
+    return fail(KOP_EINVAL, "kop_set_check_cache: buffer smaller than nb * (floor(nb / 2) + 1) * 128^2 floats");
   if (reinterpret_cast<uintptr_t>(buffer) % 16 != 0)
     return fail(KOP_EINVAL, "kop_set_check_cache: buffer not 16-byte aligned");
   if (int rc = check_cache_release(op)) return rc;
   op->kc = buffer;
-  op->kc_ld = ld;
   op->kc_owned = 0;
   return KOP_OK;
 }

@@ -44,8 +44,9 @@ extern "C" int kop_sfu_rates(double* rates, void* stream) {
   KOP_CUDA_TRY(cudaEventCreate(&e1));
   int rc = KOP_OK;
   for (int op = 0; op < 3 && rc == KOP_OK; ++op) {
-    float ms = 0.0f;
-    for (int rep = 0; rep < 2; ++rep) {  // the first pass warms up
+    float best = 0.0f;
+    for (int rep = 0; rep < 4; ++rep) {  // the first pass warms up; the fastest of the others counts
+      float ms = 0.0f;
       cudaEventRecord(e0, st);
       if (op == 0) sfu_probe_kernel<0><<<blocks, threads, 0, st>>>(out, iters);
       else if (op == 1) sfu_probe_kernel<1><<<blocks, threads, 0, st>>>(out, iters);
@@ -57,8 +58,9 @@ extern "C" int kop_sfu_rates(double* rates, void* stream) {
         break;
       }
       cudaEventElapsedTime(&ms, e0, e1);
+      if (rep == 1 || (rep > 1 && ms < best)) best = ms;
     }
-    rates[op] = (double)blocks * threads * iters * 16 / (ms * 1e-3);
+    rates[op] = (double)blocks * threads * iters * 16 / (best * 1e-3);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -73,12 +73,6 @@ struct KSLayout {
     total = abort_word + 4;
   }
 };
-// Tiles of CTA I (the diagonal tile included).
-__host__ __device__ inline int ks_count(int I, int nb) {
-  const int h = nb / 2;
-  if (nb & 1) return h + 1;
-  return I < h ? h + 1 : h;
-}
 
 // Warp-uniform bounded wait; the common case (the phase has completed) costs
 // one try_wait and one vote.
@@ -133,7 +127,7 @@ __global__ void __launch_bounds__(KS_THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int I = blockIdx.x;
   const int row0 = I * 128;
-  const int cnt = ks_count(I, a.nb);
+  const int cnt = sym_band_count(I, a.nb);
   const int rb = a.row_bytes;
   const int nsub = (a.dp * 2) / rb;
   const CUtensorMap* maps[3] = {&tp0, &tp1, &tp2};
@@ -388,7 +382,7 @@ __global__ void sym_combine_kernel(float* __restrict__ O, const float* __restric
   float s = O[j], e = 0.0f;
   for (int t = 1; t <= h; ++t) {
     const int I = J - t >= 0 ? J - t : J - t + nb;
-    if (t < ks_count(I, nb)) two_sum_acc(s, e, C[((int64_t)J * h + (t - 1)) * 128 + jj]);
+    if (t < sym_band_count(I, nb)) two_sum_acc(s, e, C[((int64_t)J * h + (t - 1)) * 128 + jj]);
   }
   O[j] = s + e;
 }

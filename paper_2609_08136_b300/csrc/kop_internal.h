@@ -134,10 +134,13 @@ struct kop_s {
   int64_t rn = 0;       // rows of X
   int rp = 0;           // columns of X: the operator's dimension
   // the stored direct-difference kernel matrix of the solver's checks
-  // (kop_set_check_cache): n x kc_ld FP32, or NULL
+  // (kop_set_check_cache): the 128 x 128 tiles of each row block's band
+  // (sym_band_count), tile-packed FP32, or NULL
   float* kc = nullptr;
-  int64_t kc_ld = 0;
   int kc_owned = 0;  // kc was allocated by the library (else the caller's)
+  // column parts of the symmetric product with the stored matrix (on demand)
+  float* kc_scratch = nullptr;
+  size_t kc_scratch_floats = 0;
 };
 
 namespace kop {
@@ -151,14 +154,32 @@ int op_apply(kop_s* op, int mode, const float* V, int m, int ldv, float* O, int 
 int op_apply_f64(kop_s* op, const double* V, int m, int ldv, double* O, int ldo, cudaStream_t st);
 int ridge_apply(const kop_s* op, int mode, const float* V, int m, int ldv, float* O, int ldo, cudaStream_t st);
 int ridge_apply_f64(const kop_s* op, const double* V, int m, int ldv, double* O, int ldo, cudaStream_t st);
-// Row pitch (floats) of the stored kernel matrix of an n-point operator.
-inline int64_t check_cache_ld(int64_t n) { return (n + 127) / 128 * 128; }
+// The band of block pairs that the symmetric products evaluate: with nb row
+// blocks of 128 points, block I takes the blocks J = I + t (mod nb) for
+// t = 0 .. sym_band_count(I, nb) - 1, which covers every unordered pair once
+// (floor(nb / 2) + 1 blocks; one fewer for I >= nb / 2 when nb is even).
+__host__ __device__ inline int sym_band_count(int I, int nb) {
+  const int h = nb / 2;
+  if (nb & 1) return h + 1;
+  return I < h ? h + 1 : h;
+}
+// Floats of the stored kernel matrix of an n-point operator: nb x
+// (floor(nb / 2) + 1) tiles of 128 x 128 (each pair of row blocks once; the
+// tile of row block I and band position t at (I (floor(nb / 2) + 1) + t) 128^2,
+// row-major within the tile).
+inline int64_t check_cache_floats(int64_t n) {
+  const int64_t nb = (n + 127) / 128;
+  return nb * (nb / 2 + 1) * 128 * 128;
+}
 // Reserve op->kc for the kernel matrix (KOP_ENOMEM when it does not fit).
 int check_cache_reserve(kop_s* op);
 // The compensated direct-difference product (KOP_PLAIN_CHECK) of a kernel
-// operator with op->kc set: build = true computes it by direct differences
-// and stores K in op->kc; build = false multiplies the stored K.
-int check_matvec_cached(kop_s* op, bool build, const float* V, int m, int ldv, float* O, int ldo, cudaStream_t st);
+// operator with op->kc set, for the solver's checks: V2 (n x 2 cols) holds
+// the exact hi / lo FP32 split of cols vectors (columns c and cols + c); T
+// (n x 2 cols) receives each product as an unevaluated (sum, error) pair in
+// the same two columns.  build = true first computes the stored matrix by
+// direct differences.
+int check_matvec_cached(kop_s* op, bool build, const float* V2, int cols, float* T, cudaStream_t st);
 }  // namespace kop
 
 // Stream-ordered device scratch, freed on the same stream when it goes out of scope.

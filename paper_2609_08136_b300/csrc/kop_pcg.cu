@@ -462,7 +462,7 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
   bool kc_built = false;
   auto check2 = [&](int mode) -> int {
     if (mode != KOP_PLAIN_CHECK || op->ridge || !op->kc) return matvec2(V2, T, mode);
-    const int rc2 = check_matvec_cached(op, !kc_built, V2, 2 * cols, 2 * cols, T, 2 * cols, st);
+    const int rc2 = check_matvec_cached(op, !kc_built, V2, cols, T, st);
     if (rc2 == KOP_OK) kc_built = true;
     return rc2;
   };

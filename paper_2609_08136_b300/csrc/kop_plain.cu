@@ -63,16 +63,15 @@ KOP_DEV float plain_kernel_value(float d2, const PlainConst& p) {
   }
 }
 
-// Kst != NULL: the column block 0 also stores every kernel value it computes,
-// Kst[i * ldk + j] for the rows i < nq and all keys of its tiles (0 for the
-// padding keys j >= nk); ldk a multiple of 4.  BUILD: only store, for the keys
-// j >= the block's first row (the upper block triangle of a symmetric K; the
-// rest is mirrored afterwards), with no contraction and no output.
+// BUILD: no contraction and no output; the kernel values of the key blocks
+// of the row block's band (sym_band_count: each pair of blocks of the
+// symmetric K once) are stored into the tile-packed Kst (see
+// check_cache_floats; 0 for the padding keys j >= nk).
 template <int KF, int MV, bool COMP, bool BUILD = false>
 __global__ void __launch_bounds__(K2_ROWS) k2_plain_kernel(const float* __restrict__ Q, const float* __restrict__ Xk,
                                                            const float* __restrict__ V, float* __restrict__ O, int nq,
                                                            int nk, int dp, int m, int ldv, int ldo, PlainConst pc,
-                                                           float* __restrict__ Kst, int64_t ldk) {
+                                                           float* __restrict__ Kst) {
   extern __shared__ float sm[];
   float* Qs = sm;                              // dp x (K2_ROWS + 1), transposed
   float* Xs = Qs + dp * (K2_ROWS + 1);         // K2_KEYS x dp
@@ -82,7 +81,7 @@ __global__ void __launch_bounds__(K2_ROWS) k2_plain_kernel(const float* __restri
   const int col0 = blockIdx.y * MV;
   const int mc = (m - col0) < MV ? (m - col0) : MV;
   const int gi = row0 + tid;
-  float* const krow = (Kst != nullptr && blockIdx.y == 0 && gi < nq) ? Kst + (int64_t)gi * ldk : nullptr;
+  const int hb = (nk + K2_ROWS - 1) / K2_ROWS / 2;  // band positions per row block - 1
   for (int idx = tid; idx < K2_ROWS * dp; idx += K2_ROWS) {
     const int r = idx / dp, k = idx - r * dp;
     Qs[k * (K2_ROWS + 1) + r] = Q[(int64_t)(row0 + r) * dp + k];
@@ -90,7 +89,16 @@ __global__ void __launch_bounds__(K2_ROWS) k2_plain_kernel(const float* __restri
   float acc_s[MV], acc_e[MV];
 #pragma unroll
   for (int c = 0; c < MV; ++c) acc_s[c] = acc_e[c] = 0.0f;
-  for (int j0 = BUILD ? row0 : 0; j0 < nk; j0 += K2_KEYS) {
+  const int nb = (nk + K2_ROWS - 1) / K2_ROWS;
+  const int ntl = BUILD ? sym_band_count(blockIdx.x, nb) * (K2_ROWS / K2_KEYS) : (nk + K2_KEYS - 1) / K2_KEYS;
+  for (int tl = 0; tl < ntl; ++tl) {
+    int j0 = tl * K2_KEYS;
+    if constexpr (BUILD) {
+      // sub-tile tl % 4 of band block I + tl / 4 (mod nb); keys past nk (but
+      // below the padded count) are stored as 0
+      const int J = (int)blockIdx.x + tl / (K2_ROWS / K2_KEYS);
+      j0 = (J < nb ? J : J - nb) * K2_ROWS + (tl % (K2_ROWS / K2_KEYS)) * K2_KEYS;
+    }
     __syncthreads();
     for (int idx = tid; idx < K2_KEYS * dp; idx += K2_ROWS) Xs[idx] = Xk[(int64_t)j0 * dp + idx];
     if constexpr (!BUILD) {
@@ -133,16 +141,20 @@ __global__ void __launch_bounds__(K2_ROWS) k2_plain_kernel(const float* __restri
     // kernel values in place of the distances
 #pragma unroll
     for (int jj = 0; jj < K2_KEYS; ++jj) d2[jj] = plain_kernel_value<KF>(d2[jj], pc);
-    if (krow != nullptr) {
+    if constexpr (BUILD) {
+      // row tid of tile (I, t = tl / 4), columns (tl % 4) * 32 ..
+      if (gi < nq) {
+        float* kd = Kst + (((int64_t)blockIdx.x * (hb + 1) + tl / (K2_ROWS / K2_KEYS)) * K2_ROWS + tid) * K2_ROWS +
+                    (tl % (K2_ROWS / K2_KEYS)) * K2_KEYS;
 #pragma unroll
-      for (int j4 = 0; j4 < K2_KEYS; j4 += 4) {
-        const int j = j0 + j4;
-        *reinterpret_cast<float4*>(krow + j) =
-            make_float4(j + 0 < nk ? d2[j4 + 0] : 0.0f, j + 1 < nk ? d2[j4 + 1] : 0.0f,
-                        j + 2 < nk ? d2[j4 + 2] : 0.0f, j + 3 < nk ? d2[j4 + 3] : 0.0f);
+        for (int j4 = 0; j4 < K2_KEYS; j4 += 4) {
+          const int j = j0 + j4;
+          *reinterpret_cast<float4*>(kd + j4) =
+              make_float4(j + 0 < nk ? d2[j4 + 0] : 0.0f, j + 1 < nk ? d2[j4 + 1] : 0.0f,
+                          j + 2 < nk ? d2[j4 + 2] : 0.0f, j + 3 < nk ? d2[j4 + 3] : 0.0f);
+        }
       }
-    }
-    if constexpr (BUILD) continue;
+    } else {
 #pragma unroll
     for (int jj = 0; jj < K2_KEYS; ++jj) {
       const float kv = d2[jj];
@@ -166,30 +178,12 @@ __global__ void __launch_bounds__(K2_ROWS) k2_plain_kernel(const float* __restri
       two_sum_acc(acc_s[c], acc_e[c], part[c]);
       acc_e[c] += perr[c];
     }
+    }
   }
   if (!BUILD && gi < nq) {
 #pragma unroll
     for (int c = 0; c < MV; ++c)
       if (c < mc) O[(int64_t)gi * ldo + col0 + c] = acc_s[c] + acc_e[c];
-  }
-}
-
-// The lower block triangle of the stored symmetric K from the upper one:
-// Kc[i][j] = Kc[j][i] for the keys j below the first row of i's 128-row block
-// (32 x 32 tiles through shared memory; rows i < n, keys j < n).
-__global__ void __launch_bounds__(256) kcache_mirror_kernel(float* __restrict__ Kc, int64_t ldk, int n) {
-  __shared__ float tile[32][33];
-  const int ti = blockIdx.y * 32, tj = blockIdx.x * 32;  // destination rows ti.., keys tj..
-  if (tj >= (ti / K2_ROWS) * K2_ROWS) return;         // on or above the block diagonal: computed
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
-  for (int r = ty; r < 32; r += 8) {
-    const int src_row = tj + r, src_col = ti + tx;  // Kc[tj + r][ti + tx]
-    tile[r][tx] = (src_row < n && src_col < n) ? Kc[(int64_t)src_row * ldk + src_col] : 0.0f;
-  }
-  __syncthreads();
-  for (int r = ty; r < 32; r += 8) {
-    const int row = ti + r, col = tj + tx;
-    if (row < n && col < n) Kc[(int64_t)row * ldk + col] = tile[tx][r];
   }
 }
 
@@ -216,7 +210,7 @@ static PlainConst plain_constants(int kf, double bw) {
 
 template <int KF, int MV, bool COMP>
 static int launch_plain_t(const PointSet& Q, const PointSet& Ks, const float* V, int m, int ldv, float* O, int ldo,
-                          const PlainConst& pc, cudaStream_t st, float* Kst, int64_t ldk) {
+                          const PlainConst& pc, cudaStream_t st) {
   auto kern = k2_plain_kernel<KF, MV, COMP>;
   const int dp = Q.dp;
   const size_t smem = sizeof(float) * ((size_t)dp * (K2_ROWS + 1) + (size_t)K2_KEYS * dp + K2_KEYS * MV);
@@ -226,30 +220,30 @@ static int launch_plain_t(const PointSet& Q, const PointSet& Ks, const float* V,
     attr_set = true;
   }
   dim3 grid((unsigned)((Q.n + K2_ROWS - 1) / K2_ROWS), (unsigned)((m + MV - 1) / MV));
-  kern<<<grid, K2_ROWS, smem, st>>>(Q.xc, Ks.xc, V, O, (int)Q.n, (int)Ks.n, dp, m, ldv, ldo, pc, Kst, ldk);
+  kern<<<grid, K2_ROWS, smem, st>>>(Q.xc, Ks.xc, V, O, (int)Q.n, (int)Ks.n, dp, m, ldv, ldo, pc, nullptr);
   KOP_LAUNCHED();
   return KOP_OK;
 }
 
 template <int KF, bool COMP>
 static int launch_plain_kf(const PointSet& Q, const PointSet& Ks, const float* V, int m, int ldv, float* O, int ldo,
-                           const PlainConst& pc, cudaStream_t st, float* Kst, int64_t ldk) {
-  if (m == 1) return launch_plain_t<KF, 1, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st, Kst, ldk);
-  if (m == 2) return launch_plain_t<KF, 2, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st, Kst, ldk);
-  if (m <= 4) return launch_plain_t<KF, 4, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st, Kst, ldk);
-  return launch_plain_t<KF, 8, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st, Kst, ldk);
+                           const PlainConst& pc, cudaStream_t st) {
+  if (m == 1) return launch_plain_t<KF, 1, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st);
+  if (m == 2) return launch_plain_t<KF, 2, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st);
+  if (m <= 4) return launch_plain_t<KF, 4, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st);
+  return launch_plain_t<KF, 8, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st);
 }
 
 template <bool COMP>
 static int plain_dispatch(int kf, const PointSet& Q, const PointSet& Ks, const float* V, int m, int ldv, float* O,
-                          int ldo, const PlainConst& pc, cudaStream_t st, float* Kst = nullptr, int64_t ldk = 0) {
+                          int ldo, const PlainConst& pc, cudaStream_t st) {
   switch (kf) {
-    case KF_RBF: return launch_plain_kf<KF_RBF, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st, Kst, ldk);
-    case KF_LAPLACE: return launch_plain_kf<KF_LAPLACE, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st, Kst, ldk);
-    case KF_MATERN: return launch_plain_kf<KF_MATERN, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st, Kst, ldk);
-    case KF_DRBF: return launch_plain_kf<KF_DRBF, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st, Kst, ldk);
-    case KF_DLAPLACE: return launch_plain_kf<KF_DLAPLACE, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st, Kst, ldk);
-    default: return launch_plain_kf<KF_DMATERN, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st, Kst, ldk);
+    case KF_RBF: return launch_plain_kf<KF_RBF, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st);
+    case KF_LAPLACE: return launch_plain_kf<KF_LAPLACE, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st);
+    case KF_MATERN: return launch_plain_kf<KF_MATERN, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st);
+    case KF_DRBF: return launch_plain_kf<KF_DRBF, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st);
+    case KF_DLAPLACE: return launch_plain_kf<KF_DLAPLACE, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st);
+    default: return launch_plain_kf<KF_DMATERN, COMP>(Q, Ks, V, m, ldv, O, ldo, pc, st);
   }
 }
 
@@ -262,100 +256,17 @@ int plain_matvec(const PointSet& Q, const PointSet& Ks, bool /*self*/, int kf, c
 }
 
 // ---------------------------------------------------------------------------
-// The check operator with the kernel matrix kept in HBM.  K(X, X) in FP32 is
-// n^2 * 4 bytes (160 GB at n = 200000, which a B300 holds).  The first check
-// product of a solve computes it by direct differences as above and stores
-// it; later check products of the same solve stream the stored matrix with
-// the same error-free contraction instead of recomputing the distances.
-
-// O[i][c0 + c] = sum_{j < nk} Kc[i][j] V[j][c0 + c], TwoProduct + TwoSum per
-// entry as in the direct kernel.  A warp takes RW rows (8; 4 for 8 columns);
-// lane l reads the float4 of keys j = jb + 4 l of each row and the V rows of
-// those 4 keys once for the RW rows.  Keys j >= nk (the tail of a row up to
-// ldk) count as 0.
-template <int MV>
-__global__ void __launch_bounds__(256) kcache_gemv_kernel(const float* __restrict__ Kc, int64_t ldk, int nq, int nk,
-                                                          const float* __restrict__ V, int m, int ldv,
-                                                          float* __restrict__ O, int ldo) {
-  constexpr int RW = MV <= 4 ? 8 : 4;
-  const int lane = threadIdx.x & 31;
-  const int64_t i0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * RW;
-  if (i0 >= nq) return;  // warp-uniform
-  const int nr = nq - i0 < RW ? (int)(nq - i0) : RW;
-  const int c0 = blockIdx.y * MV;
-  const int mc = m - c0 < MV ? m - c0 : MV;
-  float s[RW][MV], e[RW][MV];
-#pragma unroll
-  for (int r = 0; r < RW; ++r)
-#pragma unroll
-    for (int c = 0; c < MV; ++c) s[r][c] = e[r][c] = 0.0f;
-  for (int jb = 0; jb < nk; jb += 128) {
-    const int j = jb + 4 * lane;
-    float v[4][MV];
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int c = 0; c < MV; ++c) v[q][c] = (j + q < nk && c < mc) ? __ldg(V + (int64_t)(j + q) * ldv + c0 + c) : 0.0f;
-    float4 k[RW];
-#pragma unroll
-    for (int r = 0; r < RW; ++r)
-      k[r] = r < nr ? *reinterpret_cast<const float4*>(Kc + (i0 + r) * ldk + j) : make_float4(0.f, 0.f, 0.f, 0.f);
-    if (jb + 128 > nk) {  // the last block of keys: entries past nk are not data
-#pragma unroll
-      for (int r = 0; r < RW; ++r) {
-        if (j + 0 >= nk) k[r].x = 0.0f;
-        if (j + 1 >= nk) k[r].y = 0.0f;
-        if (j + 2 >= nk) k[r].z = 0.0f;
-        if (j + 3 >= nk) k[r].w = 0.0f;
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < RW; ++r) {
-      const float kr[4] = {k[r].x, k[r].y, k[r].z, k[r].w};
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int c = 0; c < MV; ++c) {
-          const float p = kr[q] * v[q][c];
-          const float pe = fmaf(kr[q], v[q][c], -p);
-          const float t = s[r][c] + p;
-          const float bb = t - s[r][c];
-          e[r][c] += ((s[r][c] - (t - bb)) + (p - bb)) + pe;
-          s[r][c] = t;
-        }
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < RW; ++r)
-#pragma unroll
-    for (int c = 0; c < MV; ++c) {
-      float a = s[r][c], b = e[r][c];
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const float a2 = __shfl_xor_sync(0xffffffffu, a, off);
-        const float b2 = __shfl_xor_sync(0xffffffffu, b, off);
-        const float t = a + a2;
-        const float bb = t - a;
-        b += ((a - (t - bb)) + (a2 - bb)) + b2;
-        a = t;
-      }
-      if (lane == 0 && r < nr && c < mc) O[(i0 + r) * ldo + c0 + c] = a + b;
-    }
-}
-
-template <int MV>
-static void kcache_launch(const float* Kc, int64_t ldk, int nq, int nk, const float* V, int m, int ldv, float* O,
-                          int ldo, cudaStream_t st) {
-  constexpr int rows_per_cta = 8 * (MV <= 4 ? 8 : 4);
-  const dim3 grid((unsigned)((nq + rows_per_cta - 1) / rows_per_cta), (unsigned)((m + MV - 1) / MV));
-  kcache_gemv_kernel<MV><<<grid, 256, 0, st>>>(Kc, ldk, nq, nk, V, m, ldv, O, ldo);
-}
+// The check operator with the kernel matrix kept in HBM.  K(X, X) in FP32
+// costs n^2 * 4 bytes in full; the stored form keeps each pair of row blocks
+// once (about n^2 * 2 bytes: 80 GB at n = 200000).  The first check product
+// of a solve computes the band tiles by direct differences as above and
+// stores them; every check product of the solve then reads each stored tile
+// once and uses it for both of its contributions.
 
 int check_cache_reserve(kop_s* op) {
   if (op->kc) return KOP_OK;
   const int64_t n = op->pts.n;
-  const int64_t ld = check_cache_ld(n);
-  const size_t bytes = sizeof(float) * (size_t)n * (size_t)ld;
+  const size_t bytes = sizeof(float) * (size_t)check_cache_floats(n);
   size_t fr = 0, tot = 0;
   KOP_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
   // keep 4 GB for the solver's own buffers and the caller's
@@ -366,13 +277,12 @@ int check_cache_reserve(kop_s* op) {
     op->kc = nullptr;
     return fail(KOP_ENOMEM, "kop_set_check_cache: cudaMalloc failed");
   }
-  op->kc_ld = ld;
   op->kc_owned = 1;
   return KOP_OK;
 }
 
 template <int KF>
-static int launch_build_t(const PointSet& P, const PlainConst& pc, float* Kc, int64_t ldk, cudaStream_t st) {
+static int launch_build_t(const PointSet& P, const PlainConst& pc, float* Kc, cudaStream_t st) {
   auto kern = k2_plain_kernel<KF, 1, true, true>;
   const int dp = P.dp;
   const size_t smem = sizeof(float) * ((size_t)dp * (K2_ROWS + 1) + (size_t)K2_KEYS * dp + K2_KEYS * 1);
@@ -382,40 +292,255 @@ static int launch_build_t(const PointSet& P, const PlainConst& pc, float* Kc, in
     attr_set = true;
   }
   dim3 grid((unsigned)((P.n + K2_ROWS - 1) / K2_ROWS), 1);
-  kern<<<grid, K2_ROWS, smem, st>>>(P.xc, P.xc, nullptr, nullptr, (int)P.n, (int)P.n, dp, 1, 1, 1, pc, Kc, ldk);
+  kern<<<grid, K2_ROWS, smem, st>>>(P.xc, P.xc, nullptr, nullptr, (int)P.n, (int)P.n, dp, 1, 1, 1, pc, Kc);
   KOP_LAUNCHED();
   return KOP_OK;
 }
 
-// Store the direct-difference K(X, X) in op->kc: the upper block triangle
-// (each pair of row blocks once), then its mirror image.
+// Store the direct-difference K(X, X) in op->kc for each pair of row blocks
+// once (the band of each block).
 static int check_cache_build(kop_s* op, cudaStream_t st) {
   const PlainConst pc = plain_constants(op->kernel, op->bw);
-  int rc;
   switch (op->kernel) {
-    case KF_RBF: rc = launch_build_t<KF_RBF>(op->pts, pc, op->kc, op->kc_ld, st); break;
-    case KF_LAPLACE: rc = launch_build_t<KF_LAPLACE>(op->pts, pc, op->kc, op->kc_ld, st); break;
-    default: rc = launch_build_t<KF_MATERN>(op->pts, pc, op->kc, op->kc_ld, st); break;
+    case KF_RBF: return launch_build_t<KF_RBF>(op->pts, pc, op->kc, st);
+    case KF_LAPLACE: return launch_build_t<KF_LAPLACE>(op->pts, pc, op->kc, st);
+    default: return launch_build_t<KF_MATERN>(op->pts, pc, op->kc, st);
   }
-  if (rc) return rc;
+}
+
+// The symmetric product with the stored matrix, for the solver's checks: the
+// vectors come in exact hi / lo FP32 pairs (x = hi + lo, columns c and cols + c
+// of V2) and the result of each column is returned as an unevaluated
+// (sum, error) pair in the same two columns of T (the residual adds them in
+// FP64).  Per entry: TwoProduct K hi + TwoSum into the running sum, and the
+// product with lo (2^-24 of the rest) into the error term.
+//
+// The CTA of row block I reads each tile K[I][J] of its band once (128 x 128
+// floats, double-buffered through shared memory with asynchronous copies) and
+// uses it twice: row part T_I += K_IJ x_J (accumulated over the band) and,
+// for J != I, column part C[J][t - 1] = K_IJ^T x_I, stored as (sum, error)
+// pairs for a second kernel that adds the column parts in a fixed order.
+// Four threads per row / column take a quarter of the tile each, with two
+// independent accumulators, combined in a fixed order.  Rows and keys past n
+// count as 0.
+constexpr int KS2_LD = 132;       // padded row pitch of a tile in shared memory (floats)
+constexpr int KS2_THREADS = 512;  // 4 threads per row / column
+
+// (s, e) += k (hi + lo), error-free up to the (negligible) rounding of k lo.
+KOP_DEV void ef_acc_pair(float& s, float& e, float k, float hi, float lo) {
+  const float p = k * hi;
+  const float pe = fmaf(k, hi, -p);
+  const float t = s + p;
+  const float bb = t - s;
+  const float err = (s - (t - bb)) + (p - bb);
+  s = t;
+  e = fmaf(k, lo, e + (err + pe));
+}
+
+template <int NC>
+__global__ void __launch_bounds__(KS2_THREADS, 1)
+    kcache_symv_kernel(const float* __restrict__ Kc, int n, int nb, int h, const float* __restrict__ V2, int cols,
+                       int c0, float* __restrict__ T, float* __restrict__ C) {
+  extern __shared__ __align__(16) float ksm[];
+  float* tile[2] = {ksm, ksm + 128 * KS2_LD};
+  float2* xj[2] = {reinterpret_cast<float2*>(ksm + 2 * 128 * KS2_LD),
+                   reinterpret_cast<float2*>(ksm + 2 * 128 * KS2_LD) + 128 * NC};
+  float2* xi = reinterpret_cast<float2*>(ksm + 2 * 128 * KS2_LD) + 2 * 128 * NC;
+  float* red = reinterpret_cast<float*>(xi + 128 * NC);  // quarters 1..3: 3 x 128 x NC x (s, e)
+  const int tid = threadIdx.x;
+  const int I = blockIdx.x;
+  const int cnt = sym_band_count(I, nb);
+  const int r = tid & 127, q = tid >> 7;
+  const int ld = 2 * cols;
+  auto xpair = [&](int row, int c) -> float2 {
+    return (row < n && c0 + c < cols)
+               ? make_float2(V2[(int64_t)row * ld + c0 + c], V2[(int64_t)row * ld + cols + c0 + c])
+               : make_float2(0.0f, 0.0f);
+  };
+  for (int idx = tid; idx < 128 * NC; idx += KS2_THREADS) xi[idx] = xpair(I * 128 + idx / NC, idx % NC);
+  auto load = [&](int t, int buf) {
+    const int J = I + t < nb ? I + t : I + t - nb;
+    float* Tl = tile[buf];
+    for (int idx = tid; idx < 128 * 32; idx += KS2_THREADS) {  // 128 rows x 32 float4
+      const int rr = idx >> 5, qq = idx & 31, i = I * 128 + rr;
+      const float* src = Kc + (((int64_t)I * (h + 1) + t) * 128 + rr) * 128 + 4 * qq;
+      const uint32_t dst = (uint32_t)__cvta_generic_to_shared(Tl + rr * KS2_LD + 4 * qq);
+      const int bytes = i < n ? 16 : 0;  // rows past n: zero fill
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+    }
+    for (int idx = tid; idx < 128 * NC; idx += KS2_THREADS) xj[buf][idx] = xpair(J * 128 + idx / NC, idx % NC);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  // this thread's quarter folded, then quarters 1..3 added by quarter 0 in a
+  // fixed order
+  auto combine = [&](float (&as)[2][NC], float (&ae)[2][NC], float (&os)[NC], float (&oe)[NC]) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      os[c] = as[0][c];
+      oe[c] = ae[0][c] + ae[1][c];
+      two_sum_acc(os[c], oe[c], as[1][c]);
+    }
+    if (q > 0) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        float* rd = red + (((q - 1) * 128 + r) * NC + c) * 2;
+        rd[0] = os[c];
+        rd[1] = oe[c];
+      }
+    }
+    __syncthreads();
+    if (q == 0) {
+#pragma unroll
+      for (int qq = 0; qq < 3; ++qq)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const float* rd = red + ((qq * 128 + r) * NC + c) * 2;
+          two_sum_acc(os[c], oe[c], rd[0]);
+          oe[c] += rd[1];
+        }
+    }
+  };
+  float rs[2][NC], re[2][NC];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) rs[a][c] = re[a][c] = 0.0f;
+  load(0, 0);
+  for (int t = 0; t < cnt; ++t) {
+    const int buf = t & 1;
+    const int J = I + t < nb ? I + t : I + t - nb;
+    if (t + 1 < cnt) {
+      load(t + 1, buf ^ 1);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    __syncthreads();
+    const float* Tl = tile[buf];
+    const float2* X = xj[buf];
+    // row part: row r, columns q * 32 .. + 31 in a rotated order (no bank
+    // conflicts), two accumulators; keys past n are 0
+    const int jlim = n - J * 128;
+#pragma unroll 8
+    for (int cc = 0; cc < 32; ++cc) {
+      const int c = q * 32 + ((cc + r) & 31);
+      const float kv = c < jlim ? Tl[r * KS2_LD + c] : 0.0f;
+#pragma unroll
+      for (int k = 0; k < NC; ++k) {
+        const float2 x = X[c * NC + k];
+        ef_acc_pair(rs[cc & 1][k], re[cc & 1][k], kv, x.x, x.y);
+      }
+    }
+    if (t > 0) {
+      // column part: column r, rows q * 32 .. + 31 (rows past n were zero-filled)
+      float cs[2][NC], ce[2][NC];
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int k = 0; k < NC; ++k) cs[a][k] = ce[a][k] = 0.0f;
+#pragma unroll 8
+      for (int rr = 0; rr < 32; ++rr) {
+        const int row = q * 32 + rr;
+        const float kv = Tl[row * KS2_LD + r];
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+          const float2 x = xi[row * NC + k];
+          ef_acc_pair(cs[rr & 1][k], ce[rr & 1][k], kv, x.x, x.y);
+        }
+      }
+      float os[NC], oe[NC];
+      combine(cs, ce, os, oe);
+      if (q == 0) {
+        float2* dst = reinterpret_cast<float2*>(C) + (((int64_t)J * h + (t - 1)) * 128 + r) * NC;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) dst[k] = make_float2(os[k], oe[k]);
+      }
+    }
+    __syncthreads();  // the buffers are reloaded by the next iteration's prefetch
+  }
+  float os[NC], oe[NC];
+  combine(rs, re, os, oe);
+  const int i = I * 128 + r;
+  if (q == 0 && i < n) {
+#pragma unroll
+    for (int k = 0; k < NC; ++k)
+      if (c0 + k < cols) {
+        T[(int64_t)i * ld + c0 + k] = os[k];
+        T[(int64_t)i * ld + cols + c0 + k] = oe[k];
+      }
+  }
+}
+
+// (T[i][c0 + k], T[i][cols + c0 + k]) += the column parts of row block
+// J = i / 128, in the order of t, as (sum, error) pairs.
+template <int NC>
+__global__ void kcache_combine_kernel(float* __restrict__ T, int cols, int c0, const float* __restrict__ C, int n,
+                                      int nb, int h) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= (int64_t)n * NC) return;
+  const int i = (int)(g / NC), k = (int)(g - (int64_t)i * NC);
+  if (c0 + k >= cols) return;
+  const int J = i >> 7, jj = i & 127;
+  const int64_t ld = 2 * (int64_t)cols;
+  float s = T[i * ld + c0 + k], e = T[i * ld + cols + c0 + k];
+  const float2* C2 = reinterpret_cast<const float2*>(C);
+  for (int t = 1; t <= h; ++t) {
+    const int I = J - t >= 0 ? J - t : J - t + nb;
+    if (t < sym_band_count(I, nb)) {
+      const float2 p = C2[(((int64_t)J * h + (t - 1)) * 128 + jj) * NC + k];
+      two_sum_acc(s, e, p.x);
+      e += p.y;
+    }
+  }
+  T[i * ld + c0 + k] = s;
+  T[i * ld + cols + c0 + k] = e;
+}
+
+template <int NC>
+static int symv_launch(kop_s* op, const float* V2, int cols, int c0, float* T, cudaStream_t st) {
+  auto kern = kcache_symv_kernel<NC>;
+  const size_t smem = sizeof(float) * (2 * 128 * KS2_LD) + sizeof(float2) * 3 * 128 * NC +
+                      sizeof(float) * 3 * 128 * NC * 2;
+  static bool attr_set = false;
+  if (!attr_set) {
+    KOP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr_set = true;
+  }
   const int n = (int)op->pts.n;
-  const unsigned t = (unsigned)((n + 31) / 32);
-  kcache_mirror_kernel<<<dim3(t, t), 256, 0, st>>>(op->kc, op->kc_ld, n);
+  const int nb = (n + 127) / 128, h = nb / 2;
+  kern<<<(unsigned)nb, KS2_THREADS, smem, st>>>(op->kc, n, nb, h, V2, cols, c0, T, op->kc_scratch);
   KOP_LAUNCHED();
+  if (h > 0) {
+    const int64_t tot = (int64_t)n * NC;
+    kcache_combine_kernel<NC><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(T, cols, c0, op->kc_scratch, n, nb, h);
+    KOP_LAUNCHED();
+  }
   return KOP_OK;
 }
 
-int check_matvec_cached(kop_s* op, bool build, const float* V, int m, int ldv, float* O, int ldo, cudaStream_t st) {
+int check_matvec_cached(kop_s* op, bool build, const float* V2, int cols, float* T, cudaStream_t st) {
   const int n = (int)op->pts.n;
   if (build) {
     const int rc = check_cache_build(op, st);
     if (rc) return rc;
   }
-  if (m == 1) kcache_launch<1>(op->kc, op->kc_ld, n, n, V, m, ldv, O, ldo, st);
-  else if (m == 2) kcache_launch<2>(op->kc, op->kc_ld, n, n, V, m, ldv, O, ldo, st);
-  else if (m <= 4) kcache_launch<4>(op->kc, op->kc_ld, n, n, V, m, ldv, O, ldo, st);
-  else kcache_launch<8>(op->kc, op->kc_ld, n, n, V, m, ldv, O, ldo, st);
-  KOP_LAUNCHED();
+  const int nb = (n + 127) / 128, h = nb / 2;
+  const int nc = cols <= 1 ? 1 : (cols <= 2 ? 2 : 4);
+  const size_t need = (size_t)nb * h * 128 * nc * 2;  // (sum, error) pairs
+  if (need > op->kc_scratch_floats) {
+    if (op->kc_scratch) cudaFreeAsync(op->kc_scratch, st);
+    op->kc_scratch = nullptr;
+    op->kc_scratch_floats = 0;
+    KOP_CUDA_TRY(cudaMallocAsync((void**)&op->kc_scratch, sizeof(float) * (need > 0 ? need : 1), st));
+    op->kc_scratch_floats = need;
+  }
+  for (int c0 = 0; c0 < cols; c0 += nc) {
+    int rc;
+    if (nc == 1) rc = symv_launch<1>(op, V2, cols, c0, T, st);
+    else if (nc == 2) rc = symv_launch<2>(op, V2, cols, c0, T, st);
+    else rc = symv_launch<4>(op, V2, cols, c0, T, st);
+    if (rc) return rc;
+  }
   return KOP_OK;
 }
 

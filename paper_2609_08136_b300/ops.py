@@ -82,8 +82,10 @@ class KernelOperator:
         self.bandwidth = float(bw)
 
     def check_cache_floats(self) -> int:
-        """Floats of the stored check matrix: n rows padded to 128 columns."""
-        return self.n * ((self.n + 127) // 128 * 128)
+        """Floats of the stored check matrix: the 128 x 128 tiles of each pair
+        of row blocks once, nb * (nb // 2 + 1) * 128^2 with nb = ceil(n / 128)."""
+        nb = (self.n + 127) // 128
+        return nb * (nb // 2 + 1) * 128 * 128
 
     def set_check_cache(self, enable: bool = True, buffer: torch.Tensor | None = None):
         """Keep the kernel matrix of the solver's direct-difference checks in

@@ -33,9 +33,9 @@ def _solve(op, B, lams, ny, cache, **kw):
         op.set_check_cache(False)
 
 
-# n ragged against the 32-key tiles, the 128-column padding of the stored
-# rows and the 8-row warps of the stored product; 2 x cols = 2, 6 and 10
-# columns cover one, one and two column blocks
+# n ragged against the 32-key tiles and the 128-point row blocks, odd and even
+# numbers of row blocks (24, 16, 12, 1); 2 x cols = 2, 6 and 10 columns cover
+# one, one and two column blocks of the stored product
 @pytest.mark.parametrize("kind,n,nrhs,lams", [
     (ops.LAPLACE, 3001, 1, [1e-3]),
     (ops.RBF, 2000, 3, [1e-3]),
@@ -61,11 +61,17 @@ def test_cached_checks_match_direct_checks(kind, n, nrhs, lams):
     xa, xb, xc = a.x.cpu().numpy(), b.x.cpu().numpy(), c.x.cpu().numpy()
     assert np.max(np.abs(xa - xb)) <= 1e-6 * np.max(np.abs(xa))
     assert np.max(np.abs(xc - xb)) <= 1e-6 * np.max(np.abs(xa))
-    # the check's output K x is rounded to FP32: the two contraction orders can
-    # round an element to neighbouring floats, moving the relative residual by
-    # about 2^-24 |(K x)_i| / ||b|| per such element (~1e-9 here)
-    np.testing.assert_allclose(b.true_relres, a.true_relres, rtol=1e-4, atol=1e-8)
-    np.testing.assert_allclose(c.true_relres, a.true_relres, rtol=1e-4, atol=1e-8)
+    # the stored matrix is multiplied in another order (each stored tile used
+    # for its row and its column contributions), so each refinement replaces
+    # the residual by one that differs in the last bits and the iterates drift
+    # apart (to ~1e-7 of max |x| here); near the tolerance that moves the final
+    # FP64 residual by up to ~20% of it, so the direct and stored runs are each
+    # checked against the oracle below rather than against each other.  The
+    # library's and the caller's memory run the same code; the solver's FP64
+    # reductions add their block sums atomically in any order, which moves the
+    # reported residual by ~1e-8 of itself.
+    np.testing.assert_allclose(c.true_relres, b.true_relres, rtol=1e-5, atol=0.0)
+    assert max(a.true_relres) <= kw["tol"] and max(b.true_relres) <= kw["tol"]
     # the oracle's FP64 residual of each accepted iterate meets the tolerance,
     # and the reported residual is that FP64 residual: exact here (n <= 4096,
     # so the solver's FP64 certification covers every row) up to the FP64
@@ -76,9 +82,10 @@ def test_cached_checks_match_direct_checks(kind, n, nrhs, lams):
         bc = B[:, col % nrhs].astype(np.float64)
         lam = lam_abs[col // nrhs]
         nb = np.linalg.norm(bc)
-        rr = np.linalg.norm(K @ xb2[:, col] + lam * xb2[:, col] - bc) / nb
-        assert rr <= 1e-6, (col, rr)
-        assert abs(b.true_relres[col] - rr) <= 1e-3 * rr, (col, b.true_relres[col], rr)
+        for res, xx in ((a, xa.reshape(n, -1)), (b, xb2)):
+            rr = np.linalg.norm(K @ xx[:, col] + lam * xx[:, col] - bc) / nb
+            assert rr <= 1e-6, (col, rr)
+            assert abs(res.true_relres[col] - rr) <= 1e-3 * rr, (col, res.true_relres[col], rr)
 
 
 def test_cached_checks_in_the_adjoint():
@@ -105,7 +112,7 @@ def test_cached_checks_in_the_adjoint():
 def test_cache_reserves_and_frees_memory():
     n = 3001
     op = ops.KernelOperator(torch.from_numpy(W.random_points(n, 4, seed=1)).cuda(), ops.RBF, 2.0)
-    need = n * 3072 * 4  # rows padded to a multiple of 128 floats
+    need = 24 * 13 * 128 * 128 * 4  # 24 row blocks x 13 band tiles of 128 x 128 floats
     torch.cuda.synchronize()
     f0 = torch.cuda.mem_get_info()[0]
     op.set_check_cache(True)
@@ -118,8 +125,9 @@ def test_cache_reserves_and_frees_memory():
 
 
 def test_cache_refused_when_it_does_not_fit_and_for_ridge():
-    # 300000^2 * 4 bytes = 360 GB: more than the device holds, nothing reserved
-    n = 300_000
+    # 3125 row blocks x 1563 band tiles x 64 KB = 320 GB: more than the device
+    # holds, nothing reserved
+    n = 400_000
     op = ops.KernelOperator(torch.from_numpy(W.random_points(n, 1, seed=2)).cuda(), ops.RBF, 1.0)
     f0 = torch.cuda.mem_get_info()[0]
     with pytest.raises(KopError, match="not enough free device memory"):
@@ -134,7 +142,7 @@ def test_caller_buffer_checked():
     n = 500
     op = ops.KernelOperator(torch.from_numpy(W.random_points(n, 4, seed=6)).cuda(), ops.RBF, 2.0)
     need = op.check_cache_floats()
-    assert need == n * 512
+    assert need == 4 * 3 * 128 * 128  # 4 row blocks x 3 band tiles
     with pytest.raises(KopError, match="buffer smaller"):
         op.set_check_cache(True, torch.empty(need - 1, device="cuda"))
     buf = torch.empty(need + 4, device="cuda")
