@@ -37,9 +37,9 @@ sys.path.insert(0, ROOT)
 METRIC = "PCG time-to-relres 1e-6 & fused kernel-matvec TFLOP/s vs plain FP32 path"
 TOL = 1e-6
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the FAST
-# single-column product, keyed by (kernel, n, d); mean of two launches at full
-# size, taken on the kernel as it stands
-TRAFFIC_BYTES = {}
+# single-vector product, keyed by (kernel, n, d); mean of seven launches at
+# full size, taken on the kernel as it stands
+TRAFFIC_BYTES = {(1, 200_000, 64): 96.22e6 + 571.19e6}
 
 # name: (generator kwargs, description, refine_every, maxit)
 WORKLOADS = {
@@ -416,7 +416,9 @@ def run_native(a):
     # BF16 splits, scaled norms, v and the output, each once
     traffic = TRAFFIC_BYTES.get((wl.kernel, n, d))
     dp = 16 if d <= 16 else (32 if d <= 32 else (64 if d <= 64 else 128))
-    alg_bytes = n * dp * 2 * 2 + 3 * n * 4
+    # X as two BF16 splits, scaled norms, v, the output, and the column parts
+    # written once (nb x floor(nb / 2) x 128 FP32)
+    alg_bytes = n * dp * 2 * 2 + 3 * n * 4 + nb * (nb // 2) * 128 * 4
     knames = {W.RBF: "RBF", W.LAPLACE: "LAPLACE", W.MATERN52: "MATERN"}
     out = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
