@@ -1,6 +1,7 @@
 // Dense helpers (kop_dense.cu): tall-skinny products over the n rows and the
 // small r x r FP64 factorizations used by the Nystrom construction.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -50,5 +51,24 @@ int nys_finish(const double* w, const double* E, const int* perm, int r, double 
                cudaStream_t st);
 int d2f(const double* a, float* b, int64_t n, cudaStream_t st);
 int eye(double* M, int r, cudaStream_t st);
+
+// Tensor-core forms (kop_tcgemm.cu).  Operands are FP32 matrices split
+// exactly into three BF16 terms; six partial products give FP32-accurate
+// products.  t-split (Gram operands): 3 x ceil(n / 64) x p_pad128 x 64 BF16;
+// r-split (row operand of the tall product): 3 x n_pad128 x kp (p rounded up
+// to 64).  A2 (optional) is added as A + beta A2 before splitting.
+int64_t tsplit_elems(int64_t n, int p);
+int64_t rsplit_elems(int64_t n, int p);
+int tsplit(const float* A, const float* A2, float beta, int lda, int64_t n, int p, __nv_bfloat16* T,
+           cudaStream_t st);
+int rsplit(const float* A, const float* A2, float beta, int lda, int64_t n, int p, __nv_bfloat16* R,
+           cudaStream_t st);
+// C (p x q, FP64, ldc) = A^T B from the t-splits of A and B (sym: B is A).
+int gram_tc(const __nv_bfloat16* At, const __nv_bfloat16* Bt, int64_t n, int p, int q, bool sym, double* C, int ldc,
+            int* status, cudaStream_t st);
+// O (n x q, ldo) = A W (+ alpha_col (.) V) from the r-split of A (n x p) and W
+// (p x q, FP32, ldw).
+int tall_tc(const __nv_bfloat16* Ar, int64_t n, int p, const float* W, int ldw, int q, const float* V, int ldv,
+            const float* alpha_col, float* O, int ldo, int* status, cudaStream_t st);
 
 }  // namespace kop

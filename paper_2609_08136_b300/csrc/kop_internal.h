@@ -196,6 +196,10 @@ struct nys_s {
   int r = 0;
   int64_t n = 0;
   float* U = nullptr;            // device, n_pad x r
+  // BF16 splits of U for the tensor-core apply on blocks of columns (built by
+  // the first such apply): t-split (U^T V) and r-split (U W)
+  __nv_bfloat16* Ut = nullptr;
+  __nv_bfloat16* Ur = nullptr;
   double* lam_dev = nullptr;     // device, r (descending)
   double* lam_host = nullptr;    // host copy
   double nu = 0.0;

@@ -16,6 +16,7 @@
 // contraction carries it as a BF16 hi + lo pair (about 2^-16 relative, the
 // accuracy of the fast operator's kernel values), the Gram blocks read it in
 // FP32.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -72,12 +73,39 @@ int nys_apply_dev(const nys_s* ny, const double* mu_dev, int adaptive, const flo
     KOP_LAUNCHED();
     return uw_ff(ny->U, r, n, r, reinterpret_cast<const float2*>(Wd), V, m, alpha, O, st);
   }
-  int rc = gram(ny->U, r, V, m, n, r, m, Wd, m, st);
+  // wider blocks: W = U^T V and O = alpha (.) V + U W' on the tensor cores
+  // (FP32-accurate products), from BF16 splits of U kept with the factor
+  nys_s* nym = const_cast<nys_s*>(ny);
+  if (!nym->Ut) {
+    KOP_CUDA_TRY(cudaMalloc(&nym->Ut, sizeof(__nv_bfloat16) * (size_t)tsplit_elems(n, r)));
+    cudaError_t e = cudaMalloc(&nym->Ur, sizeof(__nv_bfloat16) * (size_t)rsplit_elems(n, r));
+    if (e != cudaSuccess) {
+      cudaFree(nym->Ut);
+      nym->Ut = nullptr;
+      nym->Ur = nullptr;
+      return cuda_fail(e, "nys_apply: cudaMalloc");
+    }
+    int rc = tsplit(ny->U, nullptr, 0.0f, r, n, r, nym->Ut, st);
+    if (rc == KOP_OK) rc = rsplit(ny->U, nullptr, 0.0f, r, n, r, nym->Ur, st);
+    if (rc) {
+      cudaFree(nym->Ut);
+      cudaFree(nym->Ur);
+      nym->Ut = nym->Ur = nullptr;
+      return rc;
+    }
+  }
+  DevBuf vb;
+  vb.st = st;
+  KOP_CUDA_TRY(cudaMallocAsync(&vb.p, sizeof(__nv_bfloat16) * (size_t)tsplit_elems(n, m), st));
+  __nv_bfloat16* Vt = (__nv_bfloat16*)vb.p;
+  int* status = ny->op->status;
+  int rc = tsplit(V, nullptr, 0.0f, m, n, m, Vt, st);
+  if (rc == KOP_OK) rc = gram_tc(ny->Ut, Vt, n, r, m, false, Wd, m, status, st);
   if (rc) return rc;
   nys_scale_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(Wd, r, m, ny->lam_dev, mu_dev, adaptive, Wf, alpha,
                                                                   alpha_f, 0);
   KOP_LAUNCHED();
-  return tall_gemm(ny->U, nullptr, 0.0f, r, n, r, Wf, m, m, V, m, alpha_f, O, m, st);
+  return tall_tc(ny->Ur, n, r, Wf, m, m, V, m, alpha_f, O, m, status, st);
 }
 
 static int read_info(const int* dev, int* host, cudaStream_t st) {
@@ -134,9 +162,19 @@ extern "C" int nys_build(kop_t op, const float* Omega, int32_t r, double nu_rel,
   // 1. sketch Y = K Omega (fused operator, m = r)
   rc = op_apply(op, mode, Omega, r, r, Y, r, st);
   if (rc) return rc;
-  // 2. Gram blocks
-  if ((rc = gram(Omega, r, Omega, r, n, r, r, Goo, r, st))) return rc;
-  if ((rc = gram(Omega, r, Y, r, n, r, r, Goy, r, st))) return rc;
+  // 2. Gram blocks: Omega^T Omega and Omega^T Y on the tensor cores from BF16
+  // splits of the two matrices (two scratch buffers, reused below)
+  DevBuf wsS1, wsS2;
+  wsS1.st = wsS2.st = st;
+  const size_t split_elems = (size_t)std::max(tsplit_elems(n, r), rsplit_elems(n, r));
+  KOP_CUDA_TRY(cudaMallocAsync(&wsS1.p, sizeof(__nv_bfloat16) * split_elems, st));
+  KOP_CUDA_TRY(cudaMallocAsync(&wsS2.p, sizeof(__nv_bfloat16) * split_elems, st));
+  __nv_bfloat16* S1 = (__nv_bfloat16*)wsS1.p;
+  __nv_bfloat16* S2 = (__nv_bfloat16*)wsS2.p;
+  if ((rc = tsplit(Omega, nullptr, 0.0f, r, n, r, S1, st))) return rc;
+  if ((rc = tsplit(Y, nullptr, 0.0f, r, n, r, S2, st))) return rc;
+  if ((rc = gram_tc(S1, S1, n, r, r, true, Goo, r, op->status, st))) return rc;
+  if ((rc = gram_tc(S1, S2, n, r, r, false, Goy, r, op->status, st))) return rc;
   // Y^T Y error-free: the core C^-T (Y_nu^T Y_nu) C^-1 squares the condition
   // of the sketch, and FP32 sums make its smallest eigenvalues negative once
   // the spectrum spans ~1e5
@@ -201,9 +239,11 @@ extern "C" int nys_build(kop_t op, const float* Omega, int32_t r, double nu_rel,
     return code;
   };
   KOP_CUDA_TRY(cudaMemsetAsync(U2, 0, sizeof(float) * (size_t)n_pad * r, st));
-  if ((rc = tall_gemm(Y, Omega, (float)nu, r, n, r, Wf, r, r, nullptr, 0, nullptr, U2, r, st))) return drop(rc);
+  if ((rc = rsplit(Y, Omega, (float)nu, r, n, r, S2, st))) return drop(rc);
+  if ((rc = tall_tc(S2, n, r, Wf, r, r, nullptr, 0, nullptr, U2, r, op->status, st))) return drop(rc);
   // 11. Cholesky-QR: U <- U2 Lu^-T with Lu Lu^T = U2^T U2
-  if ((rc = gram(U2, r, U2, r, n, r, r, Goo, r, st))) return drop(rc);
+  if ((rc = tsplit(U2, nullptr, 0.0f, r, n, r, S1, st))) return drop(rc);
+  if ((rc = gram_tc(S1, S1, n, r, r, true, Goo, r, op->status, st))) return drop(rc);
   if ((rc = cholesky(Goo, r, info, st))) return drop(rc);
   if ((rc = read_info(info, &hinfo, st))) return drop(rc);
   if (hinfo != 0) return drop(fail(KOP_ENOTPD, "nys_build: U lost rank (Cholesky-QR failed)"));
@@ -211,7 +251,8 @@ extern "C" int nys_build(kop_t op, const float* Omega, int32_t r, double nu_rel,
   if ((rc = trsm(Goo, r, Z, r, r, 1, st))) return drop(rc);   // Z = Lu^-T
   if ((rc = d2f(Z, Wf, (int64_t)rr, st))) return drop(rc);
   if (cudaMemsetAsync(ny->U, 0, sizeof(float) * (size_t)n_pad * r, st) != cudaSuccess) return drop(KOP_ECUDA);
-  if ((rc = tall_gemm(U2, nullptr, 0.0f, r, n, r, Wf, r, r, nullptr, 0, nullptr, ny->U, r, st))) return drop(rc);
+  if ((rc = rsplit(U2, nullptr, 0.0f, r, n, r, S2, st))) return drop(rc);
+  if ((rc = tall_tc(S2, n, r, Wf, r, r, nullptr, 0, nullptr, ny->U, r, op->status, st))) return drop(rc);
   if (cudaMemcpyAsync(ny->lam_dev, lam, sizeof(double) * r, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
       cudaMemcpyAsync(ny->lam_host, lam, sizeof(double) * r, cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return drop(KOP_ECUDA);
@@ -228,6 +269,8 @@ extern "C" int nys_destroy(nys_t ny) {
   if (!ny) return KOP_OK;
   cudaDeviceSynchronize();
   cudaFree(ny->U);
+  if (ny->Ut) cudaFree(ny->Ut);
+  if (ny->Ur) cudaFree(ny->Ur);
   cudaFree(ny->lam_dev);
   delete[] ny->lam_host;
   delete ny;

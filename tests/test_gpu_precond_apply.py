@@ -92,3 +92,43 @@ def test_apply_one_and_two_columns_agree():
     one = ny.apply(torch.from_numpy(v).cuda(), [mu], adaptive=True).cpu().numpy().astype(np.float64)
     assert np.all(np.abs(got[:, 1] - 2 * got[:, 0]) <= 2.0 ** -22 * np.abs(got[:, 1]))
     assert np.all(np.abs(got[:, :1] - one) <= 2.0 ** -22 * np.abs(one))
+
+
+def _check_block(n, r, m, adaptive, seed):
+    """More than 8 columns: U^T V and U W run on the tensor cores with every
+    FP32 operand split exactly into three BF16 terms and FP32 sums, so each
+    entry is an FP32-accurate sum: its error is a few 2^-24 of the magnitudes
+    summed (chunks of 256 rows in FP32, FP64 across chunks).  The bound
+    2^-17 of the summed magnitudes leaves room for that and fails for a
+    missing split term (2^-8) or a misplaced tile (order 1); the error is also
+    compared with a plain FP32 evaluation of the same formula."""
+    op, ny, U, lam = _nystrom(n, r)
+    rng = np.random.default_rng(seed)
+    kt = max(1, int(np.sum(lam >= 0.1 * lam[0])))
+    Vc = U[:, :kt] @ rng.standard_normal((kt, m)) + 1e-6 * rng.standard_normal((n, m))
+    Vg = rng.standard_normal((n, m))
+    mus = [1e-4 * lam[0] * (1 + 0.01 * c) for c in range(m)]
+    U32 = U.astype(np.float32)
+    for V in (Vc.astype(np.float32), Vg.astype(np.float32)):
+        got = ny.apply(torch.from_numpy(V).cuda(), mus, adaptive=adaptive).cpu().numpy().astype(np.float64)
+        V64 = V.astype(np.float64)
+        mu = np.asarray(mus)
+        rho = lam[-1] + mu if adaptive else mu
+        d = 1.0 / (lam[:, None] + mu[None, :]) - 1.0 / rho[None, :]
+        ref = V64 / rho + U @ (d * (U.T @ V64))
+        mag = np.abs(V64) / rho + np.abs(U) @ (np.abs(d) * (np.abs(U).T @ np.abs(V64)))
+        err = np.abs(got - ref)
+        bound = 2.0 ** -24 * np.abs(ref) + 2.0 ** -17 * mag
+        worst = np.unravel_index(int(np.argmax(err - bound)), err.shape)
+        assert np.all(err <= bound), (n, r, m, adaptive, worst, err[worst], bound[worst], mag[worst])
+        # plain FP32 evaluation of the same formula
+        f32 = V / rho.astype(np.float32) + U32 @ (d.astype(np.float32) * (U32.T @ V))
+        e32 = np.linalg.norm(f32.astype(np.float64) - ref)
+        assert np.linalg.norm(got - ref) <= 8.0 * e32 + 2.0 ** -24 * np.linalg.norm(ref), (
+            np.linalg.norm(got - ref), e32)
+
+
+@pytest.mark.parametrize("n,r,m", [(3001, 500, 9), (3001, 700, 130), (600, 513, 16), (37, 8, 12), (5000, 24, 257)])
+def test_apply_block_tensor_core(n, r, m):
+    for adaptive in (False, True):
+        _check_block(n, r, m, adaptive, seed=n + 7 * r + m)
