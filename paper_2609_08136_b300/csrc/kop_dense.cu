@@ -14,45 +14,53 @@
 namespace kop {
 
 // ------------------------------------------------------------------ Gram
-// C (p x q, FP64, row-major, ldc) += A^T B over rows [0, n) of A (n x p, lda)
-// and B (n x q, ldb).  CTA tile 64 x 64 of C, 256 threads with 4 x 4 outputs
-// each; rows are consumed in chunks of 32 staged in shared memory, summed in
-// FP32 within a chunk and in FP64 across chunks; CTAs along z split the rows
-// and add their partial tiles atomically.  With FF every product is taken
-// exactly (p + e = a b, e by FMA) and summed error-free within the chunk
-// (TwoSum into a float-float pair), so C is accurate to about FP64 rounding;
-// the Nystrom core needs that for Y^T Y, whose small eigen-directions (down
-// to ~1e-5 of the largest, squared condition) FP32 sums would swamp.
-constexpr int GT = 64, GK = 32;
+// C (p x p, FP64, row-major, ldc) = A^T A over rows [0, n) of A (n x p, lda),
+// error-free: CTA tile 64 x 64 of C (tiles on and above the diagonal only;
+// an off-diagonal tile is added to both halves), 256 threads with 4 x 4
+// outputs each; rows are staged in shared memory 32 at a time, every product
+// is taken exactly (p + e = a b, e by FMA) and summed error-free over 128 rows
+// (TwoSum into a float-float pair), and those partials in FP64 (FP64 is slow
+// on this part, so it runs once per 128 rows); CTAs along y split the rows
+// and add their partial tiles atomically.  C is accurate to about FP64
+// rounding.  The Nystrom core needs that for Y^T Y, whose small
+// eigen-directions (down to ~1e-5 of the largest, squared condition) FP32
+// sums would swamp; the other Gram blocks run on the tensor cores
+// (kop_tcgemm.cu).
+constexpr int GT = 64, GK = 32, GFLUSH = 4;  // FP64 flush every GFLUSH * GK rows
 
-template <bool FF>
-__global__ void __launch_bounds__(256) gram_kernel(const float* __restrict__ A, int lda, const float* __restrict__ B,
-                                                   int ldb, int64_t n, int p, int q, double* __restrict__ C, int ldc,
-                                                   int64_t rows_per_split) {
+__global__ void __launch_bounds__(256) gram_sym_kernel(const float* __restrict__ A, int lda, int64_t n, int p,
+                                                       int tp, double* __restrict__ C, int ldc,
+                                                       int64_t rows_per_split) {
   __shared__ float As[GK][GT + 4];
   __shared__ float Bs[GK][GT + 4];
+  int ti = 0, idx = blockIdx.x;
+  while (idx >= tp - ti) {
+    idx -= tp - ti;
+    ++ti;
+  }
+  const int tj = ti + idx;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int p0 = blockIdx.x * GT, q0 = blockIdx.y * GT;
-  const int64_t r0 = (int64_t)blockIdx.z * rows_per_split;
+  const int p0 = ti * GT, q0 = tj * GT;
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_split;
   const int64_t r1 = r0 + rows_per_split < n ? r0 + rows_per_split : n;
   double acc[4][4];
+  float part[4][4], perr[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < 4; ++j) {
+      acc[i][j] = 0.0;
+      part[i][j] = perr[i][j] = 0.0f;
+    }
+  int chunk = 0;
   for (int64_t k0 = r0; k0 < r1; k0 += GK) {
-    for (int idx = threadIdx.x; idx < GK * GT; idx += 256) {
-      const int kk = idx / GT, c = idx - kk * GT;
+    for (int e = threadIdx.x; e < GK * GT; e += 256) {
+      const int kk = e / GT, c = e - kk * GT;
       const int64_t row = k0 + kk;
       As[kk][c] = (row < r1 && p0 + c < p) ? A[row * lda + p0 + c] : 0.0f;
-      Bs[kk][c] = (row < r1 && q0 + c < q) ? B[row * ldb + q0 + c] : 0.0f;
+      Bs[kk][c] = (row < r1 && q0 + c < p) ? A[row * lda + q0 + c] : 0.0f;
     }
     __syncthreads();
-    float part[4][4], perr[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) part[i][j] = perr[i][j] = 0.0f;
 #pragma unroll 8
     for (int kk = 0; kk < GK; ++kk) {
       float a[4], b[4];
@@ -64,22 +72,24 @@ __global__ void __launch_bounds__(256) gram_kernel(const float* __restrict__ A, 
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          if constexpr (FF) {
-            const float pr = a[i] * b[j];
-            const float pe = fmaf(a[i], b[j], -pr);
-            const float t = part[i][j] + pr;
-            const float bb = t - part[i][j];
-            perr[i][j] += ((part[i][j] - (t - bb)) + (pr - bb)) + pe;
-            part[i][j] = t;
-          } else {
-            part[i][j] = fmaf(a[i], b[j], part[i][j]);
-          }
+          const float pr = a[i] * b[j];
+          const float pe = fmaf(a[i], b[j], -pr);
+          const float t = part[i][j] + pr;
+          const float bb = t - part[i][j];
+          perr[i][j] += ((part[i][j] - (t - bb)) + (pr - bb)) + pe;
+          part[i][j] = t;
         }
     }
+    if (++chunk == GFLUSH || k0 + GK >= r1) {
+      chunk = 0;
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] += (double)part[i][j] + (double)perr[i][j];
+        for (int j = 0; j < 4; ++j) {
+          acc[i][j] += (double)part[i][j] + (double)perr[i][j];
+          part[i][j] = perr[i][j] = 0.0f;
+        }
+    }
     __syncthreads();
   }
 #pragma unroll
@@ -89,15 +99,18 @@ __global__ void __launch_bounds__(256) gram_kernel(const float* __restrict__ A, 
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int qj = q0 + tx * 4 + j;
-      if (qj < q) atomicAdd(&C[(int64_t)pi * ldc + qj], acc[i][j]);
+      if (qj >= p) continue;
+      atomicAdd(&C[(int64_t)pi * ldc + qj], acc[i][j]);
+      if (ti != tj) atomicAdd(&C[(int64_t)qj * ldc + pi], acc[i][j]);
     }
   }
 }
 
-int gram(const float* A, int lda, const float* B, int ldb, int64_t n, int p, int q, double* C, int ldc,
-         cudaStream_t st, bool error_free) {
+int gram_sym(const float* A, int lda, int64_t n, int p, double* C, int ldc, cudaStream_t st) {
   KOP_CUDA_TRY(cudaMemsetAsync(C, 0, sizeof(double) * (size_t)p * ldc, st));
-  const int tiles = ((p + GT - 1) / GT) * ((q + GT - 1) / GT);
+  if (n <= 0) return KOP_OK;
+  const int tp = (p + GT - 1) / GT;
+  const int tiles = tp * (tp + 1) / 2;
   int64_t splits = (2 * num_sms() + tiles - 1) / tiles;
   const int64_t max_splits = (n + 255) / 256;
   if (splits > max_splits) splits = max_splits;
@@ -105,83 +118,7 @@ int gram(const float* A, int lda, const float* B, int ldb, int64_t n, int p, int
   int64_t rps = (n + splits - 1) / splits;
   rps = ((rps + GK - 1) / GK) * GK;
   splits = (n + rps - 1) / rps;
-  dim3 grid((p + GT - 1) / GT, (q + GT - 1) / GT, (unsigned)splits);
-  if (error_free)
-    gram_kernel<true><<<grid, 256, 0, st>>>(A, lda, B, ldb, n, p, q, C, ldc, rps);
-  else
-    gram_kernel<false><<<grid, 256, 0, st>>>(A, lda, B, ldb, n, p, q, C, ldc, rps);
-  KOP_LAUNCHED();
-  return KOP_OK;
-}
-
-// ------------------------------------------------------------------ tall GEMM
-// O (n x q, ldo) = alpha_col[c] * V[i][c]  +  (A + beta * A2)(n x p) W (p x q, FP32)
-// (V, A2 optional).  CTA tile 64 rows x 64 columns, 256 threads x (4 x 4).
-__global__ void __launch_bounds__(256) tall_gemm_kernel(const float* __restrict__ A, const float* __restrict__ A2,
-                                                        float beta, int lda, int64_t n, int p,
-                                                        const float* __restrict__ W, int ldw, int q,
-                                                        const float* __restrict__ V, int ldv,
-                                                        const float* __restrict__ alpha_col, float* __restrict__ O,
-                                                        int ldo) {
-  __shared__ float As[GT][GK + 1];
-  __shared__ float Ws[GK][GT + 4];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int64_t i0 = (int64_t)blockIdx.x * GT;
-  const int c0 = blockIdx.y * GT;
-  float acc[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
-  for (int k0 = 0; k0 < p; k0 += GK) {
-    for (int idx = threadIdx.x; idx < GT * GK; idx += 256) {
-      const int r = idx / GK, kk = idx - r * GK;
-      const int64_t row = i0 + r;
-      float v = 0.0f;
-      if (row < n && k0 + kk < p) {
-        v = A[row * lda + k0 + kk];
-        if (A2) v = fmaf(beta, A2[row * lda + k0 + kk], v);
-      }
-      As[r][kk] = v;
-    }
-    for (int idx = threadIdx.x; idx < GK * GT; idx += 256) {
-      const int kk = idx / GT, c = idx - kk * GT;
-      Ws[kk][c] = (k0 + kk < p && c0 + c < q) ? W[(int64_t)(k0 + kk) * ldw + c0 + c] : 0.0f;
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int kk = 0; kk < GK; ++kk) {
-      float a[4], w[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[ty * 4 + i][kk];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) w[j] = Ws[kk][tx * 4 + j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], w[j], acc[i][j]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int64_t row = i0 + ty * 4 + i;
-    if (row >= n) continue;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int c = c0 + tx * 4 + j;
-      if (c >= q) continue;
-      float v = acc[i][j];
-      if (V) v = fmaf(alpha_col[c], V[row * ldv + c], v);
-      O[row * ldo + c] = v;
-    }
-  }
-}
-
-int tall_gemm(const float* A, const float* A2, float beta, int lda, int64_t n, int p, const float* W, int ldw, int q,
-              const float* V, int ldv, const float* alpha_col, float* O, int ldo, cudaStream_t st) {
-  dim3 grid((unsigned)((n + GT - 1) / GT), (unsigned)((q + GT - 1) / GT));
-  tall_gemm_kernel<<<grid, 256, 0, st>>>(A, A2, beta, lda, n, p, W, ldw, q, V, ldv, alpha_col, O, ldo);
+  gram_sym_kernel<<<dim3((unsigned)tiles, (unsigned)splits), 256, 0, st>>>(A, lda, n, p, tp, C, ldc, rps);
   KOP_LAUNCHED();
   return KOP_OK;
 }

@@ -7,14 +7,10 @@
 
 namespace kop {
 
-// C (p x q, FP64) = A^T B (A: n x p, B: n x q, FP32 row-major); error_free:
+// C (p x p, FP64) = A^T A (A: n x p, FP32 row-major) on the CUDA cores with
 // exact products and error-free sums within each chunk of rows (about FP64
-// accuracy, several times the FP32 work).
-int gram(const float* A, int lda, const float* B, int ldb, int64_t n, int p, int q, double* C, int ldc,
-         cudaStream_t st, bool error_free = false);
-// O = alpha_col (.) V + (A + beta A2) W   (n x q); V / A2 / alpha_col may be NULL.
-int tall_gemm(const float* A, const float* A2, float beta, int lda, int64_t n, int p, const float* W, int ldw, int q,
-              const float* V, int ldv, const float* alpha_col, float* O, int ldo, cudaStream_t st);
+// accuracy).
+int gram_sym(const float* A, int lda, int64_t n, int p, double* C, int ldc, cudaStream_t st);
 // w (p, FP64) = U^T v for one vector v (stride ldv).
 int utv(const float* U, int ldu, int64_t n, int p, const float* v, int ldv, double* w, cudaStream_t st);
 // o = alpha[0] v + U w for one vector (alpha on the device).

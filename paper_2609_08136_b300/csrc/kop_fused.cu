@@ -64,8 +64,10 @@ struct K1Layout {
   }
 };
 
-// Warp-uniform bounded wait: lane 0 polls, the outcome is broadcast.
+// Warp-uniform bounded wait: every lane polls once (no divergent branch when
+// the phase is already complete), then lane 0 polls and broadcasts.
 KOP_DEV bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort_word, int* status) {
+  if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
   bool ok = true;
   if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort_word, status);
   return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;

@@ -67,6 +67,8 @@ struct K3Layout {
 };
 
 KOP_DEV bool warp_wait3(uint64_t* bar, uint32_t parity, volatile int* abort_word, int* status) {
+  // fast path without a divergent branch: every lane polls once
+  if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
   bool ok = true;
   if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort_word, status);
   return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;

@@ -37,6 +37,9 @@ constexpr int KS_NWG = 4;    // epilogue warpgroups
 constexpr int KS_WCOLS = 128 / KS_NWG;  // query columns per warpgroup
 constexpr int KS_NCX = 4;    // slots of the column-part ring
 constexpr int KS_THREADS = 128 + 128 * KS_NWG;
+// arrivals per phase on the barriers the epilogue releases: one per warp
+// (lane 0, after the warp's reads or writes)
+constexpr int KS_ARRIVALS = 4 * KS_NWG;
 
 struct SymArgs {
   const float* snorm;  // scaled row norms, n_pad
@@ -140,10 +143,10 @@ __global__ void __launch_bounds__(KS_THREADS, 1)
     for (int s = 0; s < KS_NKV; ++s) mbar_init(&kvfull[s], 1);
     for (int b = 0; b < KS_NSB; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 128 * KS_NWG);
+      mbar_init(&tempty[b], KS_ARRIVALS);
     }
     for (int c = 0; c < KS_NCX; ++c) {
-      mbar_init(&cxfull[c], 128 * KS_NWG);
+      mbar_init(&cxfull[c], KS_ARRIVALS);
       mbar_init(&cxempty[c], 1);
     }
     mbar_init(qbar, 1);
@@ -304,7 +307,8 @@ __global__ void __launch_bounds__(KS_THREADS, 1)
           if (ch == KS_WCOLS / 32 - 1) {
             // the S buffer and the key slot are read: release them
             tc_fence_before();
-            mbar_arrive(&tempty[b]);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[b]);
           }
           const int cb = wgi * KS_WCOLS + ch * 32;
           float kv[32];
@@ -345,7 +349,8 @@ __global__ void __launch_bounds__(KS_THREADS, 1)
         live = ks_wait(&cxempty[c], cph ^ 1, abort_word, a.status);
         if (live) {
           colx[(c * KS_NWG + wgi) * 128 + kj] = col;
-          mbar_arrive(&cxfull[c]);
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&cxfull[c]);
         }
       }
     }
@@ -355,7 +360,8 @@ __global__ void __launch_bounds__(KS_THREADS, 1)
     named_bar_sync(1, 128 * KS_NWG);
     float* red = (float*)smem;
 #pragma unroll
-    for (int c = 0; c < KS_WCOLS; ++c) red[(wgi * 128 + kj) * (KS_WCOLS + 1) + c] = acc[c];
+    for (int c = 0; c < KS_WCOLS; ++c)
+      red[(wgi * 128 + kj) * (KS_WCOLS + 1) + c] = acc[c];
     named_bar_sync(1, 128 * KS_NWG);
     if (quarter < KS_WCOLS / 32) {
       const int c = quarter * 32 + lane;

@@ -9,13 +9,15 @@
 //   B^T B = C^-T (Y_nu^T Y_nu) C^-1 = V S^2 V^T
 // (Y_nu^T Y_nu = Y^T Y + nu (Omega^T Y + Y^T Omega) + nu^2 Omega^T Omega, so
 // only three r x r Gram blocks are needed), then U = Y_nu C^-1 V S^-1 is one
-// tall product.  All r x r work is FP64 on the device; the O(n r^2) Gram and
-// product passes read FP32 and accumulate in FP64 / FP32.  One Cholesky-QR
-// pass afterwards restores the orthonormality of U lost to FP32 rounding.
-// The caller's FP32 test matrix is used as given in every step: the sketch's
-// contraction carries it as a BF16 hi + lo pair (about 2^-16 relative, the
-// accuracy of the fast operator's kernel values), the Gram blocks read it in
-// FP32.
+// tall product.  All r x r work is FP64 on the device.  The O(n r^2) passes
+// (Omega^T Omega, Omega^T Y, U = Y_nu W and the Cholesky-QR products) run on
+// the tensor cores with FP32-accurate products (kop_tcgemm.cu); Y^T Y is
+// summed error-free on the CUDA cores, because the core squares the
+// condition of the sketch.  One Cholesky-QR pass afterwards restores the
+// orthonormality of U lost to FP32 rounding.  The caller's FP32 test matrix
+// is used as given in every step: the sketch's contraction carries it as a
+// BF16 hi + lo pair (about 2^-16 relative, the accuracy of the fast
+// operator's kernel values), the Gram blocks as the exact three-term split.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -58,8 +60,8 @@ __global__ void nys_scale_kernel(double* __restrict__ W, int r, int m, const dou
 // float-float arithmetic) on the stored FP32 U, so that P^-1 is applied as one
 // fixed symmetric operator: in plain FP32 the cancellation between v / rho and
 // the projected part loses a factor (lam_1 + mu) / rho of accuracy on the
-// leading subspace.  Wider blocks use FP32 tensor-shaped products (the solver
-// tolerates the inexact apply).
+// leading subspace.  Wider blocks use the tensor-core products with FP32
+// accuracy (the solver tolerates the inexact apply).
 int nys_apply_dev(const nys_s* ny, const double* mu_dev, int adaptive, const float* V, int m, float* O, double* Wd,
                   double* alpha, float* Wf, float* alpha_f, cudaStream_t st) {
   const int r = ny->r;
@@ -178,7 +180,7 @@ extern "C" int nys_build(kop_t op, const float* Omega, int32_t r, double nu_rel,
   // Y^T Y error-free: the core C^-T (Y_nu^T Y_nu) C^-1 squares the condition
   // of the sketch, and FP32 sums make its smallest eigenvalues negative once
   // the spectrum spans ~1e5
-  if ((rc = gram(Y, r, Y, r, n, r, r, Gyy, r, st, true))) return rc;
+  if ((rc = gram_sym(Y, r, n, r, Gyy, r, st))) return rc;
   // 3. ||Y||_2 by power iteration on Y^T Y
   if ((rc = power_max_eig(Gyy, r, 60, scal, st))) return rc;
   double ymax2 = 0.0;
