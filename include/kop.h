@@ -280,7 +280,11 @@ int nys_factor(nys_t ny, float* U_out, void* stream);
  * n <= 4096, else s = 1024 (ridge operators: every row).  What the check
  * operator missed lowers the column's next candidate threshold; when it is
  * above 0.8 tol^2 ||b||^2 the check operator cannot certify the tolerance and
- * the solve's later checks and refinements use KOP_EXACT.  Every `refine_every` iterations
+ * the solve's later checks and refinements use KOP_EXACT.  A periodic
+ * refinement with refine_mode == check_mode (not KOP_EXACT) evaluates the
+ * same sampled FP64 rows and predicts that miss from the check's difference
+ * to them, D = (n/s) sum (r64 - r)^2 plus the estimator's margin at the
+ * tolerance, so that the first candidate stop already allows for it.  Every `refine_every` iterations
  * (0 = only at candidate stops and at maxit) the recursive residual is
  * replaced by the true one computed with `refine_mode` (iterative refinement:
  * operator products with `inner_mode`).  Recommended: inner KOP_FAST, refine

@@ -263,13 +263,14 @@ __global__ void gather_rows_kernel(const float* __restrict__ X, int d, int64_t n
 // Per column c over the sampled rows i: with the FP64 product O64 (s x cols)
 // and the check's product T (n x 2 cols, the two columns of x's exact split),
 //   r64 = b_i - O64_kc - lam_c x_ic,  rchk = b_i - (T_i,c + T_i,cols+c) - lam_c x_ic,
-//   d = r64^2 - rchk^2;   sd_c += d, sd2_c += d^2.
+//   d = r64^2 - rchk^2;   sd_c += d, sd2_c += d^2, sd3_c += (r64 - rchk)^2.
 __global__ void __launch_bounds__(256) certify_kernel(int64_t n, int64_t s, int cols, int nrhs,
                                                       const float* __restrict__ B, const double* __restrict__ X,
                                                       const float* __restrict__ T, const double* __restrict__ O64,
-                                                      const double* __restrict__ lam, double* sd, double* sd2) {
+                                                      const double* __restrict__ lam, double* sd, double* sd2,
+                                                      double* sd3) {
   const int c = blockIdx.y * 32 + threadIdx.x;
-  double a = 0.0, a2 = 0.0;
+  double a = 0.0, a2 = 0.0, a3 = 0.0;
   if (c < cols)
     for (int64_t k = (int64_t)blockIdx.x * 8 + threadIdx.y; k < s; k += (int64_t)gridDim.x * 8) {
       const int64_t i = cert_row(k, n, s);
@@ -280,20 +281,37 @@ __global__ void __launch_bounds__(256) certify_kernel(int64_t n, int64_t s, int 
       const double dd = (r64 - rc) * (r64 + rc);
       a += dd;
       a2 += dd * dd;
+      a3 += (r64 - rc) * (r64 - rc);
     }
-  __shared__ double red[2][8][33];
+  __shared__ double red[3][8][33];
   red[0][threadIdx.y][threadIdx.x] = a;
   red[1][threadIdx.y][threadIdx.x] = a2;
+  red[2][threadIdx.y][threadIdx.x] = a3;
   __syncthreads();
   if (threadIdx.y == 0 && c < cols) {
-    double u = 0.0, u2 = 0.0;
+    double u = 0.0, u2 = 0.0, u3 = 0.0;
     for (int y = 0; y < 8; ++y) {
       u += red[0][y][threadIdx.x];
       u2 += red[1][y][threadIdx.x];
+      u3 += red[2][y][threadIdx.x];
     }
     atomicAdd(sd + c, u);
     atomicAdd(sd2 + c, u2);
+    atomicAdd(sd3 + c, u3);
   }
+}
+
+// What the check operator will miss at a stop, predicted from its difference
+// to the FP64 operator on the current iterate, D = (n / s) sum (r64 - rchk)^2
+// (relative to ||b||^2, like tol^2): at a residual near the tolerance the
+// certified excess is D plus the one-sided margin of the estimator, whose
+// variance is dominated by the cross term 2 rchk (r64 - rchk):
+//   D + kCertSigmas * 2 tol sqrt(D) sqrt(1 - s/n) / sqrt(s).
+static double predict_excess(double sd3, double nb2, double tol, int64_t n, int64_t s) {
+  const double D = (double)n / (double)s * sd3 / nb2;
+  if (s >= n) return D;
+  const double fpc = 1.0 - (double)s / (double)n;
+  return D + kCertSigmas * 2.0 * tol * std::sqrt(D * fpc / (double)s);
 }
 
 // The certified squared residual of one column from the check's all-row sum
@@ -373,7 +391,7 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
   // product (s x cols; every row of a ridge operator) and two sums per column
   const int64_t s_rows = (op->ridge || n <= kCertAll) ? n : kCertRows;
   const int dpt = op->ridge ? 0 : op->pts.d;
-  const size_t cbytes = sizeof(double) * ((size_t)s_rows * cols + 2 * (size_t)cols) +
+  const size_t cbytes = sizeof(double) * ((size_t)s_rows * cols + 3 * (size_t)cols) +
                         sizeof(float) * (size_t)s_rows * dpt + 64;
   KOP_CUDA_TRY(cudaMallocAsync(&ws.p, xbytes + dbytes + fbytes + ibytes + 256, st));
   Workspace wc;
@@ -382,7 +400,8 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
   double* O64 = (double*)wc.p;
   double* csd = O64 + (size_t)s_rows * cols;
   double* csd2 = csd + cols;
-  float* samp_x = (float*)(csd2 + cols);
+  double* csd3 = csd2 + cols;
+  float* samp_x = (float*)(csd3 + cols);
   PointSet qs;
   if (!op->ridge) {
     qs.n = s_rows;
@@ -471,11 +490,18 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
   // estimate, urel = its upper bound; excess = (ub2 - S) / ||b||^2, what the
   // check operator's residual S misses, which lowers the column's candidate
   // threshold tol^2 - excess
-  std::vector<double> hsd(cols), hsd2(cols), trel(cols, 0.0), urel(cols, 0.0), excess(cols, 0.0);
+  std::vector<double> hsd_all(3 * (size_t)cols), trel(cols, 0.0), urel(cols, 0.0), excess(cols, 0.0);
+  const double* hsd = hsd_all.data();              // sum d
+  const double* hsd2 = hsd_all.data() + cols;      // sum d^2
+  const double* hsd3 = hsd_all.data() + 2 * cols;  // sum (r64 - rchk)^2
   // The true residual r = b - (A + lam I) x with the operator `mode` replaces
   // R; with `certify`, a non-FP64 check is corrected by the sampled FP64
-  // residual.  Fills trel / urel / excess for the active columns.
-  auto true_residual = [&](int mode, bool certify) -> int {
+  // residual.  Fills trel / urel / excess for the active columns; with
+  // `predict` (a refinement far from the tolerance, where the correction's
+  // margin would be dominated by the residual itself) excess is instead the
+  // prediction of what the check will miss at a stop (predict_excess), so
+  // that the first candidate stop already leaves room for it.
+  auto true_residual = [&](int mode, bool certify, bool predict = false) -> int {
     int rmode = mode == KOP_PLAIN ? KOP_PLAIN_CHECK : mode;
     const bool exact = rmode == KOP_EXACT;
     if (exact) {
@@ -499,15 +525,14 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
       } else {
         if ((rc = cert_matvec(qs, op->pts, op->kernel, op->bw, X, cols, cols, O64, cols, st))) return rc;
       }
-      KOP_CUDA_TRY(cudaMemsetAsync(csd, 0, sizeof(double) * 2 * cols, st));
+      KOP_CUDA_TRY(cudaMemsetAsync(csd, 0, sizeof(double) * 3 * cols, st));
       const unsigned gy = (unsigned)((cols + 31) / 32);
       int64_t gx = (s_rows + 7) / 8;
       if (gx > 2 * num_sms()) gx = 2 * num_sms();
       certify_kernel<<<dim3((unsigned)gx, gy), dim3(32, 8), 0, st>>>(n, s_rows, cols, pb.nrhs, pb.B, X, T, O64, lam,
-                                                                    csd, csd2);
+                                                                    csd, csd2, csd3);
       KOP_LAUNCHED();
-      KOP_CUDA_TRY(cudaMemcpyAsync(hsd.data(), csd, sizeof(double) * cols, cudaMemcpyDeviceToHost, st));
-      KOP_CUDA_TRY(cudaMemcpyAsync(hsd2.data(), csd2, sizeof(double) * cols, cudaMemcpyDeviceToHost, st));
+      KOP_CUDA_TRY(cudaMemcpyAsync(hsd_all.data(), csd, sizeof(double) * 3 * cols, cudaMemcpyDeviceToHost, st));
     }
     KOP_CUDA_TRY(cudaStreamSynchronize(st));
     for (int c = 0; c < cols; ++c) {
@@ -517,7 +542,8 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
       if (corr) ct = certify_column(hr[c], hsd[c], hsd2[c], n, s_rows);
       trel[c] = std::sqrt(ct.est2 / nb2);
       urel[c] = std::sqrt(ct.ub2 / nb2);
-      if (corr) excess[c] = (ct.ub2 - hr[c]) / nb2 > 0.0 ? (ct.ub2 - hr[c]) / nb2 : 0.0;
+      if (corr && predict) excess[c] = predict_excess(hsd3[c], nb2, pb.tol, n, s_rows);
+      else if (corr) excess[c] = (ct.ub2 - hr[c]) / nb2 > 0.0 ? (ct.ub2 - hr[c]) / nb2 : 0.0;
       else if (exact) excess[c] = 0.0;
     }
     return KOP_OK;
@@ -619,7 +645,10 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
       // for periodic replacement, the check operator (certified) when a
       // column may stop
       const bool stopping = any_cand || it == pb.maxit;
-      if ((rc = true_residual(stopping ? pb.check_mode : pb.refine_mode, stopping))) return rc;
+      // a periodic refinement with the check operator itself also predicts
+      // what that operator will miss at the stops
+      const bool predict = !stopping && pb.refine_mode == pb.check_mode && pb.check_mode != KOP_EXACT;
+      if ((rc = true_residual(stopping ? pb.check_mode : pb.refine_mode, stopping || predict, predict))) return rc;
       any = false;
       bool escalate = false;
       for (int c = 0; c < cols; ++c) {
@@ -628,7 +657,7 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
         if (cand[c] && urel[c] <= pb.tol) {
           act[c] = 0;
           if (pb.iters) pb.iters[c] = it;
-        } else if (stopping && excess[c] > kEscalate * tol2) {
+        } else if ((stopping || predict) && excess[c] > kEscalate * tol2) {
           // any active column, candidate or not: its threshold tol^2 - excess
           // would otherwise leave it no room to become a candidate again
           escalate = true;
