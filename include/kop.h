@@ -276,8 +276,11 @@ int nys_factor(nys_t ny, float* U_out, void* stream);
  * k < s, corrects it by the difference estimator
  *     est^2 = sum_i r_i^2 + (n/s) sum_k (r64_ik^2 - r_ik^2)
  * and the column is accepted when est^2 plus three standard errors of the
- * correction is <= tol^2 ||b||^2.  s = n (every row: the test is exact) for
- * n <= 4096, else s = 1024 (ridge operators: every row).  What the check
+ * correction is <= tol^2 ||b||^2.  s = n for n <= 4096, else s = 1024
+ * (ridge operators: every row); when s = n the FP64 residual of every row is
+ * the true residual itself (the test is exact and `check_mode` is not run).
+ * The solver's FP64 residuals take kernel values in FP64 from error-free FP32
+ * distances (about 2^-44 relative in D^2).  What the check
  * operator missed lowers the column's next candidate threshold; when it is
  * above 0.8 tol^2 ||b||^2 the check operator cannot certify the tolerance and
  * the solve's later checks and refinements use KOP_EXACT.  A periodic

@@ -503,45 +503,137 @@ int combine(const double* Goo, const double* Goy, const double* Gyy, int r, doub
 }
 
 // In-place lower Cholesky A = L L^T (row-major r x r; the strict upper part is
-// zeroed).  One CTA, right-looking.  info[0] = 0 on success, k + 1 if pivot k
-// is not positive (or not finite).
-__global__ void __launch_bounds__(1024) cholesky_kernel(double* A, int r, int* info) {
+// zeroed), blocked by CH_NB columns: per block column k0, (1) one CTA factors
+// the CH_NB x CH_NB diagonal block in shared memory, (2) the rows below solve
+// x L_kk^T = a (one thread per row), (3) the trailing lower triangle takes the
+// rank-CH_NB update on 32 x 32 tiles.  info[0] = 0 on success, k + 1 if pivot
+// k is not positive (or not finite); the later kernels then return at once.
+constexpr int CH_NB = 64;
+
+__global__ void __launch_bounds__(1024) chol_diag_kernel(double* A, int r, int k0, int nb, int* info) {
+  __shared__ double D[CH_NB][CH_NB + 1];
   __shared__ int bad;
+  if (*(volatile int*)info) return;  // uniform: every thread reads the same word
+  for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+    const int i = t / nb, j = t - i * nb;
+    D[i][j] = A[(int64_t)(k0 + i) * r + k0 + j];
+  }
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
-  for (int k = 0; k < r; ++k) {
+  for (int k = 0; k < nb; ++k) {
     if (threadIdx.x == 0) {
-      const double akk = A[(int64_t)k * r + k];
-      if (!(akk > 0.0) || !isfinite(akk)) {
-        bad = k + 1;
-      } else {
-        A[(int64_t)k * r + k] = sqrt(akk);
-      }
+      const double akk = D[k][k];
+      if (!(akk > 0.0) || !isfinite(akk)) bad = k0 + k + 1;
+      else D[k][k] = sqrt(akk);
     }
     __syncthreads();
     if (bad) break;
-    const double lkk = A[(int64_t)k * r + k];
-    for (int i = k + 1 + threadIdx.x; i < r; i += blockDim.x) A[(int64_t)i * r + k] /= lkk;
+    for (int i = k + 1 + threadIdx.x; i < nb; i += blockDim.x) D[i][k] /= D[k][k];
     __syncthreads();
-    // trailing update of the lower triangle: A[i][j] -= L[i][k] L[j][k], k < j <= i;
-    // one warp per row, lanes along j
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int i = k + 1 + warp; i < r; i += nw) {
-      const double lik = A[(int64_t)i * r + k];
-      for (int j = k + 1 + lane; j <= i; j += 32) A[(int64_t)i * r + j] -= lik * A[(int64_t)j * r + k];
+    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+      const int i = t / nb, j = t - i * nb;
+      if (j > k && j <= i) D[i][j] -= D[i][k] * D[j][k];
     }
     __syncthreads();
   }
-  __syncthreads();
-  for (int64_t t = threadIdx.x; t < (int64_t)r * r; t += blockDim.x) {
-    const int i = (int)(t / r), j = (int)(t - (int64_t)i * r);
-    if (j > i) A[t] = 0.0;
+  for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+    const int i = t / nb, j = t - i * nb;
+    if (j <= i) A[(int64_t)(k0 + i) * r + k0 + j] = D[i][j];
   }
-  if (threadIdx.x == 0) info[0] = bad;
+  if (threadIdx.x == 0 && bad) *info = bad;
+}
+
+__global__ void __launch_bounds__(128) chol_panel_kernel(double* A, int r, int k0, int nb, const int* info) {
+  __shared__ double L[CH_NB][CH_NB + 1];
+  if (*(volatile const int*)info) return;
+  for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+    const int i = t / nb, j = t - i * nb;
+    L[i][j] = j <= i ? A[(int64_t)(k0 + i) * r + k0 + j] : 0.0;
+  }
+  __syncthreads();
+  const int row = k0 + nb + blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= r) return;
+  double* a = A + (int64_t)row * r + k0;
+  double x[CH_NB];
+#pragma unroll
+  for (int j = 0; j < CH_NB; ++j)
+    if (j < nb) x[j] = a[j];
+#pragma unroll
+  for (int j = 0; j < CH_NB; ++j) {
+    if (j < nb) {
+      double s = x[j];
+#pragma unroll
+      for (int t = 0; t < j; ++t) s -= L[j][t] * x[t];
+      x[j] = s / L[j][j];
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < CH_NB; ++j)
+    if (j < nb) a[j] = x[j];
+}
+
+// trailing update of the lower triangle rows / columns [k1, r), k1 = k0 + nb:
+// A[i][j] -= sum_t A[i][k0 + t] A[j][k0 + t]; one CTA per 32 x 32 tile with
+// ti >= tj, 256 threads with 4 outputs each
+__global__ void __launch_bounds__(256) chol_update_kernel(double* A, int r, int k0, int nb, int tiles,
+                                                          const int* info) {
+  __shared__ double Pi[32][CH_NB + 1];
+  __shared__ double Pj[32][CH_NB + 1];
+  if (*(volatile const int*)info) return;
+  int ti = 0, idx = blockIdx.x;
+  while (idx > ti) {  // tile (ti, tj), tj <= ti, row-major over the lower triangle
+    idx -= ti + 1;
+    ++ti;
+  }
+  const int tj = idx;
+  const int k1 = k0 + nb;
+  const int i0 = k1 + 32 * ti, j0 = k1 + 32 * tj;
+  for (int t = threadIdx.x; t < 32 * nb; t += blockDim.x) {
+    const int rr = t / nb, c = t - rr * nb;
+    Pi[rr][c] = i0 + rr < r ? A[(int64_t)(i0 + rr) * r + k0 + c] : 0.0;
+    Pj[rr][c] = j0 + rr < r ? A[(int64_t)(j0 + rr) * r + k0 + c] : 0.0;
+  }
+  __syncthreads();
+  const int ty = threadIdx.x >> 3, tx = threadIdx.x & 7;  // rows ty, cols tx + 8 q
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int c = 0; c < nb; ++c) {
+    const double ai = Pi[ty][c];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = fma(ai, Pj[tx + 8 * q][c], acc[q]);
+  }
+  const int i = i0 + ty;
+  if (i >= r) return;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int j = j0 + tx + 8 * q;
+    if (j < r && j <= i) A[(int64_t)i * r + j] -= acc[q];
+  }
+}
+
+__global__ void zero_upper_kernel(double* A, int r) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)r * r) return;
+  const int i = (int)(t / r), j = (int)(t - (int64_t)i * r);
+  if (j > i) A[t] = 0.0;
 }
 
 int cholesky(double* A, int r, int* info, cudaStream_t st) {
-  cholesky_kernel<<<1, 1024, 0, st>>>(A, r, info);
+  KOP_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int), st));
+  for (int k0 = 0; k0 < r; k0 += CH_NB) {
+    const int nb = r - k0 < CH_NB ? r - k0 : CH_NB;
+    chol_diag_kernel<<<1, 1024, 0, st>>>(A, r, k0, nb, info);
+    KOP_LAUNCHED();
+    const int rest = r - k0 - nb;
+    if (rest <= 0) break;
+    chol_panel_kernel<<<(unsigned)((rest + 127) / 128), 128, 0, st>>>(A, r, k0, nb, info);
+    KOP_LAUNCHED();
+    const int tr = (rest + 31) / 32;
+    const int tiles = tr * (tr + 1) / 2;
+    chol_update_kernel<<<(unsigned)tiles, 256, 0, st>>>(A, r, k0, nb, tiles, info);
+    KOP_LAUNCHED();
+  }
+  const int64_t tot = (int64_t)r * r;
+  zero_upper_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(A, r);
   KOP_LAUNCHED();
   return KOP_OK;
 }
@@ -598,59 +690,78 @@ int transpose(const double* A, int r, double* B, int sym, cudaStream_t st) {
 }
 
 // Largest eigenvalue of a symmetric psd r x r matrix by power iteration (one
-// CTA, FP64).  out[0] = Rayleigh quotient after `iters` steps.
-__global__ void __launch_bounds__(1024) power_kernel(const double* __restrict__ G, int r, int iters, double* out) {
-  extern __shared__ double pv[];  // 2r
+// CTA, FP64).  Thread i forms w_i = sum_k G[k][i] v_k (G is symmetric, so the
+// reads along i are coalesced); G is staged in shared memory when it fits.
+// out[0] = the Rayleigh quotient after `iters` steps, or once it changes by
+// less than 1e-10 of itself between steps.
+__global__ void __launch_bounds__(1024) power_kernel(const double* __restrict__ G, int r, int iters, int cached,
+                                                     double* out) {
+  extern __shared__ double pv[];  // v (r), w (r), [G (r x r)]
   double* v = pv;
   double* w = pv + r;
-  __shared__ double red[32];
-  __shared__ double scal;
+  const double* M = G;
+  if (cached) {
+    double* Gs = pv + 2 * r;
+    for (int64_t t = threadIdx.x; t < (int64_t)r * r; t += blockDim.x) Gs[t] = G[t];
+    M = Gs;
+  }
+  __shared__ double red[3][32];
+  __shared__ double tot[3];
   for (int i = threadIdx.x; i < r; i += blockDim.x) v[i] = 1.0 + 0.01 * (double)(i % 7);
   __syncthreads();
   double lam = 0.0;
   for (int it = 0; it < iters; ++it) {
     for (int i = threadIdx.x; i < r; i += blockDim.x) {
       double s = 0.0;
-      for (int k = 0; k < r; ++k) s += G[(int64_t)i * r + k] * v[k];
+      for (int k = 0; k < r; ++k) s = fma(M[(int64_t)k * r + i], v[k], s);
       w[i] = s;
     }
     __syncthreads();
     // lam = v.w / v.v ; v = w / |w|
-    double vw = 0.0, vv = 0.0, ww = 0.0;
+    double vals[3] = {0.0, 0.0, 0.0};
     for (int i = threadIdx.x; i < r; i += blockDim.x) {
-      vw += v[i] * w[i];
-      vv += v[i] * v[i];
-      ww += w[i] * w[i];
+      vals[0] += v[i] * w[i];
+      vals[1] += v[i] * v[i];
+      vals[2] += w[i] * w[i];
     }
-    double vals[3] = {vw, vv, ww};
-    double tot[3];
+#pragma unroll
     for (int c = 0; c < 3; ++c) {
-      double x = vals[c];
-      for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
-      __syncthreads();
-      if (threadIdx.x < 32) {
-        double y = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-        for (int off = 16; off > 0; off >>= 1) y += __shfl_xor_sync(0xffffffffu, y, off);
-        if (threadIdx.x == 0) scal = y;
-      }
-      __syncthreads();
-      tot[c] = scal;
-      __syncthreads();
+      for (int off = 16; off > 0; off >>= 1) vals[c] += __shfl_xor_sync(0xffffffffu, vals[c], off);
+      if ((threadIdx.x & 31) == 0) red[c][threadIdx.x >> 5] = vals[c];
     }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        double y = threadIdx.x < (blockDim.x >> 5) ? red[c][threadIdx.x] : 0.0;
+        for (int off = 16; off > 0; off >>= 1) y += __shfl_xor_sync(0xffffffffu, y, off);
+        if (threadIdx.x == 0) tot[c] = y;
+      }
+    }
+    __syncthreads();
+    const double prev = lam;
     lam = tot[1] > 0.0 ? tot[0] / tot[1] : 0.0;
     const double inv = tot[2] > 0.0 ? 1.0 / sqrt(tot[2]) : 0.0;
     for (int i = threadIdx.x; i < r; i += blockDim.x) v[i] = w[i] * inv;
     __syncthreads();
+    if (it > 0 && fabs(lam - prev) <= 1e-10 * fabs(lam)) break;  // uniform: every thread reads tot
   }
   if (threadIdx.x == 0) out[0] = lam;
 }
 
 int power_max_eig(const double* G, int r, int iters, double* out, cudaStream_t st) {
-  const size_t smem = sizeof(double) * 2 * r;
-  if (smem > 48 * 1024) KOP_CUDA_TRY(cudaFuncSetAttribute(power_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                          (int)smem));
-  power_kernel<<<1, 1024, smem, st>>>(G, r, iters, out);
+  // dynamic shared memory: at most the per-CTA limit less the kernel's
+  // static reduction arrays
+  const size_t dyn_limit = smem_limit_bytes() - 1024;
+  const size_t base = sizeof(double) * 2 * r;
+  const bool cached = base + sizeof(double) * (size_t)r * r <= dyn_limit;
+  const size_t smem = cached ? base + sizeof(double) * (size_t)r * r : base;
+  static bool attr = false;
+  if (!attr) {
+    KOP_CUDA_TRY(cudaFuncSetAttribute(power_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_limit));
+    attr = true;
+  }
+  power_kernel<<<1, 1024, smem, st>>>(G, r, iters, cached ? 1 : 0, out);
   KOP_LAUNCHED();
   return KOP_OK;
 }
@@ -719,12 +830,17 @@ KOP_DEV bool grid_barrier(unsigned int* count, unsigned int* gen, unsigned int n
   return ok_s != 0;
 }
 
-__global__ void __launch_bounds__(256) jacobi_kernel(JacobiArgs a) {
+// Block shape: every CTA recomputes the step's rotations (FP64 square roots
+// and divisions, slow on this part), so large matrices run one CTA of 512
+// threads per SM; small ones two of 256 (measured: r = 500 223 vs 240 ms per
+// build, r = 100 7.1 vs 7.8 ms).
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) jacobi_kernel(JacobiArgs a) {
   extern __shared__ double js[];
   double* ca = js;            // re: a_i
   double* cb = js + a.re;     // re: b_i
   int* partner = (int*)(js + 2 * a.re);
-  __shared__ double red[2][8];
+  __shared__ double red[2][THREADS / 32];
   const int re = a.re;
   const unsigned int nblocks = gridDim.x;
   const int64_t tot = (int64_t)re * re;
@@ -865,17 +981,19 @@ int sym_eig(const double* H, int r, double* work, int* status, double* evals_out
   a.status = status;
   a.sweeps_done = sweeps;
   const size_t smem = sizeof(double) * 2 * re + sizeof(int) * re;
-  if (smem > 48 * 1024)
-    KOP_CUDA_TRY(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const bool big = re >= 256;
+  const void* fn = big ? (const void*)jacobi_kernel<512> : (const void*)jacobi_kernel<256>;
+  const int threads = big ? 512 : 256, per_sm_max = big ? 1 : 2;
+  if (smem > 48 * 1024) KOP_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  KOP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, 256, smem));
+  KOP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem));
   if (per_sm < 1) return fail(KOP_ECUDA, "jacobi: kernel does not fit on an SM");
-  int blocks = num_sms() * (per_sm < 2 ? per_sm : 2);
-  const int64_t want = (int64_t)((rr + 255) / 256);
+  int blocks = num_sms() * (per_sm < per_sm_max ? per_sm : per_sm_max);
+  const int64_t want = (int64_t)((rr + threads - 1) / threads);
   if (want < blocks) blocks = (int)want;
   if (blocks < 1) blocks = 1;
   void* args[] = {&a};
-  KOP_CUDA_TRY(cudaLaunchCooperativeKernel((void*)jacobi_kernel, dim3(blocks), dim3(256), args, smem, st));
+  KOP_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(threads), args, smem, st));
   note_launch();
   // unpad: eigenvalues = diag(A)[0..r), eigenvectors = V[0..r, 0..r)
   extract_eig(A, V, r, re, evals_out, evecs_out, st);

@@ -77,9 +77,17 @@ struct KSLayout {
   }
 };
 
-// Warp-uniform bounded wait; the common case (the phase has completed) costs
-// one try_wait and one vote.
+// Warp-uniform bounded wait of the epilogue warps; the common case (the phase
+// has completed) costs one try_wait and one vote; a warp that has run ahead
+// of the others backs off instead of taking issue slots from them.
 KOP_DEV bool ks_wait(uint64_t* bar, uint32_t parity, volatile int* abort_word, int* status) {
+  if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
+  bool ok = true;
+  if ((threadIdx.x & 31) == 0) ok = mbar_wait_backoff(bar, parity, abort_word, status);
+  return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+}
+// The MMA warp's wait: it is on the critical path, so it never sleeps.
+KOP_DEV bool ks_wait_spin(uint64_t* bar, uint32_t parity, volatile int* abort_word, int* status) {
   if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
   bool ok = true;
   if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort_word, status);
@@ -216,14 +224,14 @@ __global__ void __launch_bounds__(KS_THREADS, 1)
     const uint64_t dq0 = sdesc(smem_u32(qs), sbo, a.swz);
     const uint64_t dx0 = sdesc(smem_u32(xs), sbo, a.swz);
     const uint32_t split16 = L.q_split >> 4, sub16 = (128u * rb) >> 4;
-    bool ok = ks_wait(qbar, 0, abort_word, a.status);
+    bool ok = ks_wait_spin(qbar, 0, abort_word, a.status);
     int s = 0;
     uint32_t ph = 0;
     for (int t = 0; ok && t < cnt; ++t) {
       const int b = t % KS_NSB;
       const uint32_t bph = (t / KS_NSB) & 1;
-      if (!ks_wait(&full[s], ph, abort_word, a.status)) break;
-      if (!ks_wait(&tempty[b], bph ^ 1, abort_word, a.status)) break;
+      if (!ks_wait_spin(&full[s], ph, abort_word, a.status)) break;
+      if (!ks_wait_spin(&tempty[b], bph ^ 1, abort_word, a.status)) break;
       tc_fence_after();
       const uint32_t d = tmem + b * 128;
       const uint64_t xb = dx0 + (uint64_t)(s * NSPLIT) * split16;

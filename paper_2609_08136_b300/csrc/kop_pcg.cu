@@ -503,14 +503,24 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
   // that the first candidate stop already leaves room for it.
   auto true_residual = [&](int mode, bool certify, bool predict = false) -> int {
     int rmode = mode == KOP_PLAIN ? KOP_PLAIN_CHECK : mode;
-    const bool exact = rmode == KOP_EXACT;
+    // when the certification reads every row anyway (n <= kCertAll, ridge
+    // operators), its FP64 product is the true residual itself and the check
+    // operator is not run
+    const bool exact = rmode == KOP_EXACT || ((certify || predict) && s_rows == n);
     if (exact) {
       if (!T64) {
         KOP_CUDA_TRY(cudaMallocAsync(&wx.p, sizeof(double) * nc, st));
         T64 = (double*)wx.p;
         va.T64 = T64;
       }
-      if ((rc = op_apply_f64(op, X, cols, cols, T64, cols, st))) return rc;
+      // FP64 product: kernel values in FP64 from error-free FP32 distances
+      // (about 2^-44 relative in D^2; FP64 distances are several times
+      // slower on this part)
+      if (op->ridge) {
+        if ((rc = op_apply_f64(op, X, cols, cols, T64, cols, st))) return rc;
+      } else {
+        if ((rc = cert_matvec(op->pts, op->pts, op->kernel, op->bw, X, cols, cols, T64, cols, st))) return rc;
+      }
       if ((rc = vec_launch<OP_RES64>(va, st))) return rc;
     } else {
       if ((rc = vec_launch<OP_SPLIT>(va, st))) return rc;
