@@ -9,21 +9,21 @@
 namespace kop {
 
 int op_matvec(const PointSet& Q, const PointSet& Ks, bool self, int kf, const KConst& kc, int mode,
-              const float* V, int m, int ldv, float* O, int ldo, int* status, cudaStream_t st, bool v_bf16_exact) {
+              const float* V, int m, int ldv, float* O, int ldo, int* status, cudaStream_t st, bool sketch) {
   if (kf >= KF_GRBF && (mode == KOP_PLAIN || mode == KOP_PLAIN_CHECK))
     return fail(KOP_EINVAL, "point-gradient products run in the FAST, ACCURATE or EXACT mode");
   if (mode == KOP_PLAIN) return plain_matvec(Q, Ks, self, kf, kc, V, m, ldv, O, ldo, st);
   if (mode == KOP_PLAIN_CHECK) return plain_matvec(Q, Ks, self, kf, kc, V, m, ldv, O, ldo, st, true);
   if (mode == KOP_EXACT) return exact_matvec_f32(Q, Ks, kf, kc.bw, V, m, ldv, O, ldo, st);
   return fused_matvec(Q, Ks, self, kf, kc, mode == KOP_ACCURATE ? 3 : 2, V, m, ldv, O, ldo, status, st,
-                      v_bf16_exact);
+                      sketch);
 }
 
 int op_apply(kop_s* op, int mode, const float* V, int m, int ldv, float* O, int ldo, cudaStream_t st,
-             bool v_bf16_exact) {
+             bool sketch) {
   if (op->ridge) return ridge_apply(op, mode, V, m, ldv, O, ldo, st);
   const KConst kc = kernel_constants(op->kernel, op->bw);
-  return op_matvec(op->pts, op->pts, true, op->kernel, kc, mode, V, m, ldv, O, ldo, op->status, st, v_bf16_exact);
+  return op_matvec(op->pts, op->pts, true, op->kernel, kc, mode, V, m, ldv, O, ldo, op->status, st, sketch);
 }
 
 int op_apply_f64(kop_s* op, const double* V, int m, int ldv, double* O, int ldo, cudaStream_t st) {

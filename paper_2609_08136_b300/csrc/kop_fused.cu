@@ -491,11 +491,11 @@ static int launch_fma_kf(int nsplit, int bn, int mv, const PointSet& Q, const Po
 }
 
 int fused_matvec(const PointSet& Q, const PointSet& Ks, bool self, int kf, const KConst& kc, int nsplit,
-                 const float* V, int m, int ldv, float* O, int ldo, int* status, cudaStream_t st, bool v_bf16_exact) {
+                 const float* V, int m, int ldv, float* O, int ldo, int* status, cudaStream_t st, bool sketch) {
   if (Q.dp != Ks.dp) return fail(KOP_EINVAL, "fused_matvec: point sets of different widths");
   if (Q.n == 0 || Ks.n == 0 || m == 0) return KOP_OK;
   if (m > 8 && nsplit == 2)
-    return fused_matvec_mma(Q, Ks, self, kf, kc, V, m, ldv, O, ldo, status, st, v_bf16_exact);
+    return fused_matvec_mma(Q, Ks, self, kf, kc, V, m, ldv, O, ldo, status, st, sketch);
   const int dp = Q.dp;
   const size_t lim = smem_limit_bytes();
   // tile width: 128 points where a 2-stage X ring fits, else 64.  (256-point

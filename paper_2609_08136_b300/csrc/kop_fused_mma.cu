@@ -5,19 +5,22 @@
 // the sketch Y = K Omega of the Nystrom preconditioner is this product with
 // m = r), but after the epilogue has turned the distance tile S into kernel
 // values K_IJ in registers, it writes them back into the same TMEM columns as
-// a BF16 hi/lo pair (K = hi + lo to about 2^-16), and one thread issues
+// a 16-bit hi/lo pair, and one thread issues
 //   O += K_lo V_hi + K_hi V_lo + K_hi V_hi
-// with A read from TMEM and V^T (split into BF16 hi/lo by a prep kernel) read
+// with A read from TMEM and V^T (split into hi/lo by a prep kernel) read
 // from shared memory.  O (128 rows x MC columns, FP32) stays in TMEM for the
-// whole sweep over X and is written once at the end.  Tiles of 64 points.
+// whole sweep over X (restarted every few tiles into a running sum, see
+// K3_DRAIN) and is written once at the end.  Tiles of 64 points.  Kernel
+// values (in [0, 1]) and V (scaled per column by a power of two) travel as
+// FP16 hi / lo pairs, 22 significant bits; derivative kernels as BF16 pairs.
 // S has four TMEM buffers and the MMA warp issues PV(t) before S(t+3), so the
 // tensor pipe works on one tile's contraction while two pairs of epilogue
 // warpgroups (even and odd tiles) turn the next tiles' distances into kernel
 // values.  Two producer warps keep three rings filled: X tiles (released as
 // soon as their distance MMAs finish), the X tiles' norms (read by the
-// epilogue) and V tiles (released by the contraction).  When V holds BF16-exact
-// values (the Nystrom test matrix is rounded once on entry) its lo split is
-// skipped: half the V traffic and two contraction MMAs instead of three.
+// epilogue) and V tiles (released by the contraction).
+#include <cuda_fp16.h>
+
 #include "kop_device.cuh"
 #include "kop_epilogue.cuh"
 #include "kop_internal.h"
@@ -36,6 +39,17 @@ constexpr int K3_NSB = 4;  // S buffers in TMEM (even: a buffer always serves th
 // issued after the contraction of tile t + K3_NKS - nx - lookahead >= t, which
 // waited for the epilogue of tile t; so K3_NKS >= K3_MAXX + K3_NSB - 1.
 constexpr int K3_NKS = 8;
+// The tensor core truncates when it adds to an FP32 accumulator, so a long
+// chain of MMAs into O drifts towards zero (about 2^-24 of |O| per MMA, 12
+// MMAs per tile: measured -6e-4 relative at n = 1e5, enough to make
+// K + lam I indefinite for lam = 1e-3 there).  For the solver's products O is
+// therefore restarted every K3_DRAIN tiles and its partials summed, rounding
+// to nearest, into a running sum in TMEM (128-column chunks; measured bias
+// -7e-7).  The Nystrom sketch keeps one accumulator and 256-column chunks:
+// its drift rescales the sketch by the same relative amount, which the
+// randomized preconditioner does not notice, and the narrower chunks would
+// double its distance and kernel-value work.
+constexpr int K3_DRAIN = 4;
 static_assert(K3_NKS >= K3_MAXX + K3_NSB - 1, "norm ring too shallow");
 
 struct MmaArgs {
@@ -47,6 +61,13 @@ struct MmaArgs {
   int m_pad;  // rows of one blocked V^T tile (all column chunks)
   float m2c, c2;
   int* status;
+  // contraction in FP16 hi / lo pairs (kernel values in [0, 1]) with V scaled
+  // per column by an exact power of two; inv_scale[c] undoes it on output
+  int f16;
+  const float* inv_scale;
+  // O is restarted every `drain` tiles (0: never) and its partial added to a
+  // running sum in TMEM (columns OCOL + mc .., so mc <= 128)
+  int drain;
 };
 
 struct K3Layout {
@@ -60,7 +81,7 @@ struct K3Layout {
     vs = xs + nx * 2 * x_split;
     kn = vs + nv * vsplits * v_split;
     bars = kn + K3_NKS * K3_BN * 4;
-    holder = bars + (2 * K3_MAXX + 2 * K3_MAXV + K3_NKS + 3 * K3_NSB + 4) * 8;
+    holder = bars + (2 * K3_MAXX + 2 * K3_MAXV + K3_NKS + 3 * K3_NSB + 6) * 8;
     abort_word = holder + 4;
     total = abort_word + 12;
   }
@@ -108,6 +129,8 @@ __global__ void __launch_bounds__(K3_THREADS, 1)
   uint64_t* qbar = sfree + K3_NSB;
   uint64_t* ofull = qbar + 1;
   uint64_t* drain = ofull + 1;
+  uint64_t* opart = drain + 1;  // O holds the partial of the last K3_DRAIN tiles
+  uint64_t* odone = opart + 1;  // the epilogue has added it to the output
   uint32_t* holder = (uint32_t*)(smem + L.holder);
   volatile int* abort_word = (volatile int*)(smem + L.abort_word);
 
@@ -142,6 +165,8 @@ __global__ void __launch_bounds__(K3_THREADS, 1)
     mbar_init(qbar, 1);
     mbar_init(ofull, 1);
     mbar_init(drain, 1);
+    mbar_init(opart, 1);
+    mbar_init(odone, 16);
     *abort_word = 0;
     fence_mbar_init();
   }
@@ -211,7 +236,7 @@ __global__ void __launch_bounds__(K3_THREADS, 1)
     // 128 x 64 x 16 distance step), so the loop only adds constant offsets to
     // descriptors prepared here, and ring slots and phases are counters.
     const uint32_t idesc_s = idesc_bf16_f32(128, K3_BN);
-    const uint32_t idesc_o = idesc_bf16_f32(128, a.mc);
+    const uint32_t idesc_o = a.f16 ? idesc_f16_f32(128, a.mc) : idesc_bf16_f32(128, a.mc);
     const uint32_t sbo = 8u * rb;
     const int nks = a.dp / 16;  // K steps of 16 over the padded feature width
     const uint64_t dq_hi = sdesc(smem_u32(qs), sbo, a.swz);
@@ -233,6 +258,11 @@ __global__ void __launch_bounds__(K3_THREADS, 1)
         const int b = u & (K3_NSB - 1);
         if (!warp_wait3(&vfull[sv], phv, abort_word, a.status)) { ok = false; break; }
         if (!warp_wait3(&pfull[b], (u / K3_NSB) & 1, abort_word, a.status)) { ok = false; break; }
+        if (a.drain && u > 0 && u % a.drain == 0) {
+          // the epilogue has drained O: the next partial starts from zero
+          if (!warp_wait3(odone, ((u / a.drain) - 1) & 1, abort_word, a.status)) { ok = false; break; }
+          oacc = 0;
+        }
         tc_fence_after();
         {
           // (P split, V split): lo*hi, hi*hi [, hi*lo]; P hi at +0, lo at +16 of each 32-column chunk
@@ -253,6 +283,7 @@ __global__ void __launch_bounds__(K3_THREADS, 1)
           }
           tc_commit_elect(&sfree[b]);
           tc_commit_elect(&vempty[sv]);
+          if (a.drain && (u + 1) % a.drain == 0 && u + 1 < ntiles) tc_commit_elect(opart);
         }
         __syncwarp();
         if (++sv == nv) { sv = 0; phv ^= 1u; }
@@ -294,8 +325,71 @@ __global__ void __launch_bounds__(K3_THREADS, 1)
     const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
     bool ok = true;
     const float qni = a.qnorm[gi];
+    // O is drained every a.drain tiles into a running sum in TMEM (rounding to
+    // nearest); the final write outputs O + sum.  Warpgroup q = ep / 4 takes
+    // columns [q mc / 4, (q + 1) mc / 4) of its rows in every drain and in
+    // the final write.
+    const int q4 = ep >> 2, mq = a.mc / 4;
+    const uint32_t OSUM = OCOL + (uint32_t)a.mc;
+    int ndrained = 0;
+    // O (+ the running sum, once there is one) to the output
+    auto flush = [&]() {
+      for (int c0 = q4 * mq; c0 < (q4 + 1) * mq; c0 += 16) {
+        uint32_t r[16];
+        tmem_ld16(lane_addr + OCOL + c0, r);
+        if (ndrained > 0) {
+          uint32_t sm[16];
+          tmem_ld16(lane_addr + OSUM + c0, sm);
+          tmem_ld_wait16(sm);
+          tmem_ld_wait16(r);
+#pragma unroll
+          for (int c = 0; c < 16; ++c) r[c] = __float_as_uint(__uint_as_float(r[c]) + __uint_as_float(sm[c]));
+        } else {
+          tmem_ld_wait16(r);
+        }
+        if (gi < a.nq && !*abort_word) {
+          float* orow = a.O + (int64_t)gi * a.ldo + m0 + c0;
+          const float* isc = a.inv_scale + m0 + c0;
+#pragma unroll
+          for (int c = 0; c < 16; ++c)
+            if (m0 + c0 + c < a.m) orow[c] = a.f16 ? __uint_as_float(r[c]) * isc[c] : __uint_as_float(r[c]);
+        }
+      }
+    };
+    // one drain: the running sum takes O
+    auto drain_once = [&]() {
+      for (int c0 = q4 * mq; c0 < (q4 + 1) * mq; c0 += 16) {
+        uint32_t r[16];
+        tmem_ld16(lane_addr + OCOL + c0, r);
+        if (ndrained > 0) {
+          uint32_t sm[16];
+          tmem_ld16(lane_addr + OSUM + c0, sm);
+          tmem_ld_wait16(sm);
+          tmem_ld_wait16(r);
+#pragma unroll
+          for (int c = 0; c < 16; ++c) r[c] = __float_as_uint(__uint_as_float(r[c]) + __uint_as_float(sm[c]));
+        } else {
+          tmem_ld_wait16(r);
+        }
+        tmem_st16(lane_addr + OSUM + c0, r);
+      }
+      tmem_st_wait();
+    };
+    auto drain_to = [&](int k) -> bool {  // drains 1 .. k
+      while (ndrained < k) {
+        if (!warp_wait3(opart, ndrained & 1, abort_word, a.status)) return false;
+        tc_fence_after();
+        drain_once();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(odone);
+        ++ndrained;
+      }
+      return true;
+    };
     for (int t = pair; ok && t < ntiles; t += 2) {
       const int b = t % K3_NSB;
+      if (a.drain && !drain_to(t / a.drain)) { ok = false; break; }
       const uint32_t bph = (t / K3_NSB) & 1;
       if (!warp_wait3(&sfull[b], bph, abort_word, a.status)) { ok = false; break; }
       tc_fence_after();
@@ -330,15 +424,25 @@ __global__ void __launch_bounds__(K3_THREADS, 1)
         for (int jj = 0; jj < 32; ++jj)
           if (jbase + jj >= a.nk) kv[jj] = 0.0f;
       }
-      // K = hi + lo in BF16, packed two per 32-bit TMEM column
+      // K = hi + lo in BF16 (or FP16), packed two per 32-bit TMEM column
       uint32_t ph16[16], pl16[16];
+      if (a.f16) {
 #pragma unroll
-      for (int e = 0; e < 16; ++e) {
-        const __nv_bfloat162 h = __floats2bfloat162_rn(kv[2 * e], kv[2 * e + 1]);
-        const __nv_bfloat162 l =
-            __floats2bfloat162_rn(kv[2 * e] - __low2float(h), kv[2 * e + 1] - __high2float(h));
-        ph16[e] = *reinterpret_cast<const uint32_t*>(&h);
-        pl16[e] = *reinterpret_cast<const uint32_t*>(&l);
+        for (int e = 0; e < 16; ++e) {
+          const __half2 h = __floats2half2_rn(kv[2 * e], kv[2 * e + 1]);
+          const __half2 l = __floats2half2_rn(kv[2 * e] - __low2float(h), kv[2 * e + 1] - __high2float(h));
+          ph16[e] = *reinterpret_cast<const uint32_t*>(&h);
+          pl16[e] = *reinterpret_cast<const uint32_t*>(&l);
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const __nv_bfloat162 h = __floats2bfloat162_rn(kv[2 * e], kv[2 * e + 1]);
+          const __nv_bfloat162 l =
+              __floats2bfloat162_rn(kv[2 * e] - __low2float(h), kv[2 * e + 1] - __high2float(h));
+          ph16[e] = *reinterpret_cast<const uint32_t*>(&h);
+          pl16[e] = *reinterpret_cast<const uint32_t*>(&l);
+        }
       }
       tmem_st16(lane_addr + col, ph16);
       tmem_st16(lane_addr + col + 16, pl16);
@@ -346,21 +450,11 @@ __global__ void __launch_bounds__(K3_THREADS, 1)
       tc_fence_before();
       mbar_arrive(&pfull[b]);
     }
-    // write out O (pair 0): each warpgroup half of the MC columns, 32 at a time
-    if (pair == 0 && ok && warp_wait3(ofull, 0, abort_word, a.status)) {
+    // the drains this warp has not reached, then the last partial
+    if (ok && a.drain) ok = drain_to((ntiles - 1) / a.drain);
+    if (ok && warp_wait3(ofull, 0, abort_word, a.status)) {
       tc_fence_after();
-      const int half = a.mc / 2;
-      for (int c0 = wg * half; c0 < (wg + 1) * half; c0 += 32) {
-        uint32_t r[32];
-        tmem_ld32(lane_addr + OCOL + c0, r);
-        tmem_ld_wait(r);
-        if (gi < a.nq && !*abort_word) {
-          float* orow = a.O + (int64_t)gi * a.ldo + m0 + c0;
-#pragma unroll
-          for (int c = 0; c < 32; ++c)
-            if (m0 + c0 + c < a.m) orow[c] = __uint_as_float(r[c]);
-        }
-      }
+      flush();
     }
   }
   tc_fence_before();
@@ -376,8 +470,10 @@ __global__ void __launch_bounds__(K3_THREADS, 1)
 // column c is the 128-byte row jt * m_pad + c, so that the box one CTA loads
 // for a tile (mc columns) is one contiguous run of memory.  (Rows of a plain
 // V^T lie nk_pad * 2 bytes apart, and boxes of such strided rows load slowly.)
+// F16: the FP16 pair of V[j][c] * scale[c] (scale an exact power of two).
+template <bool F16>
 __global__ void vsplit_kernel(const float* __restrict__ V, int nk, int m, int ldv, int nk_pad, int m_pad,
-                              __nv_bfloat16* __restrict__ vh, __nv_bfloat16* __restrict__ vl) {
+                              const float* __restrict__ scale, uint16_t* __restrict__ vh, uint16_t* __restrict__ vl) {
   __shared__ float tile[32][33];
   const int j0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
@@ -388,13 +484,56 @@ __global__ void vsplit_kernel(const float* __restrict__ V, int nk, int m, int ld
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int c = c0 + r, j = j0 + threadIdx.x;
     if (c < m_pad && j < nk_pad) {
-      const float v = tile[threadIdx.x][r];
-      const __nv_bfloat16 h = __float2bfloat16_rn(v);
       const int64_t o = ((int64_t)(j / K3_BN) * m_pad + c) * K3_BN + (j % K3_BN);
-      vh[o] = h;
-      vl[o] = __float2bfloat16_rn(v - __bfloat162float(h));
+      if constexpr (F16) {
+        const float v = tile[threadIdx.x][r] * (c < m ? scale[c] : 1.0f);
+        const __half h = __float2half_rn(v);
+        const __half l = __float2half_rn(v - __half2float(h));
+        vh[o] = __half_as_ushort(h);
+        vl[o] = __half_as_ushort(l);
+      } else {
+        const float v = tile[threadIdx.x][r];
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+        vh[o] = __bfloat16_as_ushort(h);
+        vl[o] = __bfloat16_as_ushort(l);
+      }
     }
   }
+}
+
+// Largest |V[j][c]| of each column (as the bits of a non-negative float,
+// which order like integers), over a grid of row blocks.
+__global__ void colmax_kernel(const float* __restrict__ V, int nk, int m, int ldv, int* __restrict__ cmax) {
+  __shared__ float red[8][33];
+  const int c = blockIdx.x * 32 + threadIdx.x;
+  float mx = 0.0f;
+  if (c < m)
+    for (int j = blockIdx.y * 8 + threadIdx.y; j < nk; j += gridDim.y * 8) mx = fmaxf(mx, fabsf(V[(int64_t)j * ldv + c]));
+  red[threadIdx.y][threadIdx.x] = mx;
+  __syncthreads();
+  if (threadIdx.y == 0 && c < m) {
+    for (int y = 1; y < 8; ++y) mx = fmaxf(mx, red[y][threadIdx.x]);
+    atomicMax(cmax + c, __float_as_int(mx));
+  }
+}
+
+// scale[c] = 2^s with max|V[:, c]| * 2^s <= 2^14 (FP16 holds it with room for
+// the hi + lo pair); inv_scale[c] = 2^-s; 1 for an all-zero column.
+__global__ void colscale_kernel(const int* __restrict__ cmax, int m, float* __restrict__ scale,
+                                float* __restrict__ inv_scale) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= m) return;
+  const float mx = __int_as_float(cmax[c]);
+  int sh = 0;
+  if (mx > 0.0f && isfinite(mx)) {
+    int k;
+    frexpf(mx, &k);  // mx < 2^k
+    sh = 14 - k;
+    sh = sh > 100 ? 100 : (sh < -100 ? -100 : sh);
+  }
+  scale[c] = ldexpf(1.0f, sh);
+  inv_scale[c] = ldexpf(1.0f, -sh);
 }
 
 size_t mma_smem_bytes(int dp, int mc, int nx, int nv, int vsplits) {
@@ -404,9 +543,9 @@ size_t mma_smem_bytes(int dp, int mc, int nx, int nv, int vsplits) {
 // Column chunk per CTA: a multiple of 64 (each epilogue warpgroup writes out
 // half of it, 32 columns at a time), at most 256 (MMA N limit), the widest
 // whose pipeline fits in shared memory, then narrowed to balance the chunks.
-int mma_chunk(int dp, int m, int vsplits) {
+int mma_chunk(int dp, int m, int vsplits, int mc_max) {
   const int mpad = ((m + 63) / 64) * 64;
-  int mc = mpad < 256 ? mpad : 256;
+  int mc = mpad < mc_max ? mpad : mc_max;
   while (mc > 64 && mma_smem_bytes(dp, mc, 2, 2, vsplits) > smem_limit_bytes()) mc -= 64;
   if (mma_smem_bytes(dp, mc, 2, 2, vsplits) > smem_limit_bytes()) return 0;
   const int nch = (mpad + mc - 1) / mc;
@@ -432,9 +571,12 @@ static int launch_mma_t(const PointSet& Q, const PointSet& Ks, const CUtensorMap
 }
 
 int fused_matvec_mma(const PointSet& Q, const PointSet& Ks, bool self, int kf, const KConst& kc, const float* V,
-                     int m, int ldv, float* O, int ldo, int* status, cudaStream_t st, bool v_bf16_exact) {
-  const int vsplits = v_bf16_exact ? 1 : 2;
-  const int mc = mma_chunk(Q.dp, m, vsplits);
+                     int m, int ldv, float* O, int ldo, int* status, cudaStream_t st, bool sketch) {
+  const int vsplits = 2;
+  // kernel values lie in [0, 1]: the contraction carries them (and V, scaled
+  // per column) as FP16 pairs, 22 significant bits instead of BF16's 16
+  const bool f16 = kf == KF_RBF || kf == KF_LAPLACE || kf == KF_MATERN;
+  const int mc = mma_chunk(Q.dp, m, vsplits, sketch ? 256 : 128);
   if (mc == 0) return fail(KOP_EINVAL, "fused_matvec_mma: feature width too large");
   {
     int sc = ensure_scaled_norms(const_cast<PointSet&>(Q), kc.scale, st);
@@ -444,14 +586,37 @@ int fused_matvec_mma(const PointSet& Q, const PointSet& Ks, bool self, int kf, c
   const int nch = (m + mc - 1) / mc;
   const int m_pad = nch * mc;
   const int64_t nk_pad = Ks.n_pad;
-  __nv_bfloat16* vsplit = nullptr;
-  KOP_CUDA_TRY(cudaMallocAsync((void**)&vsplit, (size_t)2 * m_pad * nk_pad * 2, st));
-  __nv_bfloat16* vh = vsplit;
-  __nv_bfloat16* vl = vsplit + (size_t)m_pad * nk_pad;
+  uint16_t* vsplit = nullptr;
+  // V^T pairs, then (FP16) the column maxima and the two scale arrays
+  const size_t vbytes = (size_t)2 * m_pad * nk_pad * 2;
+  KOP_CUDA_TRY(cudaMallocAsync((void**)&vsplit, vbytes + (size_t)3 * 4 * m_pad, st));
+  uint16_t* vh = vsplit;
+  uint16_t* vl = vsplit + (size_t)m_pad * nk_pad;
+  int* cmax = (int*)((uint8_t*)vsplit + vbytes);
+  float* vscale = (float*)(cmax + m_pad);
+  float* vinv = vscale + m_pad;
   dim3 vb(32, 8), vg((unsigned)(nk_pad / 32), (unsigned)((m_pad + 31) / 32));
-  vsplit_kernel<<<vg, vb, 0, st>>>(V, (int)Ks.n, m, ldv, (int)nk_pad, m_pad, vh, vl);
+  int rc = KOP_OK;
+  if (f16) {
+    cudaError_t e0 = cudaMemsetAsync(cmax, 0, sizeof(int) * m_pad, st);
+    if (e0 != cudaSuccess) rc = cuda_fail(e0, "cudaMemsetAsync");
+    if (rc == KOP_OK) {
+      int gy = (int)((Ks.n + 8 * 64 - 1) / (8 * 64));
+      if (gy > 4 * num_sms()) gy = 4 * num_sms();
+      if (gy < 1) gy = 1;
+      colmax_kernel<<<dim3((unsigned)((m + 31) / 32), (unsigned)gy), dim3(32, 8), 0, st>>>(V, (int)Ks.n, m, ldv, cmax);
+      note_launch();
+      colscale_kernel<<<(unsigned)((m_pad + 127) / 128), 128, 0, st>>>(cmax, m, vscale, vinv);
+      note_launch();
+      vsplit_kernel<true><<<vg, vb, 0, st>>>(V, (int)Ks.n, m, ldv, (int)nk_pad, m_pad, vscale, vh, vl);
+      note_launch();
+    }
+  } else {
+    vsplit_kernel<false><<<vg, vb, 0, st>>>(V, (int)Ks.n, m, ldv, (int)nk_pad, m_pad, nullptr, vh, vl);
+    note_launch();
+  }
   cudaError_t e = cudaGetLastError();
-  int rc = e == cudaSuccess ? KOP_OK : cuda_fail(e, "vsplit_kernel");
+  if (rc == KOP_OK && e != cudaSuccess) rc = cuda_fail(e, "vsplit_kernel");
   CUtensorMap tv[2];
   const int64_t vrows = (nk_pad / K3_BN) * m_pad;  // blocked V^T: 64 values per row
   if (rc == KOP_OK) rc = encode_tmap_bf16(&tv[0], vh, vrows, K3_BN, K3_BN, mc);
@@ -482,6 +647,9 @@ int fused_matvec_mma(const PointSet& Q, const PointSet& Ks, bool self, int kf, c
     a.m2c = -2.0f * kc.scale;
     a.c2 = kc.c2;
     a.status = status;
+    a.f16 = f16 ? 1 : 0;
+    a.inv_scale = vinv;
+    a.drain = sketch ? 0 : K3_DRAIN;
     switch (kf) {
       case KF_RBF: rc = launch_mma_t<KF_RBF>(Q, Ks, tv, a, st); break;
       case KF_LAPLACE: rc = launch_mma_t<KF_LAPLACE>(Q, Ks, tv, a, st); break;

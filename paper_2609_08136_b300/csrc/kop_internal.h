@@ -63,15 +63,16 @@ int column_mean(const float* X, int64_t n, int d, double* mean, cudaStream_t st)
 // points, so the diagonal distance is set to exactly 0.
 int fused_matvec(const PointSet& Q, const PointSet& Ks, bool self, int kf, const KConst& kc, int nsplit,
                  const float* V, int m, int ldv, float* O, int ldo, int* status, cudaStream_t st,
-                 bool v_bf16_exact = false);
+                 bool sketch = false);
 // Single-vector product of a point set with itself using the symmetry of K
 // (2-term split): v holds n floats (n_pad when v_padded), 16-byte aligned.
 int fused_matvec_sym(PointSet& P, int kf, const KConst& kc, const float* v, int v_padded, float* O, int* status,
                      cudaStream_t st);
 // Tensor-core contraction variant for m > 8 (2-term split only).
-// v_bf16_exact: V holds BF16-representable values, so its lo split is zero.
+// sketch: the Nystrom sketch, which tolerates a contraction that drifts by
+// ~1e-5 relative (wider column chunks); other products keep it near FP32.
 int fused_matvec_mma(const PointSet& Q, const PointSet& Ks, bool self, int kf, const KConst& kc, const float* V,
-                     int m, int ldv, float* O, int ldo, int* status, cudaStream_t st, bool v_bf16_exact = false);
+                     int m, int ldv, float* O, int ldo, int* status, cudaStream_t st, bool sketch = false);
 // Plain FP32 CUDA-core operator (same contract, no tensor cores); with
 // `compensated` the contraction is error-free per entry (acceptance checks).
 int plain_matvec(const PointSet& Q, const PointSet& Ks, bool self, int kf, const KConst& kc, const float* V,
@@ -91,7 +92,7 @@ int cert_matvec(const PointSet& Q, const PointSet& Ks, int kf, double bw, const 
 // Any mode.
 int op_matvec(const PointSet& Q, const PointSet& Ks, bool self, int kf, const KConst& kc, int mode,
               const float* V, int m, int ldv, float* O, int ldo, int* status, cudaStream_t st,
-              bool v_bf16_exact = false);
+              bool sketch = false);
 
 int num_sms();
 inline size_t smem_limit_bytes() { return 227u * 1024u; }
@@ -149,7 +150,7 @@ inline int64_t op_dim(const kop_s* op) { return op->ridge ? op->rp : op->pts.n; 
 inline int64_t op_dim_pad(const kop_s* op) { return op->ridge ? ((int64_t)op->rp + 127) / 128 * 128 : op->pts.n_pad; }
 // O = A V with the operator's product in `mode` (kernel K(X, X) or X^T X).
 int op_apply(kop_s* op, int mode, const float* V, int m, int ldv, float* O, int ldo, cudaStream_t st,
-             bool v_bf16_exact = false);
+             bool sketch = false);
 // FP64 product with the operator (KOP_EXACT arithmetic).
 int op_apply_f64(kop_s* op, const double* V, int m, int ldv, double* O, int ldo, cudaStream_t st);
 int ridge_apply(const kop_s* op, int mode, const float* V, int m, int ldv, float* O, int ldo, cudaStream_t st);

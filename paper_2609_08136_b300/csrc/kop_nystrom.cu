@@ -162,7 +162,7 @@ extern "C" int nys_build(kop_t op, const float* Omega, int32_t r, double nu_rel,
 
   int rc;
   // 1. sketch Y = K Omega (fused operator, m = r)
-  rc = op_apply(op, mode, Omega, r, r, Y, r, st);
+  rc = op_apply(op, mode, Omega, r, r, Y, r, st, /*sketch=*/true);
   if (rc) return rc;
   // 2. Gram blocks: Omega^T Omega and Omega^T Y on the tensor cores from BF16
   // splits of the two matrices (two scratch buffers, reused below)

@@ -146,3 +146,25 @@ def test_matvec_parity_wide_blocks_and_many_waves(n, d, m, mode, kind):
     op.sync()
     rows = np.unique(np.concatenate([np.arange(0, n, max(1, n // 200)), [n - 1]]))
     assert _sampled_rel_err(kind, X, V, bw, got, rows) < TOL[mode]
+
+
+@pytest.mark.parametrize("n,d,kind", [(20000, 64, ops.RBF), (30001, 128, ops.LAPLACE)])
+def test_block_product_has_no_drift(n, d, kind):
+    """The tensor core truncates when it adds into its FP32 accumulator, so
+    one accumulator over the whole sweep of n keys drifts towards zero
+    (measured -1.2e-4 relative at n = 2e4, -6e-4 at n = 1e5: enough to make
+    K + lam I indefinite for small lam).  The block product (m > 8) restarts
+    its accumulator every few tiles; its error against the FP64 operator must
+    stay near FP32 rounding: a bias v^T (O - O64) / v^T O64 below 1e-5 and a
+    relative error below 1e-5, whatever n."""
+    rng = np.random.default_rng(n)
+    X = torch.from_numpy(rng.standard_normal((n, d)).astype(np.float32)).cuda()
+    op = ops.KernelOperator(X, kind, float(np.sqrt(d)))
+    V = torch.from_numpy(rng.standard_normal((n, 16)).astype(np.float32)).cuda()
+    O64 = op.matvec_f64(V.double())
+    Of = op.matvec(V, mode=ops.FAST).double()
+    Vd = V.double()
+    bias = ((Vd * (Of - O64)).sum(0) / (Vd * O64).sum(0)).cpu().numpy()
+    rel = ((Of - O64).norm() / O64.norm()).item()
+    assert np.all(np.abs(bias) < 1e-5), bias
+    assert rel < 1e-5, rel
