@@ -273,18 +273,22 @@ static int launch_cert_t(const PointSet& Q, const PointSet& Ks, const double* V,
   return KOP_OK;
 }
 
+// Column groups of up to 32: the error-free distance (most of the FP32 work)
+// is formed once per group.
 template <int KF>
 static int launch_cert_kf(const PointSet& Q, const PointSet& Ks, const double* V, int m, int ldv, double* O, int ldo,
                           double bw, cudaStream_t st) {
-  for (int c0 = 0; c0 < m; c0 += 8) {
-    const int mc = (m - c0) < 8 ? (m - c0) : 8;
+  for (int c0 = 0; c0 < m; c0 += 32) {
+    const int mc = (m - c0) < 32 ? (m - c0) : 32;
     int rc;
     if (mc == 1)
       rc = launch_cert_t<KF, 1>(Q, Ks, V + c0, mc, ldv, O + c0, ldo, bw, st);
     else if (mc <= 2)
       rc = launch_cert_t<KF, 2>(Q, Ks, V + c0, mc, ldv, O + c0, ldo, bw, st);
-    else
+    else if (mc <= 8)
       rc = launch_cert_t<KF, 8>(Q, Ks, V + c0, mc, ldv, O + c0, ldo, bw, st);
+    else
+      rc = launch_cert_t<KF, 32>(Q, Ks, V + c0, mc, ldv, O + c0, ldo, bw, st);
     if (rc) return rc;
   }
   return KOP_OK;
