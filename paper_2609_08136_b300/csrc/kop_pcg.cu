@@ -363,6 +363,34 @@ struct Workspace {
   }
 };
 
+// A column becomes a stop candidate on the device as soon as its recursive
+// residual meets the host's threshold thr2 = (tol^2 - excess) ||b||^2: it is
+// made inactive (alpha = 0 from then on, so x and r keep that iteration's
+// values) and the iteration is recorded for the host, which certifies the
+// candidates at its next synchronization.
+__global__ void freeze_kernel(int cols, const double* __restrict__ rr, const double* __restrict__ thr2,
+                              int* __restrict__ active, int* __restrict__ frozen, int it) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  if (active[c] && rr[c] <= thr2[c]) {
+    active[c] = 0;
+    frozen[c] = it;
+  }
+}
+
+// Iterations between host synchronizations: a small system's iteration takes
+// less device time than a host round trip, so its iterations run in chunks
+// whose residual norms are read back together (a candidate stop is frozen on
+// the device at its own iteration, so the chunk costs at most a few idle
+// iterations).  Large systems synchronize every iteration.
+static int chunk_len(int64_t n, int cols) {
+  const double work = (double)n * (double)n * (double)cols;
+  if (work <= 268435456.0) return 8;    // e.g. n <= 16384 for one column
+  if (work <= 1073741824.0) return 4;   // n <= 32768
+  return 1;
+}
+constexpr int kChunkMax = 8;
+
 static int device_status(kop_s* op, cudaStream_t st, int* h) {
   KOP_CUDA_TRY(cudaMemcpyAsync(h, op->status, sizeof(int), cudaMemcpyDeviceToHost, st));
   KOP_CUDA_TRY(cudaStreamSynchronize(st));
@@ -392,7 +420,8 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
   const int64_t s_rows = (op->ridge || n <= kCertAll) ? n : kCertRows;
   const int dpt = op->ridge ? 0 : op->pts.d;
   const size_t cbytes = sizeof(double) * ((size_t)s_rows * cols + 3 * (size_t)cols) +
-                        sizeof(float) * (size_t)s_rows * dpt + 64;
+                        sizeof(float) * (size_t)s_rows * dpt + 64 +
+                        sizeof(double) * (size_t)(kChunkMax + 1) * cols + sizeof(int) * (size_t)cols + 64;
   KOP_CUDA_TRY(cudaMallocAsync(&ws.p, xbytes + dbytes + fbytes + ibytes + 256, st));
   Workspace wc;
   wc.st = st;
@@ -402,6 +431,11 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
   double* csd2 = csd + cols;
   double* csd3 = csd2 + cols;
   float* samp_x = (float*)(csd3 + cols);
+  // the chunk's squared residual norms, the candidate thresholds, the
+  // iteration at which each column froze (0: none)
+  double* hist = (double*)(((uintptr_t)(samp_x + (size_t)s_rows * dpt) + 63) & ~(uintptr_t)63);
+  double* thr2 = hist + (size_t)kChunkMax * cols;
+  int* frozen = (int*)(thr2 + cols);
   PointSet qs;
   if (!op->ridge) {
     qs.n = s_rows;
@@ -615,15 +649,39 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
   int it = 0;
   bool breakdown = false;
   std::vector<char> cand(cols);
+  // candidate thresholds on ||r||^2 for the device: tol^2 - excess, times ||b||^2
+  std::vector<double> hthr(cols);
+  auto upload_thresholds = [&]() -> int {
+    for (int c = 0; c < cols; ++c) hthr[c] = (tol2 - excess[c]) * nb[c] * nb[c];
+    KOP_CUDA_TRY(cudaMemcpyAsync(thr2, hthr.data(), sizeof(double) * cols, cudaMemcpyHostToDevice, st));
+    return KOP_OK;
+  };
+  if ((rc = upload_thresholds())) return rc;
+  KOP_CUDA_TRY(cudaMemsetAsync(frozen, 0, sizeof(int) * cols, st));
+  const int chunk = chunk_len(n, cols);
+  std::vector<double> hh((size_t)kChunkMax * cols);
+  std::vector<int> hf(cols), stop_it(cols, 0);
+  int slot = 0;
   for (it = 1; any && it <= pb.maxit; ++it) {
     if ((rc = matvec(P, Q, pb.inner_mode))) return rc;
     va.acc = pq;
     if ((rc = vec_launch<OP_PQ>(va, st))) return rc;
     fin_alpha_kernel<<<(cols + 127) / 128, 128, 0, st>>>(cols, rz, pq, active, alpha, op->status);
     KOP_LAUNCHED();
-    va.acc = acc;
+    va.acc = hist + (size_t)slot * cols;
     if ((rc = vec_launch<OP_XR>(va, st))) return rc;
-    KOP_CUDA_TRY(cudaMemcpyAsync(hr.data(), acc, sizeof(double) * cols, cudaMemcpyDeviceToHost, st));
+    va.acc = acc;
+    freeze_kernel<<<(cols + 127) / 128, 128, 0, st>>>(cols, hist + (size_t)slot * cols, thr2, active, frozen, it);
+    KOP_LAUNCHED();
+    // the host looks at the chunk at its last iteration and wherever a
+    // refinement or the last iteration falls
+    const bool sync = slot == chunk - 1 || it == pb.maxit || (pb.refine_every > 0 && it % pb.refine_every == 0);
+    if (!sync) {
+      ++slot;
+    } else {
+    KOP_CUDA_TRY(cudaMemcpyAsync(hh.data(), hist, sizeof(double) * (size_t)(slot + 1) * cols,
+                                 cudaMemcpyDeviceToHost, st));
+    KOP_CUDA_TRY(cudaMemcpyAsync(hf.data(), frozen, sizeof(int) * cols, cudaMemcpyDeviceToHost, st));
     int hs = 0;
     if ((rc = device_status(op, st, &hs))) return rc;
     if (hs == KOP_DEV_BREAKDOWN) {
@@ -631,20 +689,28 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
       break;
     }
     if (hs == KOP_DEV_TIMEOUT) return fail(KOP_ETIMEOUT, "pcg: a bounded device wait timed out");
+    const int it0 = it - slot;  // first iteration of the chunk
     bool any_cand = false, all_near = true;
     for (int c = 0; c < cols; ++c) {
       cand[c] = 0;
       if (!act[c]) continue;
-      rel[c] = std::sqrt(hr[c]) / nb[c];
-      if (pb.res_hist) pb.res_hist[(size_t)it * cols + c] = rel[c];
+      // a column frozen at iteration f kept its residual from then on
+      const int last = hf[c] > 0 ? hf[c] : it;
+      if (pb.res_hist)
+        for (int j = it0; j <= last; ++j)
+          pb.res_hist[(size_t)j * cols + c] = std::sqrt(hh[(size_t)(j - it0) * cols + c]) / nb[c];
+      rel[c] = std::sqrt(hh[(size_t)(last - it0) * cols + c]) / nb[c];
       // a candidate stop once the recursive residual leaves room for what
-      // the last certification found the check operator to miss
-      if (rel[c] * rel[c] <= tol2 - excess[c]) {
+      // the last certification found the check operator to miss (the
+      // device froze the column at that iteration)
+      if (hf[c] > 0) {
         cand[c] = 1;
         any_cand = true;
+        stop_it[c] = hf[c];
       }
       all_near = all_near && rel[c] <= kNearTol * pb.tol;
     }
+    slot = 0;
     // a periodic refinement is skipped when every active column is within
     // kNearTol of the tolerance: its candidate stop, a few iterations later,
     // recomputes the true residual anyway
@@ -666,7 +732,7 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
         if (stopping && pb.true_relres) pb.true_relres[c] = trel[c];
         if (cand[c] && urel[c] <= pb.tol) {
           act[c] = 0;
-          if (pb.iters) pb.iters[c] = it;
+          if (pb.iters) pb.iters[c] = stop_it[c];
         } else if ((stopping || predict) && excess[c] > kEscalate * tol2) {
           // any active column, candidate or not: its threshold tol^2 - excess
           // would otherwise leave it no room to become a candidate again
@@ -680,9 +746,13 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
         pb.check_mode = pb.refine_mode = KOP_EXACT;
         for (int c = 0; c < cols; ++c) excess[c] = 0.0;
       }
+      // columns whose candidate stop was not certified continue from it
       KOP_CUDA_TRY(cudaMemcpyAsync(active, act.data(), sizeof(int) * cols, cudaMemcpyHostToDevice, st));
+      KOP_CUDA_TRY(cudaMemsetAsync(frozen, 0, sizeof(int) * cols, st));
+      if ((rc = upload_thresholds())) return rc;
       if (!any) break;
     }
+    }  // sync
     if ((rc = apply_prec())) return rc;
     va.acc = acc;
     va.acc2 = qz;
