@@ -94,6 +94,20 @@ int64_t kop_launch_count(void);
  * measurement helper. */
 int kop_sfu_rates(double* rates, void* stream);
 
+/* Tile autotuner of the block operator product (m > 8 columns): the column
+ * chunk and the ring depths of the fused tensor-core kernel.  When on (the
+ * default), the first product of a shape (kernel, log2 n, feature width,
+ * columns rounded up to 64, sketch or solver form) runs every candidate that
+ * fits in shared memory once, timed with CUDA events on the caller's stream
+ * (which this synchronizes), keeps the fastest for that shape, and returns
+ * the product computed with it; later products of the shape reuse it.
+ * Candidates differ only in rounding.  Off: a fixed heuristic (widest chunk,
+ * deepest rings).  A stream being captured is never tuned.  kop_set_autotune
+ * clears the tuned shapes; kop_autotune_shapes returns how many are cached.
+ * Not in the paper: a performance control. */
+int kop_set_autotune(int32_t enable);
+int32_t kop_autotune_shapes(void);
+
 /* ---------------------------------------------------------------------------
  * Kernel operator (the matrix-free linear operator of Sec. 4.3; K of
  * Sec. 2.1 Eq. "rlaopt-krr").

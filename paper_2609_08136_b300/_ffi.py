@@ -19,6 +19,8 @@ SIGNATURES = {
     "kop_last_error": (ctypes.c_char_p, []),
     "kop_launch_count": (c_i64, []),
     "kop_sfu_rates": (c_int, [P(c_dbl), c_vp]),
+    "kop_set_autotune": (c_int, [c_i32]),
+    "kop_autotune_shapes": (c_i32, []),
     "kop_create": (c_int, [c_vp, c_i64, c_i32, c_i32, c_dbl, c_vp, P(c_vp)]),
     "kop_destroy": (c_int, [c_vp]),
     "kop_set_bandwidth": (c_int, [c_vp, c_dbl]),

@@ -67,3 +67,10 @@ extern "C" int kop_sfu_rates(double* rates, void* stream) {
   cudaFreeAsync(out, st);
   return rc;
 }
+
+extern "C" int kop_set_autotune(int32_t enable) {
+  kop::set_mma_autotune(enable);
+  return KOP_OK;
+}
+
+extern "C" int32_t kop_autotune_shapes(void) { return kop::mma_tuned_shapes(); }

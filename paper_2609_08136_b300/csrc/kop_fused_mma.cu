@@ -21,6 +21,12 @@
 // epilogue) and V tiles (released by the contraction).
 #include <cuda_fp16.h>
 
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
 #include "kop_device.cuh"
 #include "kop_epilogue.cuh"
 #include "kop_internal.h"
@@ -570,19 +576,13 @@ static int launch_mma_t(const PointSet& Q, const PointSet& Ks, const CUtensorMap
   return KOP_OK;
 }
 
-int fused_matvec_mma(const PointSet& Q, const PointSet& Ks, bool self, int kf, const KConst& kc, const float* V,
-                     int m, int ldv, float* O, int ldo, int* status, cudaStream_t st, bool sketch) {
+// One block product with a given column chunk mc and X / V ring depths.
+static int run_mma(const PointSet& Q, const PointSet& Ks, bool self, int kf, const KConst& kc, const float* V, int m,
+                   int ldv, float* O, int ldo, int* status, cudaStream_t st, bool sketch, int mc, int nx, int nv) {
   const int vsplits = 2;
   // kernel values lie in [0, 1]: the contraction carries them (and V, scaled
   // per column) as FP16 pairs, 22 significant bits instead of BF16's 16
   const bool f16 = kf == KF_RBF || kf == KF_LAPLACE || kf == KF_MATERN;
-  const int mc = mma_chunk(Q.dp, m, vsplits, sketch ? 256 : 128);
-  if (mc == 0) return fail(KOP_EINVAL, "fused_matvec_mma: feature width too large");
-  {
-    int sc = ensure_scaled_norms(const_cast<PointSet&>(Q), kc.scale, st);
-    if (sc == KOP_OK && &Q != &Ks) sc = ensure_scaled_norms(const_cast<PointSet&>(Ks), kc.scale, st);
-    if (sc) return sc;
-  }
   const int nch = (m + mc - 1) / mc;
   const int m_pad = nch * mc;
   const int64_t nk_pad = Ks.n_pad;
@@ -638,12 +638,8 @@ int fused_matvec_mma(const PointSet& Q, const PointSet& Ks, bool self, int kf, c
     a.tcols = 512;
     a.vsplits = vsplits;
     a.m_pad = m_pad;
-    // deepest rings that fit, the X ring first (it sets the MMA lookahead)
-    const size_t lim = smem_limit_bytes();
-    a.nx = K3_MAXX;
-    while (a.nx > 2 && mma_smem_bytes(Q.dp, mc, a.nx, 2, vsplits) > lim) --a.nx;
-    a.nv = K3_MAXV;
-    while (a.nv > 2 && mma_smem_bytes(Q.dp, mc, a.nx, a.nv, vsplits) > lim) --a.nv;
+    a.nx = nx;
+    a.nv = nv;
     a.m2c = -2.0f * kc.scale;
     a.c2 = kc.c2;
     a.status = status;
@@ -664,6 +660,121 @@ int fused_matvec_mma(const PointSet& Q, const PointSet& Ks, bool self, int kf, c
   }
   cudaFreeAsync(vsplit, st);
   return rc;
+}
+
+// ------------------------------------------------------------------ autotuner
+// Tile shape of the block product: the column chunk mc (a multiple of 64; at
+// most 128 for the solver's products, whose running sum takes TMEM columns,
+// 256 for the sketch) and the X / V ring depths.  The first product of a
+// shape (kernel, log2 n, feature width, columns, form) times every candidate
+// that fits in shared memory once with CUDA events on the caller's stream and
+// keeps the fastest; later products of that shape reuse it.  The choice does
+// not change the result beyond rounding (all candidates compute the same
+// product); the heuristic (widest chunk, deepest rings) serves while the
+// tuner is off (kop_set_autotune) or the stream is being captured.
+struct MmaShape {
+  int kf, lgn, dp, mpad, sketch;
+  bool operator<(const MmaShape& o) const {
+    return std::tie(kf, lgn, dp, mpad, sketch) < std::tie(o.kf, o.lgn, o.dp, o.mpad, o.sketch);
+  }
+};
+struct MmaTile {
+  int mc, nx, nv;
+};
+static std::mutex g_tune_mu;
+static std::map<MmaShape, MmaTile> g_tune;
+static std::atomic<int> g_autotune{1};
+
+static MmaTile heuristic_tile(int dp, int m, bool sketch) {
+  const int vsplits = 2;
+  MmaTile t;
+  t.mc = mma_chunk(dp, m, vsplits, sketch ? 256 : 128);
+  const size_t lim = smem_limit_bytes();
+  // deepest rings that fit, the X ring first (it sets the MMA lookahead)
+  t.nx = K3_MAXX;
+  while (t.nx > 2 && mma_smem_bytes(dp, t.mc, t.nx, 2, vsplits) > lim) --t.nx;
+  t.nv = K3_MAXV;
+  while (t.nv > 2 && mma_smem_bytes(dp, t.mc, t.nx, t.nv, vsplits) > lim) --t.nv;
+  return t;
+}
+
+int fused_matvec_mma(const PointSet& Q, const PointSet& Ks, bool self, int kf, const KConst& kc, const float* V,
+                     int m, int ldv, float* O, int ldo, int* status, cudaStream_t st, bool sketch) {
+  const MmaTile h = heuristic_tile(Q.dp, m, sketch);
+  if (h.mc == 0) return fail(KOP_EINVAL, "fused_matvec_mma: feature width too large");
+  {
+    int sc = ensure_scaled_norms(const_cast<PointSet&>(Q), kc.scale, st);
+    if (sc == KOP_OK && &Q != &Ks) sc = ensure_scaled_norms(const_cast<PointSet&>(Ks), kc.scale, st);
+    if (sc) return sc;
+  }
+  int lgn = 0;
+  while ((int64_t(1) << (lgn + 1)) <= Ks.n) ++lgn;
+  const MmaShape key{kf, lgn, Q.dp, (m + 63) / 64 * 64, sketch ? 1 : 0};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end())
+      return run_mma(Q, Ks, self, kf, kc, V, m, ldv, O, ldo, status, st, sketch, it->second.mc, it->second.nx,
+                     it->second.nv);
+  }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  KOP_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
+  if (!g_autotune.load() || cap != cudaStreamCaptureStatusNone)
+    return run_mma(Q, Ks, self, kf, kc, V, m, ldv, O, ldo, status, st, sketch, h.mc, h.nx, h.nv);
+  // candidates: every chunk width up to the form's limit (no wider than the
+  // columns need) with X rings of depth 2 .. 4 and the deepest V ring that fits
+  std::vector<MmaTile> cand;
+  const int mpad = (m + 63) / 64 * 64;
+  const size_t lim = smem_limit_bytes();
+  for (int mc = 64; mc <= (sketch ? 256 : 128) && mc <= mpad; mc += 64)
+    for (int nx = 2; nx <= K3_MAXX; ++nx) {
+      if (mma_smem_bytes(Q.dp, mc, nx, 2, 2) > lim) continue;
+      int nv = K3_MAXV;
+      while (nv > 2 && mma_smem_bytes(Q.dp, mc, nx, nv, 2) > lim) --nv;
+      cand.push_back(MmaTile{mc, nx, nv});
+    }
+  if (cand.empty()) cand.push_back(h);
+  cudaEvent_t e0, e1;
+  KOP_CUDA_TRY(cudaEventCreate(&e0));
+  KOP_CUDA_TRY(cudaEventCreate(&e1));
+  MmaTile best = h;
+  float best_ms = 0.0f;
+  int rc = KOP_OK;
+  for (size_t i = 0; i < cand.size() && rc == KOP_OK; ++i) {
+    const MmaTile& c = cand[i];
+    cudaEventRecord(e0, st);
+    rc = run_mma(Q, Ks, self, kf, kc, V, m, ldv, O, ldo, status, st, sketch, c.mc, c.nx, c.nv);
+    cudaEventRecord(e1, st);
+    if (rc == KOP_OK && cudaEventSynchronize(e1) == cudaSuccess) {
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (i == 0 || ms < best_ms) {
+        best_ms = ms;
+        best = c;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = best;
+  }
+  // the output of the chosen shape (so that every product of this shape,
+  // the first included, comes from the same arithmetic)
+  return run_mma(Q, Ks, self, kf, kc, V, m, ldv, O, ldo, status, st, sketch, best.mc, best.nx, best.nv);
+}
+
+void set_mma_autotune(int enable) {
+  g_autotune.store(enable ? 1 : 0);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune.clear();
+}
+
+int mma_tuned_shapes() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return (int)g_tune.size();
 }
 
 }  // namespace kop

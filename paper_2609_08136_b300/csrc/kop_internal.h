@@ -73,6 +73,10 @@ int fused_matvec_sym(PointSet& P, int kf, const KConst& kc, const float* v, int 
 // ~1e-5 relative (wider column chunks); other products keep it near FP32.
 int fused_matvec_mma(const PointSet& Q, const PointSet& Ks, bool self, int kf, const KConst& kc, const float* V,
                      int m, int ldv, float* O, int ldo, int* status, cudaStream_t st, bool sketch = false);
+// Autotuner of the block product's tile shape (kop_fused_mma.cu): on / off
+// (clears the cache), and the number of shapes tuned so far.
+void set_mma_autotune(int enable);
+int mma_tuned_shapes();
 // Plain FP32 CUDA-core operator (same contract, no tensor cores); with
 // `compensated` the contraction is error-free per entry (acceptance checks).
 int plain_matvec(const PointSet& Q, const PointSet& Ks, bool self, int kf, const KConst& kc, const float* V,

@@ -41,6 +41,17 @@ def _kind(kernel) -> int:
     return KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
 
 
+def set_autotune(enable: bool = True):
+    """Turn the block product's tile autotuner on or off (kop_set_autotune;
+    clears the tuned shapes)."""
+    check(_ffi.lib().kop_set_autotune(int(bool(enable))), "kop_set_autotune")
+
+
+def autotune_shapes() -> int:
+    """Number of block-product shapes tuned so far."""
+    return int(_ffi.lib().kop_autotune_shapes())
+
+
 def sfu_rates(stream=None):
     """Measured SFU throughput (ops/s): {'ex2': ..., 'sqrt': ..., 'rsqrt': ...}."""
     arr = (ctypes.c_double * 3)()

@@ -168,3 +168,25 @@ def test_block_product_has_no_drift(n, d, kind):
     rel = ((Of - O64).norm() / O64.norm()).item()
     assert np.all(np.abs(bias) < 1e-5), bias
     assert rel < 1e-5, rel
+
+
+def test_block_product_autotuner():
+    """The tile autotuner of the block product (kop_set_autotune) tunes a shape
+    once, caches it, and returns the same product as the fixed heuristic up
+    to rounding (the candidates differ only in how the work is tiled)."""
+    rng = np.random.default_rng(7)
+    n, d, m = 6000, 32, 200
+    X = torch.from_numpy(rng.standard_normal((n, d)).astype(np.float32)).cuda()
+    V = torch.from_numpy(rng.standard_normal((n, m)).astype(np.float32)).cuda()
+    op = ops.KernelOperator(X, ops.RBF, float(np.sqrt(d)))
+    ops.set_autotune(False)
+    ref = op.matvec(V, mode=ops.FAST)
+    assert ops.autotune_shapes() == 0
+    ops.set_autotune(True)
+    got = op.matvec(V, mode=ops.FAST)
+    assert ops.autotune_shapes() == 1
+    again = op.matvec(V, mode=ops.FAST)
+    assert ops.autotune_shapes() == 1
+    assert torch.equal(got, again)  # the cached shape: the same arithmetic
+    scale = (torch.exp(-torch.cdist(X, X) ** 2 / (2 * d)).abs() @ V.abs()).max().item()
+    assert (got - ref).abs().max().item() <= 1e-5 * scale
