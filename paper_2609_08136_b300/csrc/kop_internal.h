@@ -185,6 +185,11 @@ int check_cache_reserve(kop_s* op);
 // the same two columns.  build = true first computes the stored matrix by
 // direct differences.
 int check_matvec_cached(kop_s* op, bool build, const float* V2, int cols, float* T, cudaStream_t st);
+// The same product without the stored matrix: each pair of row blocks is
+// computed once by direct differences (the build's arithmetic) in shared
+// memory and used for both of its contributions.  *done = false (and nothing
+// launched) when its column-part scratch does not fit in device memory.
+int check_matvec_computed(kop_s* op, const float* V2, int cols, float* T, cudaStream_t st, bool* done);
 }  // namespace kop
 
 // Stream-ordered device scratch, freed on the same stream when it goes out of scope.

@@ -514,7 +514,15 @@ int pcg_core(PcgProblem& pb, cudaStream_t st) {
   // never reused across solves)
   bool kc_built = false;
   auto check2 = [&](int mode) -> int {
-    if (mode != KOP_PLAIN_CHECK || op->ridge || !op->kc) return matvec2(V2, T, mode);
+    if (mode != KOP_PLAIN_CHECK || op->ridge) return matvec2(V2, T, mode);
+    if (!op->kc) {
+      // no stored matrix: the symmetric product computes each pair of row
+      // blocks once, else (its scratch does not fit) every entry is evaluated
+      bool done = false;
+      const int rc2 = check_matvec_computed(op, V2, cols, T, st, &done);
+      if (rc2 || done) return rc2;
+      return matvec2(V2, T, mode);
+    }
     const int rc2 = check_matvec_cached(op, !kc_built, V2, cols, T, st);
     if (rc2 == KOP_OK) kc_built = true;
     return rc2;

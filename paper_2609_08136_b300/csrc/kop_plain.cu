@@ -337,16 +337,27 @@ KOP_DEV void ef_acc_pair(float& s, float& e, float k, float hi, float lo) {
   e = fmaf(k, lo, e + (err + pe));
 }
 
-template <int NC>
+// COMPUTE: no stored matrix.  The CTA computes each band tile K[I][J] into
+// shared memory by direct differences, with the arithmetic of the build (so
+// both forms give the same values), from the centred points Xc (n_pad x dp):
+// thread (r, q) forms row r against keys q * 32 .. + 31.  One buffer, no
+// prefetch (the distances dominate).  Shared memory: tile, then the two
+// vector tiles and the reduction area, then (COMPUTE) X_I transposed
+// (dp x 129) and X_J (128 x dp).
+template <int NC, int KF = KF_RBF, bool COMPUTE = false>
 __global__ void __launch_bounds__(KS2_THREADS, 1)
     kcache_symv_kernel(const float* __restrict__ Kc, int n, int nb, int h, const float* __restrict__ V2, int cols,
-                       int c0, float* __restrict__ T, float* __restrict__ C) {
+                       int c0, float* __restrict__ T, float* __restrict__ C, const float* __restrict__ Xc, int dp,
+                       PlainConst pc) {
   extern __shared__ __align__(16) float ksm[];
-  float* tile[2] = {ksm, ksm + 128 * KS2_LD};
-  float2* xj[2] = {reinterpret_cast<float2*>(ksm + 2 * 128 * KS2_LD),
-                   reinterpret_cast<float2*>(ksm + 2 * 128 * KS2_LD) + 128 * NC};
-  float2* xi = reinterpret_cast<float2*>(ksm + 2 * 128 * KS2_LD) + 2 * 128 * NC;
+  constexpr int NBUF = COMPUTE ? 1 : 2;
+  float* tile[2] = {ksm, ksm + (NBUF - 1) * 128 * KS2_LD};
+  float2* xj[2] = {reinterpret_cast<float2*>(ksm + NBUF * 128 * KS2_LD),
+                   reinterpret_cast<float2*>(ksm + NBUF * 128 * KS2_LD) + (NBUF - 1) * 128 * NC};
+  float2* xi = reinterpret_cast<float2*>(ksm + NBUF * 128 * KS2_LD) + NBUF * 128 * NC;
   float* red = reinterpret_cast<float*>(xi + 128 * NC);  // quarters 1..3: 3 x 128 x NC x (s, e)
+  float* Qs = red + 3 * 128 * NC * 2;                   // COMPUTE: dp x (128 + 1)
+  float* Xs = Qs + (COMPUTE ? dp * 129 : 0);            // COMPUTE: 128 x dp (16-byte aligned: dp % 16 == 0)
   const int tid = threadIdx.x;
   const int I = blockIdx.x;
   const int cnt = sym_band_count(I, nb);
@@ -358,6 +369,47 @@ __global__ void __launch_bounds__(KS2_THREADS, 1)
                : make_float2(0.0f, 0.0f);
   };
   for (int idx = tid; idx < 128 * NC; idx += KS2_THREADS) xi[idx] = xpair(I * 128 + idx / NC, idx % NC);
+  if constexpr (COMPUTE) {
+    for (int idx = tid; idx < 128 * dp; idx += KS2_THREADS) {
+      const int rr = idx / dp, k = idx - rr * dp;
+      Qs[k * 129 + rr] = Xc[(int64_t)(I * 128 + rr) * dp + k];
+    }
+  }
+  // COMPUTE: block J's points and vector tile, then the kernel values
+  auto compute = [&](int t) {
+    const int J = I + t < nb ? I + t : I + t - nb;
+    for (int idx = tid; idx < 128 * dp / 4; idx += KS2_THREADS)
+      reinterpret_cast<float4*>(Xs)[idx] = reinterpret_cast<const float4*>(Xc + (int64_t)J * 128 * dp)[idx];
+    for (int idx = tid; idx < 128 * NC; idx += KS2_THREADS) xj[0][idx] = xpair(J * 128 + idx / NC, idx % NC);
+    __syncthreads();
+    uint64_t d2p[32];  // (sum over even features, sum over odd features)
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) d2p[jj] = 0ull;
+    for (int k0 = 0; k0 < dp; k0 += 16) {
+      uint64_t q2[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) q2[i] = pk2(Qs[(k0 + 2 * i) * 129 + r], Qs[(k0 + 2 * i + 1) * 129 + r]);
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) {
+        const float4* xr = reinterpret_cast<const float4*>(Xs + (q * 32 + jj) * dp + k0);
+#pragma unroll
+        for (int k4 = 0; k4 < 4; ++k4) {
+          const float4 x4 = xr[k4];
+          uint64_t d = sub_f32x2(q2[2 * k4], pk2(x4.x, x4.y));
+          d2p[jj] = fma_f32x2(d, d, d2p[jj]);
+          d = sub_f32x2(q2[2 * k4 + 1], pk2(x4.z, x4.w));
+          d2p[jj] = fma_f32x2(d, d, d2p[jj]);
+        }
+      }
+    }
+    const bool row_in = I * 128 + r < n;
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) {
+      const float2 hh = unpk2(d2p[jj]);
+      const float kv = plain_kernel_value<KF>(hh.x + hh.y, pc);
+      tile[0][r * KS2_LD + q * 32 + jj] = (row_in && J * 128 + q * 32 + jj < n) ? kv : 0.0f;
+    }
+  };
   auto load = [&](int t, int buf) {
     const int J = I + t < nb ? I + t : I + t - nb;
     float* Tl = tile[buf];
@@ -405,11 +457,13 @@ __global__ void __launch_bounds__(KS2_THREADS, 1)
   for (int a = 0; a < 2; ++a)
 #pragma unroll
     for (int c = 0; c < NC; ++c) rs[a][c] = re[a][c] = 0.0f;
-  load(0, 0);
+  if constexpr (!COMPUTE) load(0, 0);
   for (int t = 0; t < cnt; ++t) {
-    const int buf = t & 1;
+    const int buf = COMPUTE ? 0 : (t & 1);
     const int J = I + t < nb ? I + t : I + t - nb;
-    if (t + 1 < cnt) {
+    if constexpr (COMPUTE) {
+      compute(t);
+    } else if (t + 1 < cnt) {
       load(t + 1, buf ^ 1);
       asm volatile("cp.async.wait_group 1;" ::: "memory");
     } else {
@@ -496,19 +550,29 @@ __global__ void kcache_combine_kernel(float* __restrict__ T, int cols, int c0, c
   T[i * ld + cols + c0 + k] = e;
 }
 
-template <int NC>
-static int symv_launch(kop_s* op, const float* V2, int cols, int c0, float* T, cudaStream_t st) {
-  auto kern = kcache_symv_kernel<NC>;
-  const size_t smem = sizeof(float) * (2 * 128 * KS2_LD) + sizeof(float2) * 3 * 128 * NC +
-                      sizeof(float) * 3 * 128 * NC * 2;
+static size_t symv_smem(int nc, bool compute, int dp) {
+  const int nbuf = compute ? 1 : 2;
+  size_t b = sizeof(float) * (nbuf * 128 * KS2_LD) + sizeof(float2) * (nbuf + 1) * 128 * nc +
+             sizeof(float) * 3 * 128 * nc * 2;
+  if (compute) b += sizeof(float) * ((size_t)dp * 129 + (size_t)128 * dp) + 16;
+  return b;
+}
+
+template <int NC, int KF, bool COMPUTE>
+static int symv_launch_t(kop_s* op, const float* V2, int cols, int c0, float* T, cudaStream_t st) {
+  auto kern = kcache_symv_kernel<NC, KF, COMPUTE>;
+  const int dp = op->pts.dp;
+  const size_t smem = symv_smem(NC, COMPUTE, dp);
   static bool attr_set = false;
   if (!attr_set) {
-    KOP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    KOP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_limit_bytes()));
     attr_set = true;
   }
   const int n = (int)op->pts.n;
   const int nb = (n + 127) / 128, h = nb / 2;
-  kern<<<(unsigned)nb, KS2_THREADS, smem, st>>>(op->kc, n, nb, h, V2, cols, c0, T, op->kc_scratch);
+  const PlainConst pc = plain_constants(op->kernel, op->bw);
+  kern<<<(unsigned)nb, KS2_THREADS, smem, st>>>(op->kc, n, nb, h, V2, cols, c0, T, op->kc_scratch, op->pts.xc, dp,
+                                                pc);
   KOP_LAUNCHED();
   if (h > 0) {
     const int64_t tot = (int64_t)n * NC;
@@ -518,30 +582,71 @@ static int symv_launch(kop_s* op, const float* V2, int cols, int c0, float* T, c
   return KOP_OK;
 }
 
-int check_matvec_cached(kop_s* op, bool build, const float* V2, int cols, float* T, cudaStream_t st) {
-  const int n = (int)op->pts.n;
-  if (build) {
-    const int rc = check_cache_build(op, st);
-    if (rc) return rc;
+template <int NC>
+static int symv_launch(kop_s* op, bool compute, const float* V2, int cols, int c0, float* T, cudaStream_t st) {
+  if (!compute) return symv_launch_t<NC, KF_RBF, false>(op, V2, cols, c0, T, st);
+  switch (op->kernel) {
+    case KF_RBF: return symv_launch_t<NC, KF_RBF, true>(op, V2, cols, c0, T, st);
+    case KF_LAPLACE: return symv_launch_t<NC, KF_LAPLACE, true>(op, V2, cols, c0, T, st);
+    default: return symv_launch_t<NC, KF_MATERN, true>(op, V2, cols, c0, T, st);
   }
+}
+
+// Column-part scratch for the symmetric check products: nb x h x 128 pairs
+// per column group.  false when it does not fit next to the caller's data.
+static int sym_scratch(kop_s* op, int cols, cudaStream_t st, bool* fits) {
+  const int n = (int)op->pts.n;
   const int nb = (n + 127) / 128, h = nb / 2;
   const int nc = cols <= 1 ? 1 : (cols <= 2 ? 2 : 4);
   const size_t need = (size_t)nb * h * 128 * nc * 2;  // (sum, error) pairs
+  *fits = true;
   if (need > op->kc_scratch_floats) {
     if (op->kc_scratch) cudaFreeAsync(op->kc_scratch, st);
     op->kc_scratch = nullptr;
     op->kc_scratch_floats = 0;
+    size_t fr = 0, tot = 0;
+    KOP_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
+    if (fr < sizeof(float) * need + (size_t(4) << 30)) {
+      *fits = false;
+      return KOP_OK;
+    }
     KOP_CUDA_TRY(cudaMallocAsync((void**)&op->kc_scratch, sizeof(float) * (need > 0 ? need : 1), st));
     op->kc_scratch_floats = need;
   }
+  return KOP_OK;
+}
+
+static int sym_products(kop_s* op, bool compute, const float* V2, int cols, float* T, cudaStream_t st) {
+  const int nc = cols <= 1 ? 1 : (cols <= 2 ? 2 : 4);
   for (int c0 = 0; c0 < cols; c0 += nc) {
     int rc;
-    if (nc == 1) rc = symv_launch<1>(op, V2, cols, c0, T, st);
-    else if (nc == 2) rc = symv_launch<2>(op, V2, cols, c0, T, st);
-    else rc = symv_launch<4>(op, V2, cols, c0, T, st);
+    if (nc == 1) rc = symv_launch<1>(op, compute, V2, cols, c0, T, st);
+    else if (nc == 2) rc = symv_launch<2>(op, compute, V2, cols, c0, T, st);
+    else rc = symv_launch<4>(op, compute, V2, cols, c0, T, st);
     if (rc) return rc;
   }
   return KOP_OK;
+}
+
+int check_matvec_cached(kop_s* op, bool build, const float* V2, int cols, float* T, cudaStream_t st) {
+  if (build) {
+    const int rc = check_cache_build(op, st);
+    if (rc) return rc;
+  }
+  bool fits = true;
+  if (int rc = sym_scratch(op, cols, st, &fits)) return rc;
+  if (!fits) return fail(KOP_ENOMEM, "check product: no device memory for the column parts");
+  return sym_products(op, false, V2, cols, T, st);
+}
+
+int check_matvec_computed(kop_s* op, const float* V2, int cols, float* T, cudaStream_t st, bool* done) {
+  *done = false;
+  if (symv_smem(cols <= 1 ? 1 : (cols <= 2 ? 2 : 4), true, op->pts.dp) > smem_limit_bytes()) return KOP_OK;
+  bool fits = true;
+  if (int rc = sym_scratch(op, cols, st, &fits)) return rc;
+  if (!fits) return KOP_OK;
+  *done = true;
+  return sym_products(op, true, V2, cols, T, st);
 }
 
 }  // namespace kop

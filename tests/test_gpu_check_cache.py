@@ -150,3 +150,33 @@ def test_caller_buffer_checked():
         op.set_check_cache(True, buf[1:])
     op.set_check_cache(True, buf)
     op.set_check_cache(False)
+
+
+@pytest.mark.parametrize("kind,n,nrhs", [(ops.LAPLACE, 6001, 1), (ops.MATERN52, 5000, 3)])
+def test_computed_checks_match_stored_checks(kind, n, nrhs):
+    """Beyond 4096 rows the solver's checks run the direct-difference
+    operator: from the stored matrix, or (no stored matrix) with each pair of
+    row blocks computed once in shared memory by the build's arithmetic and
+    used for both of its contributions.  The two forms give the same check
+    products, so the solves take the same decisions, and the oracle's FP64
+    residual of the accepted iterates meets the tolerance."""
+    d = 8
+    X = W.random_points(n, d, seed=n)
+    bw = 2.0 * np.sqrt(d)
+    B = W.random_block(n, nrhs, seed=n + 1)
+    lam = 1e-3 * n
+    op = ops.KernelOperator(torch.from_numpy(X).cuda(), kind, bw)
+    ny = ops.Nystrom(op, torch.from_numpy(W.gaussian_sketch(n, 64, seed=n)).cuda())
+    # refinements with the check operator every 5 iterations, stops certified
+    # by the FP64 operator: every check product is a plain refinement
+    kw = dict(tol=1e-6, maxit=400, refine_every=5, refine_mode=ops.PLAIN, check_mode=ops.EXACT)
+    a = _solve(op, B, [lam], ny, None, **kw)
+    b = _solve(op, B, [lam], ny, "library", **kw)
+    assert a.converged and b.converged
+    assert a.iters == b.iters
+    xa, xb = a.x.cpu().numpy(), b.x.cpu().numpy()
+    assert np.allclose(xa, xb, rtol=0, atol=1e-9 * np.abs(xb).max())
+    K = O.kernel_matrix(_KIND[kind], X.astype(np.float64), X.astype(np.float64), bw)
+    for c in range(nrhs):
+        r = B[:, c] - (K @ xa[:, c] + lam * xa[:, c])
+        assert np.linalg.norm(r) <= 1e-6 * np.linalg.norm(B[:, c]) * (1 + 1e-9)
