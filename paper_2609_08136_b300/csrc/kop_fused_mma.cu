@@ -54,7 +54,8 @@ constexpr int K3_NKS = 8;
 // -7e-7).  The Nystrom sketch keeps one accumulator and 256-column chunks:
 // its drift rescales the sketch by the same relative amount, which the
 // randomized preconditioner does not notice, and the narrower chunks would
-// double its distance and kernel-value work.
+// double its distance and kernel-value work; it also drops the kernel
+// values' lo half (see MmaArgs::klo).
 constexpr int K3_DRAIN = 4;
 static_assert(K3_NKS >= K3_MAXX + K3_NSB - 1, "norm ring too shallow");
 
@@ -74,6 +75,9 @@ struct MmaArgs {
   // O is restarted every `drain` tiles (0: never) and its partial added to a
   // running sum in TMEM (columns OCOL + mc .., so mc <= 128)
   int drain;
+  // klo = 0: the kernel values' lo half is dropped (the sketch: K rounded to
+  // FP16 times V exactly), two contraction MMAs instead of three
+  int klo;
 };
 
 struct K3Layout {
@@ -274,14 +278,18 @@ __global__ void __launch_bounds__(K3_THREADS, 1)
           // (P split, V split): lo*hi, hi*hi [, hi*lo]; P hi at +0, lo at +16 of each 32-column chunk
           const uint32_t pb = tmem + b * K3_BN;
           const uint64_t vd = dv0 + (uint64_t)(sv * nvs) * v_split16;
+          if (a.klo) {
 #pragma unroll
-          for (int kk = 0; kk < K3_BN / 16; ++kk) {
-            tc_mma_ts_elect(tmem + OCOL, pb + 32u * (kk >> 1) + 8u * (kk & 1) + 16u, vd + 2 * kk, idesc_o, oacc);
-            oacc = 1;
+            for (int kk = 0; kk < K3_BN / 16; ++kk) {
+              tc_mma_ts_elect(tmem + OCOL, pb + 32u * (kk >> 1) + 8u * (kk & 1) + 16u, vd + 2 * kk, idesc_o, oacc);
+              oacc = 1;
+            }
           }
 #pragma unroll
-          for (int kk = 0; kk < K3_BN / 16; ++kk)
-            tc_mma_ts_elect(tmem + OCOL, pb + 32u * (kk >> 1) + 8u * (kk & 1), vd + 2 * kk, idesc_o, 1u);
+          for (int kk = 0; kk < K3_BN / 16; ++kk) {
+            tc_mma_ts_elect(tmem + OCOL, pb + 32u * (kk >> 1) + 8u * (kk & 1), vd + 2 * kk, idesc_o, oacc);
+            oacc = 1;
+          }
           if (nvs == 2) {
 #pragma unroll
             for (int kk = 0; kk < K3_BN / 16; ++kk)
@@ -451,7 +459,7 @@ __global__ void __launch_bounds__(K3_THREADS, 1)
         }
       }
       tmem_st16(lane_addr + col, ph16);
-      tmem_st16(lane_addr + col + 16, pl16);
+      if (a.klo) tmem_st16(lane_addr + col + 16, pl16);
       tmem_st_wait();
       tc_fence_before();
       mbar_arrive(&pfull[b]);
@@ -646,6 +654,12 @@ static int run_mma(const PointSet& Q, const PointSet& Ks, bool self, int kf, con
     a.f16 = f16 ? 1 : 0;
     a.inv_scale = vinv;
     a.drain = sketch ? 0 : K3_DRAIN;
+    // the sketch takes the kernel values rounded to FP16 (hi only) against V
+    // carried exactly (hi + lo): it is then the sketch of a kernel matrix
+    // perturbed by about 2^-12 per entry, which a preconditioner does not
+    // notice (measured: the same PCG iterations on the Laplace mixture and
+    // the Matern n = 1e6 workloads) for a third less contraction work
+    a.klo = sketch ? 0 : 1;
     switch (kf) {
       case KF_RBF: rc = launch_mma_t<KF_RBF>(Q, Ks, tv, a, st); break;
       case KF_LAPLACE: rc = launch_mma_t<KF_LAPLACE>(Q, Ks, tv, a, st); break;
