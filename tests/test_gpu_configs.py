@@ -119,3 +119,31 @@ def test_benchmark_path_scaled_n16384():
                         inner_mode=ops.FAST, refine_mode=ops.PLAIN, check_mode=ops.PLAIN)
     assert res.converged
     _accept(O.LAPLACE, wl.X, wl.bandwidth, [lam], wl.B, res.x.cpu().numpy())
+
+
+def test_block_workload_all_columns_n8000():
+    """The block workload's full shape at n = 8000: d = 128, RBF sigma =
+    sqrt(128), 64 right-hand sides x 16 shifts lam in logspace(-8, -3) n
+    (1024 columns, one solve), rank 800, the library's default modes.  Every
+    column must meet the paper's acceptance test (FP64 relative residual
+    <= 1e-6, against the oracle's dense K), and for the smallest and the
+    largest shift the first right-hand side must match a dense Cholesky
+    solve to 1e-4."""
+    n, nrhs, n_shifts, r = 8000, 64, 16, 800
+    wl = W.krr_rbf_block(seed=0, n=n, nrhs=nrhs, n_shifts=n_shifts, rank=r)
+    lams = [float(x) for x in wl.lambdas]
+    op = ops.KernelOperator(torch.from_numpy(wl.X).cuda(), ops.RBF, wl.bandwidth)
+    ny = ops.Nystrom(op, torch.from_numpy(W.gaussian_sketch(n, r, seed=0)).cuda())
+    res = ops.pcg_solve(op, torch.from_numpy(wl.B).cuda(), lams, nys=ny, tol=1e-6, maxit=500)
+    assert res.converged
+    Xg = res.x.cpu().numpy()
+    K = O.kernel_matrix(O.RBF, wl.X, wl.X, wl.bandwidth)
+    lam_col = np.repeat(np.asarray(lams), nrhs)
+    Bc = np.tile(wl.B.astype(np.float64), (1, n_shifts))
+    R = K @ Xg + lam_col[None, :] * Xg - Bc
+    rel = np.linalg.norm(R, axis=0) / np.linalg.norm(Bc, axis=0)
+    assert np.all(rel <= 1e-6), (int(np.argmax(rel)), rel.max())
+    for s in (0, n_shifts - 1):
+        xs = sla.cho_solve(sla.cho_factor(K + lams[s] * np.eye(n)), wl.B[:, 0].astype(np.float64))
+        x = Xg[:, s * nrhs]
+        assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= 1e-4, s
