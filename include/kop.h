@@ -97,8 +97,9 @@ int kop_sfu_rates(double* rates, void* stream);
 /* Tile autotuner of the block operator product (m > 8 columns): the column
  * chunk and the ring depths of the fused tensor-core kernel.  When on (the
  * default), the first product of a shape (kernel, log2 n, feature width,
- * columns rounded up to 64, sketch or solver form) runs every candidate that
- * fits in shared memory once, timed with CUDA events on the caller's stream
+ * columns rounded up to 64, sketch or solver form) runs each candidate (the
+ * heuristic's column chunk and the next narrower one, with every X-ring depth
+ * that fits in shared memory) once, timed with CUDA events on the caller's stream
  * (which this synchronizes), keeps the fastest for that shape, and returns
  * the product computed with it; later products of the shape reuse it.
  * Candidates differ only in rounding.  Off: a fixed heuristic (widest chunk,

@@ -735,12 +735,13 @@ int fused_matvec_mma(const PointSet& Q, const PointSet& Ks, bool self, int kf, c
   KOP_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
   if (!g_autotune.load() || cap != cudaStreamCaptureStatusNone)
     return run_mma(Q, Ks, self, kf, kc, V, m, ldv, O, ldo, status, st, sketch, h.mc, h.nx, h.nv);
-  // candidates: every chunk width up to the form's limit (no wider than the
-  // columns need) with X rings of depth 2 .. 4 and the deepest V ring that fits
+  // candidates: the heuristic's chunk width and the next narrower one (a
+  // narrower chunk repeats the distance and kernel-value work per chunk:
+  // measured 64-column chunks 3.5x slower at m = 500), with X rings of depth
+  // 2 .. 4 and the deepest V ring that fits
   std::vector<MmaTile> cand;
-  const int mpad = (m + 63) / 64 * 64;
   const size_t lim = smem_limit_bytes();
-  for (int mc = 64; mc <= (sketch ? 256 : 128) && mc <= mpad; mc += 64)
+  for (int mc = h.mc > 64 ? h.mc - 64 : h.mc; mc <= h.mc; mc += 64)
     for (int nx = 2; nx <= K3_MAXX; ++nx) {
       if (mma_smem_bytes(Q.dp, mc, nx, 2, 2) > lim) continue;
       int nv = K3_MAXV;
