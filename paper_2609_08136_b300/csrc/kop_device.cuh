@@ -277,6 +277,35 @@ KOP_DEV float rsqrt_approx(float x) {
   return y;
 }
 
+// Packed two-lane FP32 arithmetic (add / mul / fma .rn.f32x2): each lane is
+// the IEEE round-to-nearest result of the scalar operation, so a loop that
+// pairs independent scalar chains gives bit-identical results in half the
+// issued instructions.
+KOP_DEV float2 add2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n.reg .b64 pa, pb, pd;\nmov.b64 pa, {%2, %3};\nmov.b64 pb, {%4, %5};\n"
+      "add.rn.f32x2 pd, pa, pb;\nmov.b64 {%0, %1}, pd;\n}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+KOP_DEV float2 mul2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n.reg .b64 pa, pb, pd;\nmov.b64 pa, {%2, %3};\nmov.b64 pb, {%4, %5};\n"
+      "mul.rn.f32x2 pd, pa, pb;\nmov.b64 {%0, %1}, pd;\n}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+KOP_DEV float2 fma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n.reg .b64 pa, pb, pc, pd;\nmov.b64 pa, {%2, %3};\nmov.b64 pb, {%4, %5};\nmov.b64 pc, {%6, %7};\n"
+      "fma.rn.f32x2 pd, pa, pb, pc;\nmov.b64 {%0, %1}, pd;\n}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+
 // Error-free transformation s + e = a + b (Knuth's TwoSum).
 KOP_DEV void two_sum_acc(float& s, float& e, float b) {
   float t = s + b;

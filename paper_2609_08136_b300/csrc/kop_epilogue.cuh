@@ -62,4 +62,20 @@ KOP_DEV float kval_u(float u, float c2) {
   }
 }
 
+// kval_u on two independent entries; for the Laplace kernel the FP32 product
+// sqrt(u) = |u| rsqrt(|u|) is packed two lanes per instruction (each lane's
+// value is bit-identical to kval_u).  The other kernels take kval_u per lane:
+// packing Matern's arithmetic spilled registers in the symmetric product.
+template <int KF>
+KOP_DEV float2 kval_u2(float2 u, float c2) {
+  if constexpr (KF == 1) {
+    const float2 au = make_float2(fabsf(u.x), fabsf(u.y));
+    const float2 rs = make_float2(rsqrt_approx(fmaxf(au.x, 1e-30f)), rsqrt_approx(fmaxf(au.y, 1e-30f)));
+    const float2 a = mul2(au, rs);
+    return make_float2(ex2_approx(-a.x), ex2_approx(-a.y));
+  } else {
+    return make_float2(kval_u<KF>(u.x, c2), kval_u<KF>(u.y, c2));
+  }
+}
+
 }  // namespace kop

@@ -288,9 +288,10 @@ __global__ void __launch_bounds__(KS_THREADS, 1)
       vq[e] = row0 + e < a.n ? a.V[row0 + e] : 0.0f;
     }
     named_bar_sync(1, 128 * KS_NWG);
-    float acc[KS_WCOLS];
+    // row sums of the warpgroup's query columns, two columns per packed lane pair
+    float2 acc[KS_WCOLS / 2];
 #pragma unroll
-    for (int c = 0; c < KS_WCOLS; ++c) acc[c] = 0.0f;
+    for (int c = 0; c < KS_WCOLS / 2; ++c) acc[c] = make_float2(0.0f, 0.0f);
     bool live = true;
     for (int t = 0; t < cnt; ++t) {
       const int b = t % KS_NSB;
@@ -305,7 +306,8 @@ __global__ void __launch_bounds__(KS_THREADS, 1)
         tc_fence_after();
         const float knj = kn[s * 128 + kj];
         const float vj = J * 128 + kj < a.n ? vk[s * 128 + kj] : 0.0f;
-        float p4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        const float2 kn2 = make_float2(knj, knj), m2 = make_float2(a.m2c, a.m2c), vj2 = make_float2(vj, vj);
+        float2 p2a = make_float2(0.0f, 0.0f), p2b = make_float2(0.0f, 0.0f);
         // chunks of 32 query columns
 #pragma unroll
         for (int ch = 0; ch < KS_WCOLS / 32; ++ch) {
@@ -319,36 +321,36 @@ __global__ void __launch_bounds__(KS_THREADS, 1)
             if (lane == 0) mbar_arrive(&tempty[b]);
           }
           const int cb = wgi * KS_WCOLS + ch * 32;
-          float kv[32];
+          float2 kv[16];
 #pragma unroll
           for (int c4 = 0; c4 < 32; c4 += 4) {
             const float4 q4 = *reinterpret_cast<const float4*>(qn + cb + c4);
-            kv[c4 + 0] = fmaf(__uint_as_float(r[c4 + 0]), a.m2c, q4.x + knj);
-            kv[c4 + 1] = fmaf(__uint_as_float(r[c4 + 1]), a.m2c, q4.y + knj);
-            kv[c4 + 2] = fmaf(__uint_as_float(r[c4 + 2]), a.m2c, q4.z + knj);
-            kv[c4 + 3] = fmaf(__uint_as_float(r[c4 + 3]), a.m2c, q4.w + knj);
+            kv[c4 / 2] = fma2(make_float2(__uint_as_float(r[c4 + 0]), __uint_as_float(r[c4 + 1])), m2,
+                              add2(make_float2(q4.x, q4.y), kn2));
+            kv[c4 / 2 + 1] = fma2(make_float2(__uint_as_float(r[c4 + 2]), __uint_as_float(r[c4 + 3])), m2,
+                                  add2(make_float2(q4.z, q4.w), kn2));
           }
           if (t == 0 && cb <= kj && kj < cb + 32) {  // the diagonal: D2 = 0 exactly
 #pragma unroll
-            for (int c = 0; c < 32; ++c)
-              if (cb + c == kj) kv[c] = 0.0f;
+            for (int c = 0; c < 32; c += 2) {
+              if (cb + c == kj) kv[c / 2].x = 0.0f;
+              if (cb + c + 1 == kj) kv[c / 2].y = 0.0f;
+            }
           }
 #pragma unroll
-          for (int c = 0; c < 32; ++c) kv[c] = kval_u<KF>(kv[c], a.c2);
+          for (int c = 0; c < 16; ++c) kv[c] = kval_u2<KF>(kv[c], a.c2);
 #pragma unroll
-          for (int c = 0; c < 32; ++c) acc[ch * 32 + c] = fmaf(kv[c], vj, acc[ch * 32 + c]);
+          for (int c = 0; c < 16; ++c) acc[ch * 16 + c] = fma2(kv[c], vj2, acc[ch * 16 + c]);
           if (t > 0) {
 #pragma unroll
             for (int c4 = 0; c4 < 32; c4 += 4) {
               const float4 v4 = *reinterpret_cast<const float4*>(vq + cb + c4);
-              p4[0] = fmaf(kv[c4 + 0], v4.x, p4[0]);
-              p4[1] = fmaf(kv[c4 + 1], v4.y, p4[1]);
-              p4[2] = fmaf(kv[c4 + 2], v4.z, p4[2]);
-              p4[3] = fmaf(kv[c4 + 3], v4.w, p4[3]);
+              p2a = fma2(kv[c4 / 2], make_float2(v4.x, v4.y), p2a);
+              p2b = fma2(kv[c4 / 2 + 1], make_float2(v4.z, v4.w), p2b);
             }
           }
         }
-        col = (p4[0] + p4[1]) + (p4[2] + p4[3]);
+        col = (p2a.x + p2a.y) + (p2b.x + p2b.y);
       }
       if (t > 0 && live) {
         // this warpgroup's column part of key kj, for the combining warp
@@ -368,8 +370,10 @@ __global__ void __launch_bounds__(KS_THREADS, 1)
     named_bar_sync(1, 128 * KS_NWG);
     float* red = (float*)smem;
 #pragma unroll
-    for (int c = 0; c < KS_WCOLS; ++c)
-      red[(wgi * 128 + kj) * (KS_WCOLS + 1) + c] = acc[c];
+    for (int c = 0; c < KS_WCOLS / 2; ++c) {
+      red[(wgi * 128 + kj) * (KS_WCOLS + 1) + 2 * c] = acc[c].x;
+      red[(wgi * 128 + kj) * (KS_WCOLS + 1) + 2 * c + 1] = acc[c].y;
+    }
     named_bar_sync(1, 128 * KS_NWG);
     if (quarter < KS_WCOLS / 32) {
       const int c = quarter * 32 + lane;
