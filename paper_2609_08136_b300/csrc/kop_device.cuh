@@ -306,6 +306,28 @@ KOP_DEV float2 fma2(float2 a, float2 b, float2 c) {
   return d;
 }
 
+// The same operations on a pair kept packed in one 64-bit register (lo, hi).
+KOP_DEV uint64_t pk2(float lo, float hi) {
+  uint64_t d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+  return d;
+}
+KOP_DEV float2 unpk2(uint64_t v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+KOP_DEV uint64_t sub_f32x2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+KOP_DEV uint64_t fma_f32x2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
 // Error-free transformation s + e = a + b (Knuth's TwoSum).
 KOP_DEV void two_sum_acc(float& s, float& e, float b) {
   float t = s + b;
