@@ -37,9 +37,9 @@ sys.path.insert(0, ROOT)
 METRIC = "PCG time-to-relres 1e-6 & fused kernel-matvec TFLOP/s vs plain FP32 path"
 TOL = 1e-6
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the FAST
-# single-vector product, keyed by (kernel, n, d); mean of seven launches at
+# single-vector product, keyed by (kernel, n, d); mean of two launches at
 # full size, taken on the kernel as it stands
-TRAFFIC_BYTES = {(1, 200_000, 64): 96.22e6 + 571.19e6}
+TRAFFIC_BYTES = {(1, 200_000, 64): 94.67e6 + 570.85e6}
 
 # name: (generator kwargs, description, refine_every, maxit)
 WORKLOADS = {
