@@ -208,9 +208,10 @@ int kop_sync(kop_t op, void* stream);
  *
  * nys_build: Omega (device, n x r FP32) is the caller's test matrix (the
  * library does not orthonormalize it; Gaussian N(0,1)/sqrt(n) entries are
- * expected).  It is used as given in every step (the sketch's tensor-core
- * contraction carries it as a BF16 hi + lo pair, about 2^-16 relative, like
- * the fast operator's kernel values).  Steps: Y = K Omega (fused operator, `mode`),
+ * expected).  It is used as given in every step (the KOP_FAST sketch's
+ * tensor-core contraction carries it, scaled per column by a power of two,
+ * as an FP16 hi + lo pair of 22 significant bits against the kernel values
+ * rounded to FP16, about 2^-12 relative per entry).  Steps: Y = K Omega (fused operator, `mode`),
  * nu = nu_rel * ||Y||_2 (nu_rel <= 0 selects 2^-16 for KOP_FAST and 2^-21
  * otherwise), Y_nu = Y + nu Omega, C = chol(sym(Omega^T Y_nu)) in FP64 (on a
  * failed pivot nu grows 10x, at most 3 times, then KOP_ENOTPD),

@@ -15,9 +15,10 @@
 // summed error-free on the CUDA cores, because the core squares the
 // condition of the sketch.  One Cholesky-QR pass afterwards restores the
 // orthonormality of U lost to FP32 rounding.  The caller's FP32 test matrix
-// is used as given in every step: the sketch's contraction carries it as a
-// BF16 hi + lo pair (about 2^-16 relative, the accuracy of the fast
-// operator's kernel values), the Gram blocks as the exact three-term split.
+// is used as given in every step: the fast sketch's contraction carries it
+// (scaled per column by a power of two) as an FP16 hi + lo pair against the
+// kernel values rounded to FP16, the Gram blocks as the exact three-term
+// split.
 #include <algorithm>
 #include <cmath>
 #include <vector>
