@@ -34,7 +34,7 @@ def _worker(rank, world, port, out):
 
 def test_two_gloo_ranks_take_the_slowest_time():
     world = 2
-    manager = mp.Manager()
+    manager = mp.get_context("spawn").Manager()  # no fork of this multi-threaded process
     out = manager.dict()
     mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
     assert out[0][0] == 2.0 and out[1][0] == 2.0
